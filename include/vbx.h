@@ -1,0 +1,168 @@
+/* vbx.h -- C ABI of the GB300 (sm_103a) per-scan map update of Voxblox
+ * (Oleynikova et al., arXiv 1611.03631): grouped-raycast TSDF fusion into a block-hashed
+ * map, the incremental ESDF update from the changed TSDF voxels, and trilinear
+ * distance/gradient queries.
+ *
+ * Conventions for every entry point:
+ *  - All pointers named *_dev are device pointers (CUDA global memory) owned by the caller;
+ *    all other pointers are host pointers owned by the caller. The library keeps no pointer
+ *    to caller memory after the work it enqueued has finished.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream). Work is
+ *    enqueued on it in order; calls that return host data synchronise that stream.
+ *  - The map owns its device memory (block hash, voxel pools, frontiers, per-scan scratch).
+ *  - Every call returns a vbx_status. Errors detected on the device (hash probe limit,
+ *    block pool exhausted, a device loop exceeding its round or wait budget) are recorded
+ *    in a sticky per-map error word and reported by the next call that synchronises
+ *    (vbx_sync, vbx_get_stats, the export calls). After VBX_ERR_HASH_FULL or
+ *    VBX_ERR_OUT_OF_MEMORY the map stays usable; voxels of blocks that could not be
+ *    allocated are not integrated.
+ *  - vbx_last_error() returns a thread-local message for the last non-OK status.
+ *  - Voxel coordinates are integer triples i with voxel centre (i + 1/2) * voxel_size.
+ *    Block (bx,by,bz) holds voxels [b*B, b*B + B) per axis; inside a block the local index
+ *    of voxel (lx,ly,lz) is (lz*B + ly)*B + lx.
+ */
+#ifndef VBX_H_
+#define VBX_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vbx_map_s* vbx_map_t;
+
+typedef enum {
+  VBX_OK = 0,
+  VBX_ERR_INVALID_ARG = 1,   /* bad size, pointer or parameter; nothing was enqueued */
+  VBX_ERR_OUT_OF_MEMORY = 2, /* device allocation failed or the block pool is exhausted */
+  VBX_ERR_HASH_FULL = 3,     /* block hash probe limit reached */
+  VBX_ERR_TIMEOUT = 4,       /* a device loop exceeded its round budget or a wait its limit */
+  VBX_ERR_CUDA = 5           /* a CUDA runtime call failed (message in vbx_last_error) */
+} vbx_status;
+
+/* Map options (Sec. IV-A weighting, Sec. IV-B merging, Sec. V-A fixed band). */
+typedef struct {
+  int weighting;          /* 0: constant weight, Eq. (2); 1: 1/z^2 with linear drop-off
+                             behind the surface, Eq. (4)                                    */
+  float eps;              /* drop-off start epsilon of Eq. (4); <= 0 selects voxel_size     */
+  float fixed_band;       /* gamma, ESDF fixed band |D| < gamma (Sec. V-A); <= 0 selects
+                             voxel_size (the one-voxel band recommended in Sec. VI-B)       */
+  float w_max;            /* W_max of Eq. (3); <= 0 selects 1e4 (the paper gives no value)  */
+  float max_range;        /* points farther than this from the sensor are dropped;
+                             <= 0 or +inf: no limit                                          */
+  int grouped;            /* 1: grouped raycasting, one ray per voxel holding points
+                             (Sec. IV-B); 0: one ray per point                              */
+  int64_t block_capacity; /* blocks in the voxel pool (device memory budget); 0: 2^25/B^3  */
+  int64_t max_points;     /* initial per-scan point capacity; grows on demand; 0: 1<<20     */
+} vbx_map_options;
+
+/* Fills *opt with the defaults above (weighting 0, grouped 1). */
+vbx_status vbx_default_options(vbx_map_options* opt);
+
+/* Creates a map of voxel size v (> 0, metres), blocks of voxels_per_block^3 voxels
+ * (4, 8, 16 or 32), truncation distance delta (>= v) and ESDF maximum distance d_max (> 0).
+ * Sec. III: layers of fixed-size blocks indexed by block position through a hash table.
+ * opt may be NULL (defaults). On success *out holds the new map. Allocates device memory
+ * on the current device: about 65 bytes per pool voxel plus per-scan scratch. */
+vbx_status vbx_create_map(float voxel_size, int voxels_per_block, float truncation, float max_esdf_dist,
+                          const vbx_map_options* opt, vbx_map_t* out);
+
+/* Frees all device memory of the map (synchronises the device). NULL is accepted. */
+vbx_status vbx_destroy_map(vbx_map_t map);
+
+/* Integrates one posed scan into the TSDF (Sec. IV: Eq. (1)-(4), grouped raycasting).
+ * points_dev: n x 3 float32, row-major, sensor frame; non-finite rows are dropped.
+ * T_world_sensor: 16 float32, row-major 4x4 homogeneous pose (host memory, copied).
+ * Rays run from the sensor origin to truncation distance behind each (grouped) point; each
+ * traversed voxel receives the projective distance of Eq. (1), truncated, with the weight of
+ * Eq. (2) or (4); all of a scan's updates of one voxel are merged by Eq. (3) at once.
+ * Updated voxels are queued for the next vbx_update_esdf. n = 0 is a no-op. */
+vbx_status vbx_integrate_scan(vbx_map_t map, const float* points_dev, int64_t n, const float T_world_sensor[16],
+                              void* stream);
+
+/* Updates the ESDF incrementally from the TSDF voxels updated since the last call
+ * (Sec. V-A, Algorithm 1): fixed band |D| < gamma, raise wavefront, then lower wavefront over
+ * 26-connected neighbours with quasi-Euclidean steps v, v*sqrt(2), v*sqrt(3), capped at
+ * d_max. Runs as one cooperative persistent kernel on `stream`. */
+vbx_status vbx_update_esdf(vbx_map_t map, void* stream);
+
+/* Distance and gradient queries (the planner's interface, Sec. VII; trilinear interpolation
+ * as in Sec. VI-A). q_dev: n x 3 float32 world points. Outputs (device, caller-owned):
+ * dist_dev n float32, grad_dev n x 3 float32, status_dev n uint8 (0 = ok, 1 = unknown: one of
+ * the 8 surrounding voxel centres is unobserved; dist/grad are NaN then). */
+vbx_status vbx_query_distance_gradient(vbx_map_t map, const float* q_dev, int64_t n, float* dist_dev,
+                                       float* grad_dev, uint8_t* status_dev, void* stream);
+
+/* Waits for `stream` and returns (and clears) the map's sticky device error, if any. */
+vbx_status vbx_sync(vbx_map_t map, void* stream);
+
+typedef struct {
+  int64_t points_in;      /* points passed to the last vbx_integrate_scan                  */
+  int64_t points_valid;   /* of those, accepted by the filter                               */
+  int64_t rays;           /* rays cast (groups when grouped, else valid points)             */
+  int64_t records;        /* voxel updates with w > 0 emitted by the rays                  */
+  int64_t updated;        /* distinct voxels updated by the last scan                       */
+  int64_t new_blocks;     /* blocks allocated by the last scan                              */
+  int64_t blocks;         /* blocks in the map                                              */
+  int64_t esdf_in;        /* TSDF voxels consumed by the last vbx_update_esdf               */
+  int64_t seeds;          /* of those, in the fixed band                                    */
+  int64_t raise_pops;     /* voxels processed by raise rounds                               */
+  int64_t lower_pops;     /* voxels processed by lower rounds                               */
+  int64_t raise_rounds;
+  int64_t lower_rounds;
+  int64_t launches;       /* kernels launched by this map since creation                    */
+} vbx_stats;
+
+/* Synchronises `stream`, then fills *out. Returns the sticky device error if one is set. */
+vbx_status vbx_get_stats(vbx_map_t map, vbx_stats* out, void* stream);
+
+/* Number of blocks in the map (synchronises `stream`). */
+vbx_status vbx_num_blocks(vbx_map_t map, int64_t* n_out, void* stream);
+
+/* Copies the map to host memory in pool order (block allocation order), cap >= number of
+ * blocks (else VBX_ERR_INVALID_ARG). Any output pointer may be NULL to skip it.
+ *   keys:   cap x 3 int32 block coordinates
+ *   tsdf:   cap x B^3 x 2 float32 (D, W) per voxel
+ *   esdf_d: cap x B^3 float32 ESDF distance per voxel
+ *   parent: cap x B^3 uint8, direction to the parent voxel (k = (dx+1)*9+(dy+1)*3+(dz+1), 255 none)
+ *   flags:  cap x B^3 uint8, bit0 observed, bit1 fixed
+ * Synchronises `stream`. */
+vbx_status vbx_export_blocks(vbx_map_t map, int32_t* keys, float* tsdf, float* esdf_d, uint8_t* parent,
+                             uint8_t* flags, int64_t cap, void* stream);
+
+/* Voxel coordinates (cap x 3 int32, host) of the voxels updated by the last
+ * vbx_integrate_scan or vbx_import_tsdf, in unspecified order; *n_out = their number
+ * (entries beyond cap are not written). Synchronises `stream`. */
+vbx_status vbx_export_updated(vbx_map_t map, int32_t* vox, int64_t cap, int64_t* n_out, void* stream);
+
+/* Sets TSDF voxels directly (host arrays: vox n x 3 int32, D n float32, W n float32), allocating
+ * their blocks, and queues them for the next vbx_update_esdf exactly as if a scan had updated
+ * them. Used to restore a saved map and to drive the ESDF from given TSDF values.
+ * Duplicate voxels in one call are not allowed. Synchronises `stream`. */
+vbx_status vbx_import_tsdf(vbx_map_t map, const int32_t* vox, const float* D, const float* W, int64_t n,
+                           void* stream);
+
+/* Per-kernel timing with CUDA events recorded on the launch stream around each kernel of
+ * this map (off by default). */
+vbx_status vbx_set_profiling(vbx_map_t map, int enable);
+
+/* Names (static strings) and accumulated milliseconds / launch counts of the profiled
+ * kernels; *n_out = number of kernel kinds (<= cap written). Synchronises `stream`.
+ * vbx_reset_kernel_times clears the accumulators. */
+vbx_status vbx_get_kernel_times(vbx_map_t map, const char** names, double* ms, int64_t* launches, int cap,
+                                int* n_out, void* stream);
+vbx_status vbx_reset_kernel_times(vbx_map_t map);
+
+/* Kernels launched by all maps of this process (a running counter). */
+int64_t vbx_total_launches(void);
+
+/* Thread-local message describing the last error returned on this thread ("" if none). */
+const char* vbx_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VBX_H_ */

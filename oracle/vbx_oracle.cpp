@@ -260,7 +260,10 @@ bool accept_point(const Params& p, const float ps[3], float* w) {
   if (!std::isfinite(ps[0]) || !std::isfinite(ps[1]) || !std::isfinite(ps[2])) return false;
   float r2 = (ps[0] * ps[0] + ps[1] * ps[1]) + ps[2] * ps[2];
   if (!(r2 > 0.0f)) return false;
-  if (std::isfinite(p.max_range) && r2 > p.max_range * p.max_range) return false;
+  // R1: points farther than 2^14 voxels from the sensor are dropped (bounds the ray length).
+  const float lim = 16384.0f * p.v;
+  if (!(r2 < lim * lim)) return false;
+  if (std::isfinite(p.max_range) && p.max_range > 0.0f && r2 > p.max_range * p.max_range) return false;
   if (p.weighting == 1) {
     // Eq. (4): 1/z^2 with z the depth of the measurement in the sensor frame.
     if (!(ps[2] > 0.0f)) return false;

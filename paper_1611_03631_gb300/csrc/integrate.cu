@@ -1,0 +1,455 @@
+// integrate.cu -- TSDF integration of one posed scan (Sec. IV of Oleynikova et al. 2017):
+//   k_bin_points     A1+A2  transform, filter, voxel key; grouped raycasting bins points into
+//                           a per-scan hash table with exact integer sums (order-independent)
+//   k_group_rays     A2+A3  group mean and weight -> one ray per group; block-level DDA over
+//                           the ray and lock-free insertion of its blocks into the block hash
+//   k_link_blocks    A3     26-neighbour links of the new blocks (O(1) neighbour access later)
+//   k_integrate_rays A4     voxel-level integer DDA; Eq. (1) distance, Eq. (2)/(4) weight;
+//                           per-voxel sums of w and w*d in 2^-28 fixed point with integer
+//                           atomics, pre-aggregated across the warp (order-independent, so
+//                           the result does not depend on scheduling)
+//   k_apply          A5     Eq. (3) merge of each updated voxel; queues it for the ESDF
+// All float32 arithmetic that decides a set (keys, endpoints, visited voxels, w > 0) uses
+// explicitly rounded intrinsics, so the compiler cannot contract or reorder it.
+#include <cuda_runtime.h>
+
+#include "launch.h"
+#include "vbx_internal.cuh"
+
+namespace vbx {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr unsigned kFull = 0xffffffffu;
+
+// A1 filter and per-point weight. Returns false for a dropped point.
+__device__ __forceinline__ bool accept_point(const DevMap& m, float x, float y, float z, float* w) {
+  if (!isfinite(x) || !isfinite(y) || !isfinite(z)) return false;
+  const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)), __fmul_rn(z, z));
+  if (!(r2 > 0.0f)) return false;
+  if (!(r2 < m.range_lim2)) return false;
+  if (m.max_range2 > 0.0f && r2 > m.max_range2) return false;
+  if (m.weighting == 1) {
+    if (!(z > 0.0f)) return false;
+    const float wi = __fdiv_rn(1.0f, __fmul_rn(z, z));  // Eq. (4): 1/z^2, z = depth in the sensor frame
+    if (!(wi <= 1024.0f)) return false;
+    *w = wi;
+  } else {
+    *w = 1.0f;
+  }
+  return true;
+}
+
+// floor((hi * 2^64 + lo) / d) for a quotient known to be below 2^17.
+__device__ __forceinline__ unsigned div128_small(unsigned long long lo, unsigned long long hi, unsigned long long d) {
+  if (hi == 0) return (unsigned)(lo / d);
+  unsigned q = 0;
+  for (int b = 16; b >= 0; --b) {
+    const unsigned long long dl = d << b;
+    const unsigned long long dh = b ? (d >> (64 - b)) : 0ull;
+    if (hi > dh || (hi == dh && lo >= dl)) {
+      const unsigned long long borrow = lo < dl ? 1ull : 0ull;
+      lo -= dl;
+      hi = hi - dh - borrow;
+      q |= 1u << b;
+    }
+  }
+  return q;
+}
+
+__global__ void __launch_bounds__(kThreads) k_init_groups(GroupEntry* tab, uint32_t entries) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < entries; i += gridDim.x * blockDim.x) {
+    GroupEntry e;
+    e.key = kEmptyKey;
+    e.sw = 0;
+    e.swo_lo[0] = e.swo_lo[1] = e.swo_lo[2] = 0;
+    e.swo_hi[0] = e.swo_hi[1] = e.swo_hi[2] = 0;
+    e.n = 0;
+    tab[i] = e;
+  }
+}
+
+// ------------------------------------------------------------------------------- A1 + A2
+__global__ void __launch_bounds__(kThreads) k_bin_points(DevMap m, const float* __restrict__ pts, int n, Pose T) {
+  __shared__ unsigned long long sh_w[kWarps][32];
+  __shared__ unsigned long long sh_o[3][kWarps][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int stride = gridDim.x * blockDim.x;
+  for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
+    const int i = base + threadIdx.x;
+    bool valid = false;
+    unsigned long long key = kEmptyKey;
+    unsigned long long wq = 0, o[3] = {0, 0, 0};
+    float pw[3] = {0.f, 0.f, 0.f};
+    float w = 0.0f;
+    if (i < n) {
+      const float x = __ldg(&pts[3 * (size_t)i + 0]);
+      const float y = __ldg(&pts[3 * (size_t)i + 1]);
+      const float z = __ldg(&pts[3 * (size_t)i + 2]);
+      if (accept_point(m, x, y, z, &w)) {
+        bool in_range = true;
+        float q[3];
+        for (int r = 0; r < 3; ++r) {
+          pw[r] = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(T.T[4 * r], x), __fmul_rn(T.T[4 * r + 1], y)),
+                                      __fmul_rn(T.T[4 * r + 2], z)),
+                            T.T[4 * r + 3]);
+          q[r] = __fdiv_rn(pw[r], m.v);
+          if (!(fabsf(q[r]) < 1048576.0f)) in_range = false;
+        }
+        if (in_range) {
+          valid = true;
+          int k[3];
+          for (int r = 0; r < 3; ++r) {
+            const float fq = floorf(q[r]);
+            k[r] = (int)fq;
+            long long oo = __float2ll_rn(__fmul_rn(__fsub_rn(q[r], fq), 65536.0f));
+            o[r] = (unsigned long long)(oo > 65535 ? 65535 : oo);
+          }
+          key = pack_key(k[0], k[1], k[2]);
+          wq = m.weighting == 0 ? 1ull : (unsigned long long)__float2ll_rn(__fmul_rn(w, 1048576.0f));
+        }
+      }
+    }
+    const unsigned vmask = __ballot_sync(kFull, valid);
+    if (lane == 0 && vmask) atomicAdd(&m.ctr->npoints_valid, (unsigned)__popc(vmask));
+    if (!m.grouped) {  // one ray per point
+      if (valid) {
+        const unsigned r = atomicAdd(&m.ctr->ngroups, 1u);
+        m.rays[r] = make_float4(pw[0], pw[1], pw[2], w);
+      }
+      continue;
+    }
+    // warp pre-aggregation of points that share a voxel (neighbouring pixels usually do)
+    const unsigned peers = __match_any_sync(kFull, key);
+    const int leader = __ffs(peers) - 1;
+    sh_w[wid][lane] = wq;
+    for (int r = 0; r < 3; ++r) sh_o[r][wid][lane] = wq * o[r];
+    __syncwarp();
+    if (valid && lane == leader) {
+      unsigned long long sw = 0, so[3] = {0, 0, 0};
+      for (unsigned pm = peers; pm; pm &= pm - 1) {
+        const int src = __ffs(pm) - 1;
+        sw += sh_w[wid][src];
+        for (int r = 0; r < 3; ++r) so[r] += sh_o[r][wid][src];
+      }
+      uint32_t h = hash64(key) & m.gmask;
+      bool placed = false;
+      for (uint32_t probe = 0; probe <= m.gmask; ++probe) {
+        unsigned long long k = __ldcg(&m.gtab[h].key);
+        if (k == kEmptyKey) {
+          k = atomicCAS(&m.gtab[h].key, kEmptyKey, key);
+          if (k == kEmptyKey) {
+            const unsigned gi = atomicAdd(&m.ctr->ngroups, 1u);
+            m.glist[gi] = h;
+            placed = true;
+            break;
+          }
+        }
+        if (k == key) {
+          placed = true;
+          break;
+        }
+        h = (h + 1) & m.gmask;
+      }
+      if (placed) {
+        GroupEntry* e = &m.gtab[h];
+        atomicAdd(&e->n, (unsigned)__popc(peers));
+        atomicAdd(&e->sw, sw);
+        for (int r = 0; r < 3; ++r) {
+          const unsigned long long old = atomicAdd(&e->swo_lo[r], so[r]);
+          if (old + so[r] < old) atomicAdd(&e->swo_hi[r], 1u);
+        }
+      } else {
+        atomicOr(&m.ctr->error, kErrGroupTable);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------------------------- A2 + A3
+__global__ void __launch_bounds__(kThreads) k_group_rays(DevMap m, Pose T) {
+  const unsigned ng = __ldcg(&m.ctr->ngroups);
+  const float s[3] = {T.T[3], T.T[7], T.T[11]};
+  for (unsigned gi = blockIdx.x * blockDim.x + threadIdx.x; gi < ng; gi += gridDim.x * blockDim.x) {
+    float pbar[3];
+    float Wg;
+    if (m.grouped) {
+      const uint32_t h = m.glist[gi];
+      GroupEntry e = m.gtab[h];
+      GroupEntry z;  // reset the entry for the next scan
+      z.key = kEmptyKey;
+      z.sw = 0;
+      z.swo_lo[0] = z.swo_lo[1] = z.swo_lo[2] = 0;
+      z.swo_hi[0] = z.swo_hi[1] = z.swo_hi[2] = 0;
+      z.n = 0;
+      m.gtab[h] = z;
+      const int3 k = unpack_key(e.key);
+      const int kk[3] = {k.x, k.y, k.z};
+      const unsigned long long half = e.sw >> 1;
+      for (int a = 0; a < 3; ++a) {
+        const unsigned long long lo = e.swo_lo[a] + half;
+        const unsigned long long hi = (unsigned long long)e.swo_hi[a] + (lo < half ? 1ull : 0ull);
+        const unsigned mo = div128_small(lo, hi, e.sw);
+        pbar[a] = __fmul_rn(__fadd_rn((float)kk[a], __fmul_rn((float)mo, 1.0f / 65536.0f)), m.v);
+      }
+      Wg = m.weighting == 0 ? __uint2float_rn(e.n) : __fmul_rn(__ull2float_rn(e.sw), 1.0f / 1048576.0f);
+      m.rays[gi] = make_float4(pbar[0], pbar[1], pbar[2], Wg);
+    } else {
+      const float4 r = m.rays[gi];
+      pbar[0] = r.x;
+      pbar[1] = r.y;
+      pbar[2] = r.z;
+    }
+    RayGeom g;
+    if (!ray_setup(pbar, s, m.v, m.delta, &g)) continue;
+    // block-level traversal: cells of 65536*B fixed-point units; same crossing order as the
+    // voxel traversal, so it visits exactly the blocks of the traversed voxels
+    Dda dda;
+    dda.init(g.S, g.E, 16 + m.blog);
+    block_insert(m, dda.c[0], dda.c[1], dda.c[2]);
+    for (int left = dda.steps(); left > 0; --left) {
+      dda.step();
+      block_insert(m, dda.c[0], dda.c[1], dda.c[2]);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------ A3
+__global__ void __launch_bounds__(kThreads) k_link_blocks(DevMap m) {
+  const unsigned nn = __ldcg(&m.ctr->nnew);
+  // one thread per (new block, direction)
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < nn * 27u; t += gridDim.x * blockDim.x) {
+    const uint32_t p = m.newblk[t / 27u];
+    if (p >= m.cap_blocks) continue;
+    const int k = (int)(t % 27u);
+    if (k == 13) {
+      m.nbr[(size_t)p * 27 + 13] = p;
+      continue;
+    }
+    const int3 b = m.bcoord[p];
+    const uint32_t q = block_lookup(m, b.x + k / 9 - 1, b.y + (k / 3) % 3 - 1, b.z + k % 3 - 1);
+    m.nbr[(size_t)p * 27 + k] = q;
+    if (q != kInvalid) m.nbr[(size_t)q * 27 + (26 - k)] = p;
+  }
+}
+
+// ------------------------------------------------------------------------------------ A4
+__device__ __forceinline__ void accumulate(const DevMap& m, uint32_t vid, unsigned long long qw, unsigned long long qwd) {
+  const unsigned long long old = atomicAdd(&m.acc[2 * (size_t)vid], qw);
+  atomicAdd(&m.acc[2 * (size_t)vid + 1], qwd);
+  if (old == 0ull) {
+    const unsigned i = atomicAdd(&m.ctr->nupdated, 1u);
+    m.updated[i] = vid;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_integrate_rays(DevMap m, Pose T) {
+  __shared__ unsigned long long sh_w[kWarps][32];
+  __shared__ unsigned long long sh_wd[kWarps][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const unsigned nr = __ldcg(&m.ctr->ngroups);
+  const float s[3] = {T.T[3], T.T[7], T.T[11]};
+  const int B = m.B, blog = m.blog;
+  const unsigned warps_total = gridDim.x * kWarps;
+  unsigned long long nrec = 0;
+  for (unsigned base = (blockIdx.x * kWarps + wid) * 32u; base < nr; base += warps_total * 32u) {
+    const unsigned gi = base + lane;
+    bool active = gi < nr;
+    RayGeom g;
+    float Wg = 0.0f;
+    Dda dda;
+    int left = 0;
+    int bc[3] = {0, 0, 0};
+    uint32_t slot = kInvalid;
+    if (active) {
+      const float4 r = m.rays[gi];
+      const float pbar[3] = {r.x, r.y, r.z};
+      Wg = r.w;
+      active = ray_setup(pbar, s, m.v, m.delta, &g);
+      if (active) {
+        dda.init(g.S, g.E, 16);
+        left = dda.steps();
+        for (int a = 0; a < 3; ++a) bc[a] = dda.c[a] >> blog;
+        slot = block_lookup(m, bc[0], bc[1], bc[2]);
+      }
+    }
+    while (__any_sync(kFull, active)) {
+      uint32_t vid = kInvalid;
+      unsigned long long qw = 0, qwd = 0;
+      if (active) {
+        // Eq. (1) at the voxel centre, truncated to [-delta, delta]
+        float dx[3];
+        for (int a = 0; a < 3; ++a) {
+          const float xc = __fmul_rn(__fadd_rn((float)dda.c[a], 0.5f), m.v);
+          dx[a] = __fsub_rn(g.p[a], xc);
+        }
+        const float dist = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(dx[0], dx[0]), __fmul_rn(dx[1], dx[1])), __fmul_rn(dx[2], dx[2])));
+        const float dot = __fadd_rn(__fadd_rn(__fmul_rn(dx[0], g.g[0]), __fmul_rn(dx[1], g.g[1])), __fmul_rn(dx[2], g.g[2]));
+        float d = dot >= 0.0f ? dist : -dist;
+        if (d > m.delta) d = m.delta;
+        if (d < -m.delta) d = -m.delta;
+        // Eq. (2) / Eq. (4); the 1/z^2 factor is already in the group weight
+        float w = Wg;
+        if (m.weighting == 1) {
+          if (d <= -m.delta)
+            w = 0.0f;
+          else if (d < -m.eps)
+            w = __fmul_rn(Wg, __fdiv_rn(__fadd_rn(d, m.delta), __fsub_rn(m.delta, m.eps)));
+        }
+        if (w > 0.0f && slot != kInvalid) {
+          const uint32_t l = (uint32_t)((((dda.c[2] & (B - 1)) << blog | (dda.c[1] & (B - 1))) << blog) | (dda.c[0] & (B - 1)));
+          vid = (slot << m.b3log) | l;
+          long long a = __float2ll_rn(__fmul_rn(w, kAccScale));
+          qw = (unsigned long long)(a < 1 ? 1 : a);
+          qwd = (unsigned long long)__float2ll_rn(__fmul_rn(__fmul_rn(w, d), kAccScale));
+          ++nrec;
+        }
+        if (left == 0) {
+          active = false;
+        } else {
+          const int ax = dda.step();
+          --left;
+          const int nb = dda.c[ax] >> blog;
+          if (nb != bc[ax]) {
+            bc[ax] = nb;
+            if (slot != kInvalid) {
+              const int k = ax == 0 ? (dda.st[0] + 1) * 9 + 4 : (ax == 1 ? 9 + (dda.st[1] + 1) * 3 + 1 : 13 + dda.st[2]);
+              slot = __ldg(&m.nbr[(size_t)slot * 27 + k]);
+            } else {
+              slot = block_lookup(m, bc[0], bc[1], bc[2]);
+            }
+          }
+        }
+      }
+      const unsigned peers = __match_any_sync(kFull, vid);
+      const bool alone = (peers == (1u << lane)) || vid == kInvalid;
+      if (__all_sync(kFull, alone)) {
+        if (vid != kInvalid) accumulate(m, vid, qw, qwd);
+      } else {
+        sh_w[wid][lane] = qw;
+        sh_wd[wid][lane] = qwd;
+        __syncwarp();
+        if (vid != kInvalid && lane == __ffs(peers) - 1) {
+          unsigned long long sw = 0, swd = 0;
+          for (unsigned pm = peers; pm; pm &= pm - 1) {
+            const int src = __ffs(pm) - 1;
+            sw += sh_w[wid][src];
+            swd += sh_wd[wid][src];
+          }
+          accumulate(m, vid, sw, swd);
+        }
+        __syncwarp();
+      }
+    }
+  }
+  if (nrec) atomicAdd(&m.ctr->nrecords, nrec);
+}
+
+// ------------------------------------------------------------------------------------ A5
+__global__ void __launch_bounds__(kThreads) k_apply(DevMap m) {
+  const unsigned nu = __ldcg(&m.ctr->nupdated);
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < nu; i += gridDim.x * blockDim.x) {
+    const uint32_t vid = m.updated[i];
+    const long long sw = (long long)m.acc[2 * (size_t)vid];
+    const long long swd = (long long)m.acc[2 * (size_t)vid + 1];
+    m.acc[2 * (size_t)vid] = 0ull;
+    m.acc[2 * (size_t)vid + 1] = 0ull;
+    const float Sw = __fmul_rn(__ll2float_rn(sw), kAccInvScale);
+    const float Swd = __fmul_rn(__ll2float_rn(swd), kAccInvScale);
+    const float2 t = m.tsdf[vid];
+    // Eq. (3): D <- (W D + sum w d) / (W + sum w), W <- min(W + sum w, W_max)
+    const float Wn = __fadd_rn(t.y, Sw);
+    const float D = __fdiv_rn(__fadd_rn(__fmul_rn(t.y, t.x), Swd), Wn);
+    m.tsdf[vid] = make_float2(D, fminf(Wn, m.wmax));
+    if (!(m.vflags[vid] & kQueuedForEsdf)) {
+      m.vflags[vid] |= kQueuedForEsdf;
+      const unsigned j = atomicAdd(&m.ctr->ndirty, 1u);
+      m.dirty[j] = vid;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------ import (restore)
+__global__ void __launch_bounds__(kThreads) k_import_alloc(DevMap m, const int* __restrict__ vox, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    block_insert(m, vox[3 * i] >> m.blog, vox[3 * i + 1] >> m.blog, vox[3 * i + 2] >> m.blog);
+}
+
+__global__ void __launch_bounds__(kThreads) k_import_set(DevMap m, const int* __restrict__ vox, const float* __restrict__ D,
+                                                        const float* __restrict__ W, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int x = vox[3 * i], y = vox[3 * i + 1], z = vox[3 * i + 2];
+    const uint32_t slot = block_lookup(m, x >> m.blog, y >> m.blog, z >> m.blog);
+    if (slot == kInvalid) continue;
+    const int B = m.B;
+    const uint32_t vid = (slot << m.b3log) | (uint32_t)((((z & (B - 1)) << m.blog | (y & (B - 1))) << m.blog) | (x & (B - 1)));
+    m.tsdf[vid] = make_float2(D[i], W[i]);
+    const unsigned u = atomicAdd(&m.ctr->nupdated, 1u);
+    m.updated[u] = vid;
+    if (!(m.vflags[vid] & kQueuedForEsdf)) {
+      m.vflags[vid] |= kQueuedForEsdf;
+      const unsigned j = atomicAdd(&m.ctr->ndirty, 1u);
+      m.dirty[j] = vid;
+    }
+  }
+}
+
+int grid_for(long long items, int num_sms, int per_sm) {
+  long long g = (items + kThreads - 1) / kThreads;
+  const long long cap = (long long)num_sms * per_sm;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+
+cudaError_t launch_init_groups(GroupEntry* tab, uint32_t entries, cudaStream_t s, LaunchHook* hook) {
+  hook->begin(kKInitGroups, s);
+  k_init_groups<<<(entries + kThreads - 1) / kThreads > 65535 ? 65535 : (entries + kThreads - 1) / kThreads, kThreads, 0, s>>>(tab, entries);
+  hook->end(kKInitGroups, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_integrate(const DevMap& m, const float* pts, int n, const Pose& T, const LaunchCfg& cfg,
+                             LaunchHook* hook) {
+  const cudaStream_t s = cfg.stream;
+  const int gpts = grid_for(n, cfg.num_sms, 16);
+  hook->begin(kKBin, s);
+  k_bin_points<<<gpts, kThreads, 0, s>>>(m, pts, n, T);
+  hook->end(kKBin, s);
+  hook->begin(kKGroupRays, s);
+  k_group_rays<<<gpts, kThreads, 0, s>>>(m, T);
+  hook->end(kKGroupRays, s);
+  hook->begin(kKLink, s);
+  k_link_blocks<<<cfg.num_sms * 4, kThreads, 0, s>>>(m);
+  hook->end(kKLink, s);
+  hook->begin(kKIntegrateRays, s);
+  k_integrate_rays<<<gpts, kThreads, 0, s>>>(m, T);
+  hook->end(kKIntegrateRays, s);
+  hook->begin(kKApply, s);
+  k_apply<<<cfg.num_sms * 8, kThreads, 0, s>>>(m);
+  hook->end(kKApply, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_import(const DevMap& m, const int* vox, const float* D, const float* W, int n,
+                          const LaunchCfg& cfg, LaunchHook* hook) {
+  const cudaStream_t s = cfg.stream;
+  const int g = grid_for(n, cfg.num_sms, 16);
+  hook->begin(kKImportAlloc, s);
+  k_import_alloc<<<g, kThreads, 0, s>>>(m, vox, n);
+  hook->end(kKImportAlloc, s);
+  hook->begin(kKLink, s);
+  k_link_blocks<<<cfg.num_sms * 4, kThreads, 0, s>>>(m);
+  hook->end(kKLink, s);
+  hook->begin(kKImportSet, s);
+  k_import_set<<<g, kThreads, 0, s>>>(m, vox, D, W, n);
+  hook->end(kKImportSet, s);
+  return cudaGetLastError();
+}
+
+}  // namespace vbx

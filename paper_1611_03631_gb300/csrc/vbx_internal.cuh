@@ -1,0 +1,330 @@
+// vbx_internal.cuh -- device-side layout and helpers of the GB300 map update.
+//
+// HBM layout of one map (all arrays indexed by pool slot or by voxel id):
+//   block hash     : hkeys[H] u64 packed block key (EMPTY = ~0), hvals[H] u32 pool slot
+//   per block      : bcoord[slot] int3, nbr[slot*27 + k] u32 slot of the neighbour block in
+//                    direction k = (dx+1)*9 + (dy+1)*3 + (dz+1) (k = 13 is the block itself)
+//   per voxel      : voxel id vid = slot * B^3 + ((lz*B + ly)*B + lx)
+//                    tsdf[vid]   float2 (D, W)                          8 B
+//                    acc[2*vid]  u64 fixed-point sum of w, sum of w*d    16 B (zero between scans)
+//                    esdf[vid]   u64 packed {d f32 | flags u8 | parent u8} 8 B
+//                    vflags[vid] u8 (bit0 queued for the ESDF)
+//                    stamp_r/stamp_l[vid] u32 frontier de-duplication epochs
+//   lists          : updated (last scan), dirty (since last ESDF), 2+2 frontier buffers
+//   per-scan scratch: group hash table (64 B entries), group list, rays (float4)
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace vbx {
+
+constexpr unsigned long long kEmptyKey = ~0ull;
+constexpr uint32_t kInvalid = 0xffffffffu;
+constexpr int kSub = 65536;  // fixed-point units per voxel for ray endpoints and offsets
+constexpr float kAccScale = 268435456.0f;        // 2^28: fixed point of the per-voxel sums
+constexpr float kAccInvScale = 1.0f / 268435456.0f;
+
+// sticky device error bits
+constexpr unsigned kErrPoolFull = 1u;
+constexpr unsigned kErrHashFull = 2u;
+constexpr unsigned kErrTimeout = 4u;
+constexpr unsigned kErrGroupTable = 8u;
+
+// ESDF voxel word: bits 63..32 float d, bits 15..8 flags, bits 7..0 parent direction
+constexpr unsigned kObserved = 1u;
+constexpr unsigned kFixed = 2u;
+constexpr unsigned kNoParent = 255u;
+constexpr uint8_t kQueuedForEsdf = 1u;
+
+struct __align__(16) GroupEntry {
+  unsigned long long key;       // packed voxel key, kEmptyKey when free
+  unsigned long long sw;        // sum of integer point weights
+  unsigned long long swo_lo[3]; // sum of weight * sub-voxel offset, low 64 bits per axis
+  unsigned int swo_hi[3];       // carries into bit 64 and up
+  unsigned int n;               // number of points
+};
+static_assert(sizeof(GroupEntry) == 64, "group entry is one 64-byte sector pair");
+
+struct GridBarrier {
+  unsigned int count;
+  unsigned int gen;
+};
+
+// Per-scan counters are contiguous so that one memset clears them.
+struct Counters {
+  // ---- per scan (cleared by vbx_integrate_scan)
+  unsigned int ngroups;
+  unsigned int nnew;
+  unsigned int nupdated;
+  unsigned int npoints_valid;
+  unsigned long long nrecords;
+  // ---- persistent
+  unsigned int blocks;
+  unsigned int error;
+  unsigned int ndirty;
+  unsigned int epoch;
+  // ---- per ESDF update (cleared by vbx_update_esdf)
+  unsigned int rc[3];
+  unsigned int lc[3];
+  unsigned int raise_rounds;
+  unsigned int lower_rounds;
+  unsigned long long raise_pops;
+  unsigned long long lower_pops;
+  unsigned int seeds;
+  unsigned int esdf_in;
+  GridBarrier bar;
+};
+
+struct DevMap {
+  // parameters (float32, as the map holds them)
+  float v, delta, eps, gamma, wmax, dmax;
+  float max_range2;  // <= 0: no range limit
+  float range_lim2;  // (16384 v)^2: points farther than 2^14 voxels are dropped
+  float L1, L2, L3;  // quasi-Euclidean step lengths v, v*sqrt(2), v*sqrt(3)
+  int B, blog, b3log;
+  int weighting, grouped;
+  // block hash
+  unsigned long long* hkeys;
+  uint32_t* hvals;
+  uint32_t hmask;
+  // pool
+  uint32_t cap_blocks;
+  int3* bcoord;
+  uint32_t* nbr;
+  float2* tsdf;
+  unsigned long long* acc;
+  unsigned long long* esdf;
+  uint8_t* vflags;
+  uint32_t* stamp_r;
+  uint32_t* stamp_l;
+  // lists
+  uint32_t* updated;
+  uint32_t* dirty;
+  uint32_t* newblk;
+  uint32_t* rfront0;
+  uint32_t* rfront1;
+  uint32_t* lfront0;
+  uint32_t* lfront1;
+  // per-scan scratch
+  GroupEntry* gtab;
+  uint32_t gmask;
+  uint32_t* glist;
+  float4* rays;
+  Counters* ctr;
+};
+
+// ---------------------------------------------------------------------------------------
+// keys and hashing
+
+__device__ __forceinline__ unsigned long long pack_key(int x, int y, int z) {
+  return ((unsigned long long)(uint32_t)(x + (1 << 20)) << 42) | ((unsigned long long)(uint32_t)(y + (1 << 20)) << 21) |
+         (unsigned long long)(uint32_t)(z + (1 << 20));
+}
+
+__device__ __forceinline__ int3 unpack_key(unsigned long long k) {
+  return make_int3((int)((k >> 42) & 0x1fffff) - (1 << 20), (int)((k >> 21) & 0x1fffff) - (1 << 20),
+                   (int)(k & 0x1fffff) - (1 << 20));
+}
+
+__device__ __forceinline__ uint32_t hash64(unsigned long long k) {
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdull;
+  k ^= k >> 33;
+  k *= 0xc4ceb9fe1a85ec53ull;
+  k ^= k >> 33;
+  return (uint32_t)k;
+}
+
+__device__ __forceinline__ int floor_div_pow2(int a, int log2b) { return a >> log2b; }  // arithmetic shift = floor
+
+// Block hash lookup (no insertion); kInvalid when absent or not allocated.
+__device__ __forceinline__ uint32_t block_lookup(const DevMap& m, int bx, int by, int bz) {
+  const unsigned long long key = pack_key(bx, by, bz);
+  uint32_t h = hash64(key) & m.hmask;
+  for (uint32_t probe = 0; probe <= m.hmask; ++probe) {
+    const unsigned long long k = __ldcg(&m.hkeys[h]);
+    if (k == key) return __ldcg(&m.hvals[h]);
+    if (k == kEmptyKey) return kInvalid;
+    h = (h + 1) & m.hmask;
+  }
+  return kInvalid;
+}
+
+// Lock-free find-or-insert (Sec. III: O(1) hashed block insertion). The thread that claims an
+// empty slot with atomicCAS takes a pool slot and publishes it; others see the key and move on.
+// Slots are read only by later kernels, so nobody waits here.
+__device__ __forceinline__ void block_insert(const DevMap& m, int bx, int by, int bz) {
+  const unsigned long long key = pack_key(bx, by, bz);
+  uint32_t h = hash64(key) & m.hmask;
+  for (uint32_t probe = 0; probe <= m.hmask; ++probe) {
+    unsigned long long k = __ldcg(&m.hkeys[h]);
+    if (k == key) return;
+    if (k == kEmptyKey) {
+      k = atomicCAS(&m.hkeys[h], kEmptyKey, key);
+      if (k == kEmptyKey) {
+        const uint32_t slot = atomicAdd(&m.ctr->blocks, 1u);
+        if (slot >= m.cap_blocks) {
+          m.hvals[h] = kInvalid;
+          atomicOr(&m.ctr->error, kErrPoolFull);
+          return;
+        }
+        m.hvals[h] = slot;
+        m.bcoord[slot] = make_int3(bx, by, bz);
+        const uint32_t i = atomicAdd(&m.ctr->nnew, 1u);
+        m.newblk[i] = slot;
+        return;
+      }
+      if (k == key) return;
+    }
+    h = (h + 1) & m.hmask;
+  }
+  atomicOr(&m.ctr->error, kErrHashFull);
+}
+
+// ---------------------------------------------------------------------------------------
+// ESDF voxel word
+
+__device__ __forceinline__ unsigned long long ew_pack(float d, unsigned flags, unsigned parent) {
+  return ((unsigned long long)__float_as_uint(d) << 32) | ((unsigned long long)(flags & 0xffu) << 8) |
+         (unsigned long long)(parent & 0xffu);
+}
+__device__ __forceinline__ float ew_d(unsigned long long w) { return __uint_as_float((uint32_t)(w >> 32)); }
+__device__ __forceinline__ unsigned ew_flags(unsigned long long w) { return (unsigned)(w >> 8) & 0xffu; }
+__device__ __forceinline__ unsigned ew_parent(unsigned long long w) { return (unsigned)w & 0xffu; }
+
+// Voxel id of the 26-neighbour in direction k (kInvalid if its block does not exist).
+__device__ __forceinline__ uint32_t neighbor_vid(const DevMap& m, uint32_t vid, int k) {
+  const int B = m.B, blog = m.blog;
+  uint32_t slot = vid >> m.b3log;
+  const uint32_t l = vid & ((1u << m.b3log) - 1u);
+  int x = (int)(l & (B - 1)) + (k / 9 - 1);
+  int y = (int)((l >> blog) & (B - 1)) + ((k / 3) % 3 - 1);
+  int z = (int)(l >> (2 * blog)) + (k % 3 - 1);
+  const int bx = x < 0 ? -1 : (x >= B ? 1 : 0);
+  const int by = y < 0 ? -1 : (y >= B ? 1 : 0);
+  const int bz = z < 0 ? -1 : (z >= B ? 1 : 0);
+  if (bx | by | bz) {
+    slot = __ldg(&m.nbr[(size_t)slot * 27 + (bx + 1) * 9 + (by + 1) * 3 + (bz + 1)]);
+    if (slot == kInvalid) return kInvalid;
+    x -= bx * B;
+    y -= by * B;
+    z -= bz * B;
+  }
+  return (slot << m.b3log) | (uint32_t)((((z << blog) | y) << blog) | x);
+}
+
+// ---------------------------------------------------------------------------------------
+// Ray setup shared by the block and voxel traversals (identical float32 operations in both
+// kernels, no contraction): s -> e = pbar + delta * (pbar - s)/|pbar - s|, both quantised to
+// 1/65536 voxel.
+struct RayGeom {
+  float p[3];   // pbar
+  float g[3];   // pbar - s
+  long long S[3];
+  long long E[3];
+};
+
+__device__ __forceinline__ bool ray_setup(const float pbar[3], const float s[3], float v, float delta, RayGeom* r) {
+  for (int a = 0; a < 3; ++a) {
+    r->p[a] = pbar[a];
+    r->g[a] = __fsub_rn(pbar[a], s[a]);
+  }
+  const float n2 = __fadd_rn(__fadd_rn(__fmul_rn(r->g[0], r->g[0]), __fmul_rn(r->g[1], r->g[1])), __fmul_rn(r->g[2], r->g[2]));
+  const float len = __fsqrt_rn(n2);
+  if (!(len > 0.0f)) return false;
+  for (int a = 0; a < 3; ++a) {
+    const float u = __fdiv_rn(r->g[a], len);
+    const float e = __fadd_rn(pbar[a], __fmul_rn(delta, u));
+    r->S[a] = __float2ll_rn(__fmul_rn(__fdiv_rn(s[a], v), 65536.0f));
+    r->E[a] = __float2ll_rn(__fmul_rn(__fdiv_rn(e, v), 65536.0f));
+  }
+  return true;
+}
+
+// Incremental integer 3-D DDA over cells of size F fixed-point units (F = 65536 for voxels,
+// 65536*B for blocks). The next face crossing of axis a is at t_a = num_a / den_a; instead of
+// comparing the ratios at every step, the three pairwise cross differences
+// C_ab = num_a*den_b - num_b*den_a are kept and updated by additions when an axis steps.
+// Ties go to x, then y, then z.
+struct Dda {
+  int c[3];
+  int st[3];
+  int rem[3];
+  long long inc[3];  // F * den_a
+  long long cxy, cxz, cyz;
+
+  __device__ __forceinline__ void init(const long long S[3], const long long E[3], int log2F) {
+    long long num[3], den[3];
+    for (int a = 0; a < 3; ++a) {
+      c[a] = (int)(S[a] >> log2F);
+      const int ce = (int)(E[a] >> log2F);
+      st[a] = E[a] >= S[a] ? 1 : -1;
+      den[a] = E[a] >= S[a] ? E[a] - S[a] : S[a] - E[a];
+      rem[a] = ce >= c[a] ? ce - c[a] : c[a] - ce;
+      num[a] = st[a] > 0 ? (((long long)c[a] + 1) << log2F) - S[a] : S[a] - ((long long)c[a] << log2F);
+      inc[a] = den[a] << log2F;
+    }
+    cxy = num[0] * den[1] - num[1] * den[0];
+    cxz = num[0] * den[2] - num[2] * den[0];
+    cyz = num[1] * den[2] - num[2] * den[1];
+  }
+  __device__ __forceinline__ int steps() const { return rem[0] + rem[1] + rem[2]; }
+  // Advances one cell; returns the axis stepped.
+  __device__ __forceinline__ int step() {
+    const bool vx = rem[0] > 0, vy = rem[1] > 0, vz = rem[2] > 0;
+    int a;
+    if (vx && (!vy || cxy <= 0) && (!vz || cxz <= 0)) {
+      a = 0;
+      cxy += inc[1];
+      cxz += inc[2];
+    } else if (vy && (!vz || cyz <= 0)) {
+      a = 1;
+      cxy -= inc[0];
+      cyz += inc[2];
+    } else {
+      a = 2;
+      cxz -= inc[0];
+      cyz -= inc[1];
+    }
+    c[a] += st[a];
+    rem[a] -= 1;
+    return a;
+  }
+};
+
+// ---------------------------------------------------------------------------------------
+// grid-wide barrier for cooperative launches, with a bounded wait
+
+__device__ __forceinline__ bool grid_barrier(GridBarrier* bar, unsigned int nblocks, unsigned* err) {
+  __shared__ int ok_sh;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned int* genp = &bar->gen;
+    const unsigned int g = *genp;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(&bar->count, 1u);
+    if (arrived == nblocks - 1) {
+      atomicExch(&bar->count, 0u);
+      __threadfence();
+      atomicAdd(&bar->gen, 1u);
+    } else {
+      long long spins = 0;
+      while (*genp == g) {
+        if (++spins > (1ll << 25)) {
+          atomicOr(err, kErrTimeout);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    ok_sh = ok;
+  }
+  __syncthreads();
+  return ok_sh != 0;
+}
+
+}  // namespace vbx

@@ -1,0 +1,307 @@
+"""Thin Python binding of the C ABI in ``include/vbx.h`` (argument marshalling only).
+
+Every step of the map update runs in the CUDA library ``_build/libvbx.so``; this module
+only converts arguments (torch device tensors for device memory, numpy arrays for host
+data) and checks statuses. There is no CPU fallback: without the library or a CUDA device
+every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from typing import Dict, Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libvbx.so")
+
+VBX_OK = 0
+STATUS_NAMES = {
+    0: "VBX_OK",
+    1: "VBX_ERR_INVALID_ARG",
+    2: "VBX_ERR_OUT_OF_MEMORY",
+    3: "VBX_ERR_HASH_FULL",
+    4: "VBX_ERR_TIMEOUT",
+    5: "VBX_ERR_CUDA",
+}
+
+
+class VbxError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class vbx_map_options(ctypes.Structure):
+    _fields_ = [
+        ("weighting", ctypes.c_int),
+        ("eps", ctypes.c_float),
+        ("fixed_band", ctypes.c_float),
+        ("w_max", ctypes.c_float),
+        ("max_range", ctypes.c_float),
+        ("grouped", ctypes.c_int),
+        ("block_capacity", ctypes.c_int64),
+        ("max_points", ctypes.c_int64),
+    ]
+
+
+class vbx_stats(ctypes.Structure):
+    _fields_ = [
+        (n, ctypes.c_int64)
+        for n in (
+            "points_in",
+            "points_valid",
+            "rays",
+            "records",
+            "updated",
+            "new_blocks",
+            "blocks",
+            "esdf_in",
+            "seeds",
+            "raise_pops",
+            "lower_pops",
+            "raise_rounds",
+            "lower_rounds",
+            "launches",
+        )
+    ]
+
+
+_lib = None
+
+# exported symbols and their (restype, argtypes)
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_SIGS = {
+    "vbx_default_options": (ctypes.c_int, [ctypes.POINTER(vbx_map_options)]),
+    "vbx_create_map": (
+        ctypes.c_int,
+        [ctypes.c_float, ctypes.c_int, ctypes.c_float, ctypes.c_float, ctypes.POINTER(vbx_map_options), ctypes.POINTER(_vp)],
+    ),
+    "vbx_destroy_map": (ctypes.c_int, [_vp]),
+    "vbx_integrate_scan": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp]),
+    "vbx_update_esdf": (ctypes.c_int, [_vp, _vp]),
+    "vbx_query_distance_gradient": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, _vp, _vp]),
+    "vbx_sync": (ctypes.c_int, [_vp, _vp]),
+    "vbx_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(vbx_stats), _vp]),
+    "vbx_num_blocks": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), _vp]),
+    "vbx_export_blocks": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _i64, _vp]),
+    "vbx_export_updated": (ctypes.c_int, [_vp, _vp, _i64, ctypes.POINTER(_i64), _vp]),
+    "vbx_import_tsdf": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, _vp]),
+    "vbx_set_profiling": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "vbx_get_kernel_times": (
+        ctypes.c_int,
+        [_vp, ctypes.POINTER(ctypes.c_char_p), _vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _vp],
+    ),
+    "vbx_reset_kernel_times": (ctypes.c_int, [_vp]),
+    "vbx_total_launches": (_i64, []),
+    "vbx_last_error": (ctypes.c_char_p, []),
+}
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads libvbx.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(st: int):
+    if st != VBX_OK:
+        raise VbxError(st, _lib.vbx_last_error().decode())
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _dev_f32(t, cols: Optional[int] = None):
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA torch tensor")
+    if t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError("expected a contiguous float32 tensor")
+    if cols is not None and (t.dim() != 2 or t.shape[1] != cols):
+        raise ValueError(f"expected shape (N, {cols})")
+    return t
+
+
+def total_launches() -> int:
+    return int(load_library().vbx_total_launches())
+
+
+class Map:
+    """A TSDF + ESDF map on the current CUDA device (see include/vbx.h)."""
+
+    def __init__(
+        self,
+        voxel_size: float,
+        voxels_per_block: int,
+        truncation: float,
+        max_esdf_dist: float,
+        weighting: int = 0,
+        eps: Optional[float] = None,
+        fixed_band: Optional[float] = None,
+        w_max: float = 1e4,
+        max_range: float = math.inf,
+        grouped: bool = True,
+        block_capacity: int = 0,
+        max_points: int = 0,
+    ):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("vbx.Map needs a CUDA device")
+        self._lib = load_library()
+        o = vbx_map_options()
+        _check(self._lib.vbx_default_options(ctypes.byref(o)))
+        o.weighting = int(weighting)
+        o.eps = 0.0 if eps is None else float(eps)
+        o.fixed_band = 0.0 if fixed_band is None else float(fixed_band)
+        o.w_max = float(w_max)
+        o.max_range = float(max_range) if math.isfinite(max_range) else 0.0
+        o.grouped = 1 if grouped else 0
+        o.block_capacity = int(block_capacity)
+        o.max_points = int(max_points)
+        h = ctypes.c_void_p()
+        _check(self._lib.vbx_create_map(voxel_size, voxels_per_block, truncation, max_esdf_dist, ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        self.B = int(voxels_per_block)
+        self.voxel_size = float(voxel_size)
+
+    @classmethod
+    def from_scene_params(cls, params: Dict[str, float], **kw) -> "Map":
+        args = dict(
+            weighting=int(params.get("weighting", 0)),
+            eps=params.get("eps"),
+            fixed_band=params.get("fixed_band"),
+            max_range=params.get("max_range", math.inf),
+        )
+        args.update(kw)
+        return cls(params["voxel_size"], params["voxels_per_block"], params["truncation"], params["max_esdf_dist"], **args)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.vbx_destroy_map(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    # -------------------------------------------------------------------- hot path
+    def integrate_scan(self, points, T_world_sensor, stream=None) -> None:
+        p = _dev_f32(points, 3)
+        T = np.ascontiguousarray(np.asarray(T_world_sensor, dtype=np.float32).reshape(16))
+        _check(self._lib.vbx_integrate_scan(self._h, p.data_ptr(), p.shape[0], T.ctypes.data, _stream_ptr(stream)))
+
+    def update_esdf(self, stream=None) -> None:
+        _check(self._lib.vbx_update_esdf(self._h, _stream_ptr(stream)))
+
+    def query(self, q, out=None, stream=None):
+        import torch
+
+        q = _dev_f32(q, 3)
+        n = q.shape[0]
+        if out is None:
+            dist = torch.empty(n, dtype=torch.float32, device=q.device)
+            grad = torch.empty((n, 3), dtype=torch.float32, device=q.device)
+            status = torch.empty(n, dtype=torch.uint8, device=q.device)
+        else:
+            dist, grad, status = out
+        _check(
+            self._lib.vbx_query_distance_gradient(
+                self._h, q.data_ptr(), n, dist.data_ptr(), grad.data_ptr(), status.data_ptr(), _stream_ptr(stream)
+            )
+        )
+        return dist, grad, status
+
+    # ------------------------------------------------------------------ inspection
+    def sync(self, stream=None) -> None:
+        _check(self._lib.vbx_sync(self._h, _stream_ptr(stream)))
+
+    def stats(self, stream=None) -> Dict[str, int]:
+        s = vbx_stats()
+        _check(self._lib.vbx_get_stats(self._h, ctypes.byref(s), _stream_ptr(stream)))
+        return {f: int(getattr(s, f)) for f, _ in vbx_stats._fields_}
+
+    def num_blocks(self, stream=None) -> int:
+        n = ctypes.c_int64()
+        _check(self._lib.vbx_num_blocks(self._h, ctypes.byref(n), _stream_ptr(stream)))
+        return int(n.value)
+
+    def export(self, sort: bool = True, stream=None) -> Dict[str, np.ndarray]:
+        """Map contents on the host; blocks sorted by key (x, y, z) when sort=True."""
+        nb = self.num_blocks(stream)
+        B3 = self.B ** 3
+        keys = np.zeros((max(nb, 1), 3), np.int32)
+        tsdf = np.zeros((max(nb, 1), B3, 2), np.float32)
+        d = np.zeros((max(nb, 1), B3), np.float32)
+        parent = np.zeros((max(nb, 1), B3), np.uint8)
+        flags = np.zeros((max(nb, 1), B3), np.uint8)
+        _check(
+            self._lib.vbx_export_blocks(
+                self._h, keys.ctypes.data, tsdf.ctypes.data, d.ctypes.data, parent.ctypes.data, flags.ctypes.data, max(nb, 1), _stream_ptr(stream)
+            )
+        )
+        keys, tsdf, d, parent, flags = keys[:nb], tsdf[:nb], d[:nb], parent[:nb], flags[:nb]
+        if sort and nb:
+            order = np.lexsort((keys[:, 2], keys[:, 1], keys[:, 0]))
+            keys, tsdf, d, parent, flags = keys[order], tsdf[order], d[order], parent[order], flags[order]
+        return dict(keys=keys, D=tsdf[..., 0], W=tsdf[..., 1], d=d, parent=parent, flags=flags)
+
+    def last_updated(self, stream=None) -> np.ndarray:
+        n = ctypes.c_int64()
+        _check(self._lib.vbx_export_updated(self._h, None, 0, ctypes.byref(n), _stream_ptr(stream)))
+        out = np.zeros((max(int(n.value), 1), 3), np.int32)
+        _check(self._lib.vbx_export_updated(self._h, out.ctypes.data, out.shape[0], ctypes.byref(n), _stream_ptr(stream)))
+        return out[: int(n.value)]
+
+    def import_tsdf(self, vox: np.ndarray, D: np.ndarray, W: np.ndarray, stream=None) -> None:
+        vox = np.ascontiguousarray(vox, dtype=np.int32).reshape(-1, 3)
+        D = np.ascontiguousarray(D, dtype=np.float32).reshape(-1)
+        W = np.ascontiguousarray(W, dtype=np.float32).reshape(-1)
+        if not (len(vox) == len(D) == len(W)):
+            raise ValueError("vox, D and W must have the same length")
+        _check(self._lib.vbx_import_tsdf(self._h, vox.ctypes.data, D.ctypes.data, W.ctypes.data, len(D), _stream_ptr(stream)))
+
+    # -------------------------------------------------------------------- profiling
+    def set_profiling(self, enable: bool) -> None:
+        _check(self._lib.vbx_set_profiling(self._h, 1 if enable else 0))
+
+    def kernel_times(self, stream=None) -> Dict[str, Dict[str, float]]:
+        cap = 32
+        names = (ctypes.c_char_p * cap)()
+        ms = np.zeros(cap, np.float64)
+        cnt = np.zeros(cap, np.int64)
+        n = ctypes.c_int()
+        _check(self._lib.vbx_get_kernel_times(self._h, names, ms.ctypes.data, cnt.ctypes.data, cap, ctypes.byref(n), _stream_ptr(stream)))
+        return {names[i].decode(): dict(ms=float(ms[i]), launches=int(cnt[i])) for i in range(min(n.value, cap))}
+
+    def reset_kernel_times(self) -> None:
+        _check(self._lib.vbx_reset_kernel_times(self._h))

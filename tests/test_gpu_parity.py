@@ -1,0 +1,266 @@
+"""GPU parity of the CUDA map update against the CPU oracle, through the C ABI.
+
+Bar: allocated-block, updated-voxel, observed and seed sets bit-exact; |dD| <= 1e-5 m,
+relative dW <= 1e-6, |d ESDF| <= 1e-4 m (bit-exact when both sides start from the same
+float32 TSDF values)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1611_03631_gb300 import scenes
+from parity_util import TOL_D, TOL_ESDF, TOL_W_REL, check_parents, compare_tsdf, sort_rows, voxel_coords
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def vbx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1611_03631_gb300 import vbx as v
+
+    v.load_library()
+    return v
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+
+
+def _run_tsdf(vbx, s, frames, check_each=True, **kw):
+    g = vbx.Map.from_scene_params(s.params, **kw)
+    o = oracle.OracleMap.from_scene_params(s.params, **{k: v for k, v in kw.items() if k in ("grouped",)})
+    worst = dict(max_dD=0.0, max_rel_dW=0.0)
+    for i in range(frames):
+        g.integrate_scan(_dev(s.points[i]), s.poses[i])
+        o.integrate(s.points[i], s.poses[i])
+        if check_each or i == frames - 1:
+            gu = sort_rows(g.last_updated())
+            ou = o.last_updated()
+            assert np.array_equal(gu, ou), f"frame {i}: updated voxel sets differ ({len(gu)} vs {len(ou)})"
+            gs, os_ = g.stats(), o.stats()
+            assert gs["points_valid"] == os_["points_valid"]
+            assert gs["rays"] == os_["groups"]
+            assert gs["records"] == os_["records"]
+            assert gs["new_blocks"] == os_["new_blocks"]
+            r = compare_tsdf(g.export(), o.export(), s.params["voxels_per_block"])
+            worst["max_dD"] = max(worst["max_dD"], r["max_dD"])
+            worst["max_rel_dW"] = max(worst["max_rel_dW"], r["max_rel_dW"])
+            assert r["max_dD"] <= TOL_D, (i, r)
+            assert r["max_rel_dW"] <= TOL_W_REL, (i, r)
+    return g, o, worst
+
+
+# ------------------------------------------------------------------------------ TSDF
+
+
+def test_tsdf_parity_plane_sphere_all_frames(vbx):
+    s = scenes.plane_sphere()
+    g, o, worst = _run_tsdf(vbx, s, len(s))
+    print("plane_sphere TSDF max |dD| %.3g m, max rel dW %.3g" % (worst["max_dD"], worst["max_rel_dW"]))
+
+
+def test_tsdf_parity_room_quadratic_weight(vbx):
+    # room scene at reduced resolution (several tiles, ragged tail: 160*120 = 19200 points)
+    s = scenes.room(frames=4, width=160, height=120, fx=131.25, fy=131.25)
+    _run_tsdf(vbx, s, len(s))
+
+
+def test_tsdf_parity_lidar_constant_weight(vbx):
+    s = scenes.lidar_terrain(scans=2, beams=16, columns=512, n_buildings=60, n_trees=100)
+    _run_tsdf(vbx, s, len(s), block_capacity=1 << 17)
+
+
+def test_tsdf_parity_per_point_raycasting(vbx):
+    s = scenes.plane_sphere(frames=2, width=32, height=24, fx=25.0, fy=25.0, cx=16.0, cy=12.0)
+    _run_tsdf(vbx, s, len(s), grouped=False)
+
+
+def test_tsdf_parity_full_size_room_frames(vbx):
+    """Two full 640x480 frames of the room workload (the benchmark's configuration)."""
+    s = scenes.room(frames=2)
+    _run_tsdf(vbx, s, len(s), check_each=True)
+
+
+def test_integration_is_deterministic(vbx):
+    s = scenes.room(frames=2, width=160, height=120, fx=131.25, fy=131.25)
+    exports = []
+    for _ in range(2):
+        g = vbx.Map.from_scene_params(s.params)
+        for i in range(len(s)):
+            g.integrate_scan(_dev(s.points[i]), s.poses[i])
+        g.update_esdf()
+        exports.append(g.export())
+    for k in ("keys", "D", "W", "d", "flags"):
+        assert np.array_equal(exports[0][k], exports[1][k]), k
+
+
+# ------------------------------------------------------------------------------ ESDF
+
+
+def _esdf_same_input(vbx, s, frames):
+    """GPU and oracle (float32 ESDF mode) run the ESDF update on identical float32 TSDF
+    values taken from a reference oracle integration: ESDF values must agree bit-exactly."""
+    ref = oracle.OracleMap.from_scene_params(s.params)
+    o32 = oracle.OracleMap.from_scene_params(s.params, esdf_fp32=1)
+    g = vbx.Map.from_scene_params(s.params)
+    B = s.params["voxels_per_block"]
+    v = np.float32(s.params["voxel_size"])
+    L = (0.0, v, np.float32(v * np.float32(1.41421356237309515)), np.float32(v * np.float32(1.73205080756887719)))
+    for i in range(frames):
+        ref.integrate(s.points[i], s.poses[i])
+        ex = ref.export()
+        upd = ref.last_updated()
+        idx = {tuple(k): j for j, k in enumerate(ex["keys"])}
+        bj = np.array([idx[(x // B, y // B, z // B)] for x, y, z in upd])
+        loc = ((upd[:, 2] % B) * B + (upd[:, 1] % B)) * B + (upd[:, 0] % B)
+        D32 = ex["D"][bj, loc].astype(np.float32)
+        W32 = ex["W"][bj, loc].astype(np.float32)
+        o32.set_tsdf(upd, D32.astype(np.float64), W32.astype(np.float64))
+        g.import_tsdf(upd, D32, W32)
+        o32.update_esdf()
+        g.update_esdf()
+        gex, oex = g.export(), o32.export()
+        assert np.array_equal(gex["keys"], oex["keys"])
+        assert np.array_equal(gex["flags"], oex["flags"]), f"frame {i}: observed/fixed flags differ"
+        obs = (oex["flags"] & 1) > 0
+        assert np.array_equal(gex["d"][obs], oex["d"][obs].astype(np.float32)), f"frame {i}: ESDF values differ"
+        gs, os_ = g.stats(), o32.stats()
+        assert gs["seeds"] == os_["seeds"]
+        bad, checked = check_parents(gex, B, L)
+        assert bad == 0 and checked > 0
+    return g, o32
+
+
+def test_esdf_parity_same_tsdf_plane_sphere(vbx):
+    s = scenes.plane_sphere(frames=6)
+    _esdf_same_input(vbx, s, len(s))
+
+
+def test_esdf_parity_same_tsdf_room(vbx):
+    s = scenes.room(frames=3, width=160, height=120, fx=131.25, fy=131.25)
+    _esdf_same_input(vbx, s, len(s))
+
+
+def test_esdf_end_to_end_plane_sphere(vbx):
+    """GPU integrate + ESDF against the float64 oracle; seeds whose TSDF value sits within
+    1e-5 m of the band edge or of zero may legitimately differ (float32 vs float64
+    accumulation) and are excluded together with their d_max neighbourhood."""
+    s = scenes.plane_sphere()
+    p = s.params
+    g = vbx.Map.from_scene_params(p)
+    o = oracle.OracleMap.from_scene_params(p)
+    B = p["voxels_per_block"]
+    gamma = np.float32(p["fixed_band"])
+    worst = 0.0
+    for i in range(len(s)):
+        g.integrate_scan(_dev(s.points[i]), s.poses[i])
+        o.integrate(s.points[i], s.poses[i])
+        g.update_esdf()
+        o.update_esdf()
+        gex, oex = g.export(), o.export()
+        assert np.array_equal(gex["keys"], oex["keys"])
+        gobs, oobs = (gex["flags"] & 1) > 0, (oex["flags"] & 1) > 0
+        assert np.array_equal(gobs, oobs)
+        gfix, ofix = (gex["flags"] & 2) > 0, (oex["flags"] & 2) > 0
+        Do = oex["D"].astype(np.float32)
+        ambiguous = (np.abs(np.abs(Do) - gamma) < 1e-5) | (np.abs(Do) < 1e-5)
+        diff = (gfix != ofix) | (np.sign(gex["D"]) != np.sign(Do)) & oobs
+        assert not np.any(diff & ~ambiguous), f"frame {i}: seed sets differ outside the guard band"
+        mask = oobs.copy()
+        if np.any(diff):
+            vc = voxel_coords(gex["keys"], B)
+            bad = vc[diff]
+            r = int(math.ceil(p["max_esdf_dist"] / p["voxel_size"])) + 1
+            for c in bad:
+                near = np.max(np.abs(vc - c), axis=-1) <= r
+                mask &= ~near
+        err = np.abs(gex["d"][mask].astype(np.float64) - oex["d"][mask])
+        worst = max(worst, float(err.max()))
+        assert err.max() <= TOL_ESDF, (i, float(err.max()))
+    print("plane_sphere ESDF end-to-end max |dd| %.3g m" % worst)
+
+
+# ----------------------------------------------------------------------------- query
+
+
+def test_query_parity(vbx):
+    s = scenes.plane_sphere(frames=4)
+    g, o32 = _esdf_same_input(vbx, s, len(s))
+    q = scenes.random_queries(s, 4099, radius=3.0, seed=9)
+    q = np.concatenate([q, np.array([[0.05, 0.05, 0.05], [100.0, 0.0, 0.0]], np.float32)])
+    dist, grad, status = g.query(_dev(q))
+    dist, grad, status = dist.cpu().numpy(), grad.cpu().numpy(), status.cpu().numpy()
+    od, og, os_ = o32.query(q)
+    assert np.array_equal(status, os_), "query status (known/unknown) differs"
+    ok = status == 0
+    assert ok.sum() > 1000 and (~ok).sum() > 0
+    assert np.all(np.isnan(dist[~ok]))
+    assert np.max(np.abs(dist[ok] - od[ok])) <= 1e-5
+    assert np.max(np.abs(grad[ok] - og[ok])) <= 1e-3
+
+
+# ------------------------------------------------------------------------ edge cases
+
+
+def test_edge_cases_empty_nan_and_single_point(vbx):
+    g = vbx.Map(0.1, 8, 0.3, 2.0)
+    T = np.eye(4, dtype=np.float32)
+    g.integrate_scan(torch.zeros((0, 3), dtype=torch.float32, device="cuda"), T)
+    g.update_esdf()
+    assert g.num_blocks() == 0
+    g.integrate_scan(_dev(np.full((37, 3), np.nan)), T)
+    assert g.stats()["points_valid"] == 0 and g.num_blocks() == 0
+    o = oracle.OracleMap(0.1, 8, 0.3, 2.0)
+    pt = np.array([[0.33, -0.21, 1.7]], np.float32)
+    g.integrate_scan(_dev(pt), T)
+    o.integrate(pt, T)
+    compare_tsdf(g.export(), o.export(), 8)
+    assert np.array_equal(sort_rows(g.last_updated()), o.last_updated())
+    g.update_esdf()
+    g.sync()
+
+
+def test_max_range_filter_and_ragged_sizes(vbx):
+    rng = np.random.default_rng(4)
+    for n in (1, 31, 33, 255, 257, 1000):
+        pts = rng.uniform(-3, 3, (n, 3)).astype(np.float32)
+        pts[::7] = np.nan
+        T = np.eye(4, dtype=np.float32)
+        T[:3, 3] = [0.01, 0.02, 0.03]
+        g = vbx.Map(0.1, 8, 0.3, 2.0, max_range=2.5)
+        o = oracle.OracleMap(0.1, 8, 0.3, 2.0, max_range=2.5)
+        g.integrate_scan(_dev(pts), T)
+        o.integrate(pts, T)
+        assert g.stats()["points_valid"] == o.stats()["points_valid"]
+        r = compare_tsdf(g.export(), o.export(), 8)
+        assert r["max_dD"] <= TOL_D
+
+
+def test_pool_exhaustion_reports_out_of_memory(vbx):
+    s = scenes.plane_sphere(frames=1)
+    g = vbx.Map.from_scene_params(s.params, block_capacity=64)
+    g.integrate_scan(_dev(s.points[0]), s.poses[0])
+    with pytest.raises(vbx.VbxError) as ei:
+        g.sync()
+    assert ei.value.status == 2
+    # the map stays usable
+    g.update_esdf()
+    g.sync()
+    assert g.num_blocks() == 64
+
+
+def test_invalid_arguments(vbx):
+    with pytest.raises(vbx.VbxError):
+        vbx.Map(0.1, 7, 0.3, 2.0)
+    with pytest.raises(vbx.VbxError):
+        vbx.Map(-0.1, 8, 0.3, 2.0)
+    with pytest.raises(vbx.VbxError):
+        vbx.Map(0.1, 8, 0.05, 2.0)
