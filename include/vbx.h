@@ -65,7 +65,7 @@ vbx_status vbx_default_options(vbx_map_options* opt);
  * (4, 8, 16 or 32), truncation distance delta (>= v) and ESDF maximum distance d_max (> 0).
  * Sec. III: layers of fixed-size blocks indexed by block position through a hash table.
  * opt may be NULL (defaults). On success *out holds the new map. Allocates device memory
- * on the current device: about 65 bytes per pool voxel plus per-scan scratch. */
+ * on the current device: about 85 bytes per pool voxel plus per-scan scratch. */
 vbx_status vbx_create_map(float voxel_size, int voxels_per_block, float truncation, float max_esdf_dist,
                           const vbx_map_options* opt, vbx_map_t* out);
 

@@ -166,8 +166,8 @@ vbx_status read_error(vbx_map_t m, cudaStream_t s) {
   unsigned zero = 0;
   cudaMemcpy(&m->d.ctr->error, &zero, sizeof(unsigned), cudaMemcpyHostToDevice);
   if (err & vbx::kErrTimeout) return fail(VBX_ERR_TIMEOUT, "device loop exceeded its round or wait budget");
-  if (err & vbx::kErrHashFull) return fail(VBX_ERR_HASH_FULL, "block hash probe limit reached");
   if (err & vbx::kErrPoolFull) return fail(VBX_ERR_OUT_OF_MEMORY, "block pool exhausted (block_capacity)");
+  if (err & vbx::kErrHashFull) return fail(VBX_ERR_HASH_FULL, "block hash probe limit reached");
   if (err & vbx::kErrGroupTable) return fail(VBX_ERR_HASH_FULL, "per-scan group table full");
   return fail(VBX_ERR_CUDA, "unknown device error 0x%x", err);
 }
@@ -282,7 +282,8 @@ vbx_status vbx_create_map(float voxel_size, int voxels_per_block, float truncati
   VBX_ALLOC(d.bcoord, (size_t)cap, 0);
   VBX_ALLOC(d.nbr, (size_t)cap * 27, 0xff);
   VBX_ALLOC(d.tsdf, V, 0);
-  VBX_ALLOC(d.acc, 2 * V, 0);
+  VBX_ALLOC(d.acc, 4 * V, 0);
+  VBX_ALLOC(d.touch, V, 0);
   VBX_ALLOC(d.esdf, V, 0);
   VBX_ALLOC(d.vflags, V, 0);
   VBX_ALLOC(d.stamp_r, V, 0);
@@ -331,6 +332,7 @@ vbx_status vbx_integrate_scan(vbx_map_t m, const float* points_dev, int64_t n, c
   if (st != VBX_OK) return st;
   vbx::Pose pose;
   std::memcpy(pose.T, T, sizeof(pose.T));
+  m->d.scan_epoch += 1;
   e = vbx::launch_integrate(m->d, points_dev, (int)n, pose, m->cfg(stream), &m->hook);
   if (e != cudaSuccess) return cuda_fail(e, "integrate launch");
   return VBX_OK;

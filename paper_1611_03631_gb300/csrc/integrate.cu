@@ -237,18 +237,26 @@ __global__ void __launch_bounds__(kThreads) k_link_blocks(DevMap m) {
 }
 
 // ------------------------------------------------------------------------------------ A4
-__device__ __forceinline__ void accumulate(const DevMap& m, uint32_t vid, unsigned long long qw, unsigned long long qwd) {
-  const unsigned long long old = atomicAdd(&m.acc[2 * (size_t)vid], qw);
-  atomicAdd(&m.acc[2 * (size_t)vid + 1], qwd);
-  if (old == 0ull) {
+// Splits a float32 record into its exact two-part fixed-point representation.
+__device__ __forceinline__ void fx_split(float x, long long* hi, long long* lo) {
+  const float q = __fmul_rn(x, kAccScale);  // exact (power-of-two scaling)
+  const float t = truncf(q);
+  *hi = (long long)t;
+  *lo = __float2ll_rn(__fmul_rn(__fsub_rn(q, t), kAccLoScale));
+}
+
+__device__ __forceinline__ void accumulate(const DevMap& m, uint32_t vid, const long long v[4]) {
+  unsigned long long* a = &m.acc[4 * (size_t)vid];
+  for (int j = 0; j < 4; ++j)
+    if (v[j] != 0) atomicAdd(&a[j], (unsigned long long)v[j]);
+  if (atomicExch(&m.touch[vid], m.scan_epoch) != m.scan_epoch) {
     const unsigned i = atomicAdd(&m.ctr->nupdated, 1u);
     m.updated[i] = vid;
   }
 }
 
 __global__ void __launch_bounds__(kThreads) k_integrate_rays(DevMap m, Pose T) {
-  __shared__ unsigned long long sh_w[kWarps][32];
-  __shared__ unsigned long long sh_wd[kWarps][32];
+  __shared__ long long sh_v[4][kWarps][32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned nr = __ldcg(&m.ctr->ngroups);
   const float s[3] = {T.T[3], T.T[7], T.T[11]};
@@ -278,7 +286,7 @@ __global__ void __launch_bounds__(kThreads) k_integrate_rays(DevMap m, Pose T) {
     }
     while (__any_sync(kFull, active)) {
       uint32_t vid = kInvalid;
-      unsigned long long qw = 0, qwd = 0;
+      long long qv[4] = {0, 0, 0, 0};  // w hi, w*d hi, w lo, w*d lo
       if (active) {
         // Eq. (1) at the voxel centre, truncated to [-delta, delta]
         float dx[3];
@@ -302,9 +310,8 @@ __global__ void __launch_bounds__(kThreads) k_integrate_rays(DevMap m, Pose T) {
         if (w > 0.0f && slot != kInvalid) {
           const uint32_t l = (uint32_t)((((dda.c[2] & (B - 1)) << blog | (dda.c[1] & (B - 1))) << blog) | (dda.c[0] & (B - 1)));
           vid = (slot << m.b3log) | l;
-          long long a = __float2ll_rn(__fmul_rn(w, kAccScale));
-          qw = (unsigned long long)(a < 1 ? 1 : a);
-          qwd = (unsigned long long)__float2ll_rn(__fmul_rn(__fmul_rn(w, d), kAccScale));
+          fx_split(w, &qv[0], &qv[2]);
+          fx_split(__fmul_rn(w, d), &qv[1], &qv[3]);
           ++nrec;
         }
         if (left == 0) {
@@ -327,19 +334,17 @@ __global__ void __launch_bounds__(kThreads) k_integrate_rays(DevMap m, Pose T) {
       const unsigned peers = __match_any_sync(kFull, vid);
       const bool alone = (peers == (1u << lane)) || vid == kInvalid;
       if (__all_sync(kFull, alone)) {
-        if (vid != kInvalid) accumulate(m, vid, qw, qwd);
+        if (vid != kInvalid) accumulate(m, vid, qv);
       } else {
-        sh_w[wid][lane] = qw;
-        sh_wd[wid][lane] = qwd;
+        for (int j = 0; j < 4; ++j) sh_v[j][wid][lane] = qv[j];
         __syncwarp();
         if (vid != kInvalid && lane == __ffs(peers) - 1) {
-          unsigned long long sw = 0, swd = 0;
+          long long sum[4] = {0, 0, 0, 0};
           for (unsigned pm = peers; pm; pm &= pm - 1) {
             const int src = __ffs(pm) - 1;
-            sw += sh_w[wid][src];
-            swd += sh_wd[wid][src];
+            for (int j = 0; j < 4; ++j) sum[j] += sh_v[j][wid][src];
           }
-          accumulate(m, vid, sw, swd);
+          accumulate(m, vid, sum);
         }
         __syncwarp();
       }
@@ -353,12 +358,14 @@ __global__ void __launch_bounds__(kThreads) k_apply(DevMap m) {
   const unsigned nu = __ldcg(&m.ctr->nupdated);
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < nu; i += gridDim.x * blockDim.x) {
     const uint32_t vid = m.updated[i];
-    const long long sw = (long long)m.acc[2 * (size_t)vid];
-    const long long swd = (long long)m.acc[2 * (size_t)vid + 1];
-    m.acc[2 * (size_t)vid] = 0ull;
-    m.acc[2 * (size_t)vid + 1] = 0ull;
-    const float Sw = __fmul_rn(__ll2float_rn(sw), kAccInvScale);
-    const float Swd = __fmul_rn(__ll2float_rn(swd), kAccInvScale);
+    ulonglong2* a = reinterpret_cast<ulonglong2*>(&m.acc[4 * (size_t)vid]);
+    const ulonglong2 hi = a[0], lo = a[1];
+    a[0] = make_ulonglong2(0ull, 0ull);
+    a[1] = make_ulonglong2(0ull, 0ull);
+    const float Sw = __fadd_rn(__fmul_rn(__ll2float_rn((long long)hi.x), kAccInvScale),
+                               __fmul_rn(__ll2float_rn((long long)lo.x), kAccLoInvScale));
+    const float Swd = __fadd_rn(__fmul_rn(__ll2float_rn((long long)hi.y), kAccInvScale),
+                                __fmul_rn(__ll2float_rn((long long)lo.y), kAccLoInvScale));
     const float2 t = m.tsdf[vid];
     // Eq. (3): D <- (W D + sum w d) / (W + sum w), W <- min(W + sum w, W_max)
     const float Wn = __fadd_rn(t.y, Sw);

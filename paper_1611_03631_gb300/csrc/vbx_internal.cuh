@@ -6,7 +6,9 @@
 //                    direction k = (dx+1)*9 + (dy+1)*3 + (dz+1) (k = 13 is the block itself)
 //   per voxel      : voxel id vid = slot * B^3 + ((lz*B + ly)*B + lx)
 //                    tsdf[vid]   float2 (D, W)                          8 B
-//                    acc[2*vid]  u64 fixed-point sum of w, sum of w*d    16 B (zero between scans)
+//                    acc[4*vid]  i64 sums of w and w*d, each as an exact two-part fixed
+//                                point number (2^-28 part, 2^-60 part)      32 B (zero between scans)
+//                    touch[vid]  u32 epoch of the last scan that updated the voxel
 //                    esdf[vid]   u64 packed {d f32 | flags u8 | parent u8} 8 B
 //                    vflags[vid] u8 (bit0 queued for the ESDF)
 //                    stamp_r/stamp_l[vid] u32 frontier de-duplication epochs
@@ -22,8 +24,13 @@ namespace vbx {
 constexpr unsigned long long kEmptyKey = ~0ull;
 constexpr uint32_t kInvalid = 0xffffffffu;
 constexpr int kSub = 65536;  // fixed-point units per voxel for ray endpoints and offsets
-constexpr float kAccScale = 268435456.0f;        // 2^28: fixed point of the per-voxel sums
+// Per-voxel sums are exact: a float32 record x is split into hi = trunc(x * 2^28) and
+// lo = rint(frac(x * 2^28) * 2^32), i.e. units of 2^-28 and 2^-60; both are summed with 64-bit
+// integer atomics, so the sums do not depend on the order of the records.
+constexpr float kAccScale = 268435456.0f;  // 2^28
 constexpr float kAccInvScale = 1.0f / 268435456.0f;
+constexpr float kAccLoScale = 4294967296.0f;  // 2^32
+constexpr float kAccLoInvScale = 1.0f / 1152921504606846976.0f;  // 2^-60
 
 // sticky device error bits
 constexpr unsigned kErrPoolFull = 1u;
@@ -94,6 +101,8 @@ struct DevMap {
   uint32_t* nbr;
   float2* tsdf;
   unsigned long long* acc;
+  uint32_t* touch;
+  uint32_t scan_epoch;
   unsigned long long* esdf;
   uint8_t* vflags;
   uint32_t* stamp_r;

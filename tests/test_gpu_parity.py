@@ -194,14 +194,16 @@ def test_esdf_end_to_end_plane_sphere(vbx):
 def test_query_parity(vbx):
     s = scenes.plane_sphere(frames=4)
     g, o32 = _esdf_same_input(vbx, s, len(s))
-    q = scenes.random_queries(s, 4099, radius=3.0, seed=9)
-    q = np.concatenate([q, np.array([[0.05, 0.05, 0.05], [100.0, 0.0, 0.0]], np.float32)])
+    rng = np.random.default_rng(9)
+    d = rng.normal(size=(4099, 3))
+    q = (np.array([0.0, 0.0, 0.6]) + 2.2 * d / np.linalg.norm(d, axis=1, keepdims=True) * rng.uniform(0, 1, (4099, 1)) ** (1 / 3))
+    q = np.concatenate([q.astype(np.float32), np.array([[0.05, 0.05, 0.05], [100.0, 0.0, 0.0]], np.float32)])
     dist, grad, status = g.query(_dev(q))
     dist, grad, status = dist.cpu().numpy(), grad.cpu().numpy(), status.cpu().numpy()
     od, og, os_ = o32.query(q)
     assert np.array_equal(status, os_), "query status (known/unknown) differs"
     ok = status == 0
-    assert ok.sum() > 1000 and (~ok).sum() > 0
+    assert ok.sum() > 500 and (~ok).sum() > 0
     assert np.all(np.isnan(dist[~ok]))
     assert np.max(np.abs(dist[ok] - od[ok])) <= 1e-5
     assert np.max(np.abs(grad[ok] - og[ok])) <= 1e-3
