@@ -3,10 +3,12 @@
 //   A6 classify : every TSDF voxel updated since the last call takes one branch of the first
 //                 loop of Algorithm 1 (fixed band |D| < gamma, leaving the band, new voxel,
 //                 sign flip) and seeds the raise and lower frontiers
-//   A7 raise    : synchronous rounds; a popped non-fixed voxel is reset to +-d_max, its
+//   A7 raise    : synchronous rounds (one warp per popped voxel, one lane per direction);
+//                 a popped non-fixed voxel is reset to +-d_max, its
 //                 children (neighbours whose parent direction points back at it) form the
 //                 next raise frontier and all other observed neighbours join the lower frontier
-//   A8 lower    : synchronous rounds; each popped voxel relaxes its observed, non-fixed,
+//   A8 lower    : synchronous rounds; each popped voxel (one warp, one lane per direction)
+//                 relaxes its observed, non-fixed,
 //                 same-sign 26-neighbours with quasi-Euclidean steps; the neighbour's
 //                 {distance, parent} word is lowered with a 64-bit atomicMin whose high half
 //                 is the float's bit pattern (monotone in |d| for a fixed sign)
@@ -16,6 +18,7 @@
 // order). Frontier pushes are de-duplicated per round with monotone epoch stamps and
 // appended with one atomic per coalesced warp group.
 #include <cooperative_groups.h>
+#include <cstdlib>
 #include <cuda_runtime.h>
 
 #include "launch.h"
@@ -49,6 +52,10 @@ __global__ void __launch_bounds__(kThreads) k_esdf(DevMap m) {
   Counters* c = m.ctr;
   const unsigned tid = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned nthreads = gridDim.x * blockDim.x;
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned gwarp = tid >> 5, nwarps = nthreads >> 5;
+  const int kdir = lane < 13 ? (int)lane : (int)lane + 1;  // lanes 0..25 -> the 26 directions
+  const float klen = lane < 26 ? step_len(m, kdir) : 0.0f;
   const unsigned base = __ldcg(&c->epoch);
   const unsigned e0 = base + 1;  // epoch of the frontiers seeded by classification
   const float dmax = m.dmax;
@@ -108,23 +115,26 @@ __global__ void __launch_bounds__(kThreads) k_esdf(DevMap m) {
     uint32_t* nxt = (r & 1) ? m.rfront0 : m.rfront1;
     unsigned* ncnt = &c->rc[(r + 1) % 3];
     const unsigned ep = base + 2 + r;
-    for (unsigned i = tid; i < cnt; i += nthreads) {
+    for (unsigned i = gwarp; i < cnt; i += nwarps) {  // one warp per voxel, one lane per direction
       const uint32_t vid = cur[i];
-      ++pops;
       const unsigned long long w = __ldcg(&m.esdf[vid]);
       const unsigned fl = ew_flags(w);
-      if (!(fl & kFixed)) m.esdf[vid] = ew_pack(ew_d(w) < 0.0f ? -dmax : dmax, fl, kNoParent);
-      for (int k = 0; k < 27; ++k) {
-        if (k == 13) continue;
-        const uint32_t n = neighbor_vid(m, vid, k);
-        if (n == kInvalid) continue;
-        const unsigned long long nw = __ldcg(&m.esdf[n]);
-        const unsigned nfl = ew_flags(nw);
-        if (!(nfl & kObserved)) continue;
-        if (!(nfl & kFixed) && ew_parent(nw) == (unsigned)(26 - k))
-          push(nxt, ncnt, m.stamp_r, n, ep);
-        else
-          push(m.lfront0, &c->lc[0], m.stamp_l, n, e0);
+      if (lane == 0) {
+        ++pops;
+        if (!(fl & kFixed)) m.esdf[vid] = ew_pack(ew_d(w) < 0.0f ? -dmax : dmax, fl, kNoParent);
+      }
+      if (lane < 26) {
+        const uint32_t n = neighbor_vid(m, vid, kdir);
+        if (n != kInvalid) {
+          const unsigned long long nw = __ldcg(&m.esdf[n]);
+          const unsigned nfl = ew_flags(nw);
+          if (nfl & kObserved) {
+            if (!(nfl & kFixed) && ew_parent(nw) == (unsigned)(26 - kdir))
+              push(nxt, ncnt, m.stamp_r, n, ep);
+            else
+              push(m.lfront0, &c->lc[0], m.stamp_l, n, e0);
+          }
+        }
       }
     }
     if (!grid_barrier(&c->bar, gridDim.x, &c->error)) return;
@@ -147,28 +157,25 @@ __global__ void __launch_bounds__(kThreads) k_esdf(DevMap m) {
     uint32_t* nxt = (l & 1) ? m.lfront0 : m.lfront1;
     unsigned* ncnt = &c->lc[(l + 1) % 3];
     const unsigned ep = base + 2 + l;
-    for (unsigned i = tid; i < cnt; i += nthreads) {
+    for (unsigned i = gwarp; i < cnt; i += nwarps) {  // one warp per voxel, one lane per direction
       const uint32_t vid = cur[i];
       const unsigned long long w = __ldcg(&m.esdf[vid]);
       if (!(ew_flags(w) & kObserved)) continue;
-      ++pops;
+      if (lane == 0) ++pops;
+      if (lane >= 26) continue;
       const float dv = ew_d(w);
       const bool neg = dv < 0.0f;
-      const float av = fabsf(dv);
-      for (int k = 0; k < 27; ++k) {
-        if (k == 13) continue;
-        const uint32_t n = neighbor_vid(m, vid, k);
-        if (n == kInvalid) continue;
-        const unsigned long long nw = __ldcg(&m.esdf[n]);
-        const unsigned nfl = ew_flags(nw);
-        if ((nfl & (kObserved | kFixed)) != kObserved) continue;
-        const float dn = ew_d(nw);
-        if ((dn < 0.0f) != neg) continue;
-        const float cand = __fadd_rn(av, step_len(m, k));
-        if (cand < fabsf(dn)) {
-          const unsigned long long old = atomicMin(&m.esdf[n], ew_pack(neg ? -cand : cand, nfl, (unsigned)(26 - k)));
-          if (fabsf(ew_d(old)) > cand) push(nxt, ncnt, m.stamp_l, n, ep);
-        }
+      const uint32_t n = neighbor_vid(m, vid, kdir);
+      if (n == kInvalid) continue;
+      const unsigned long long nw = __ldcg(&m.esdf[n]);
+      const unsigned nfl = ew_flags(nw);
+      if ((nfl & (kObserved | kFixed)) != kObserved) continue;
+      const float dn = ew_d(nw);
+      if ((dn < 0.0f) != neg) continue;
+      const float cand = __fadd_rn(fabsf(dv), klen);
+      if (cand < fabsf(dn)) {
+        const unsigned long long old = atomicMin(&m.esdf[n], ew_pack(neg ? -cand : cand, nfl, (unsigned)(26 - kdir)));
+        if (fabsf(ew_d(old)) > cand) push(nxt, ncnt, m.stamp_l, n, ep);
       }
     }
     if (!grid_barrier(&c->bar, gridDim.x, &c->error)) return;
@@ -195,7 +202,10 @@ cudaError_t launch_esdf(const DevMap& m, const LaunchCfg& cfg, LaunchHook* hook)
   static int per_sm = -1;
   if (per_sm < 0) {
     per_sm = esdf_max_blocks_per_sm();
-    if (per_sm > 4) per_sm = 4;
+    // resident CTAs per SM of the cooperative grid: 4 by default, VBX_ESDF_CTAS_PER_SM to tune
+    int want = 4;
+    if (const char* e = getenv("VBX_ESDF_CTAS_PER_SM")) want = atoi(e) > 0 ? atoi(e) : want;
+    if (per_sm > want) per_sm = want;
   }
   if (per_sm <= 0) return cudaErrorCooperativeLaunchTooLarge;
   dim3 grid(cfg.num_sms * per_sm), block(kThreads);
