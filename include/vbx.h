@@ -82,6 +82,21 @@ vbx_status vbx_destroy_map(vbx_map_t map);
 vbx_status vbx_integrate_scan(vbx_map_t map, const float* points_dev, int64_t n, const float T_world_sensor[16],
                               void* stream);
 
+/* vbx_integrate_scan for callers that must not allocate device memory while they run, such
+ * as a robot's real-time loop (cudaMalloc/cudaFree synchronise the whole device and can stall
+ * it past the loop's deadline) or a process that committed its device-memory budget at
+ * start-up. The paper has no counterpart: it only changes where the per-scan scratch lives.
+ * Same arguments and results as vbx_integrate_scan, but the scratch (point group table, group
+ * list, ray buffer) is a file-scope device array of the library sized for at most 65536
+ * points; n above 65536 returns VBX_ERR_INVALID_ARG and enqueues nothing. The call allocates
+ * nothing. Every GPU that loads the library holds that array (about 9.3 MiB) until exit. The
+ * first call on a device looks up the array's device address (cudaGetSymbolAddress); make that
+ * first call before any stream capture. All calls share the array: calls whose work overlaps
+ * on the GPU (other streams, other maps at the same time) race and must be serialised. The
+ * current device must be the map's device. */
+vbx_status vbx_integrate_scan_noalloc(vbx_map_t map, const float* points_dev, int64_t n, const float T_world_sensor[16],
+                                      void* stream);
+
 /* Updates the ESDF incrementally from the TSDF voxels updated since the last call
  * (Sec. V-A, Algorithm 1): fixed band |D| < gamma, raise wavefront, then lower wavefront over
  * 26-connected neighbours with quasi-Euclidean steps v, v*sqrt(2), v*sqrt(3), capped at

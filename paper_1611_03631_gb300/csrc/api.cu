@@ -338,6 +338,34 @@ vbx_status vbx_integrate_scan(vbx_map_t m, const float* points_dev, int64_t n, c
   return VBX_OK;
 }
 
+vbx_status vbx_integrate_scan_noalloc(vbx_map_t m, const float* points_dev, int64_t n, const float T[16],
+                                      void* stream) {
+  if (!m) return fail(VBX_ERR_INVALID_ARG, "map is NULL");
+  if (n < 0 || n > vbx::kNoAllocMaxPoints)
+    return fail(VBX_ERR_INVALID_ARG, "n = %lld outside [0, %d], the scratch limit of vbx_integrate_scan_noalloc",
+                (long long)n, vbx::kNoAllocMaxPoints);
+  if (n > 0 && !points_dev) return fail(VBX_ERR_INVALID_ARG, "points_dev is NULL");
+  if (!T) return fail(VBX_ERR_INVALID_ARG, "T_world_sensor is NULL");
+  int device = 0;
+  cudaError_t e = cudaGetDevice(&device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (device != m->device) return fail(VBX_ERR_INVALID_ARG, "the current device is not the map's device");
+  void* scratch = nullptr;
+  e = vbx::noalloc_scratch_setup(device, &scratch);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the static scratch");
+  cudaStream_t s = (cudaStream_t)stream;
+  e = cudaMemsetAsync(m->d.ctr, 0, offsetof(vbx::Counters, blocks), s);
+  if (e != cudaSuccess) return cuda_fail(e, "reset scan counters");
+  m->last_points_in = n;
+  if (n == 0) return VBX_OK;
+  vbx::Pose pose;
+  std::memcpy(pose.T, T, sizeof(pose.T));
+  m->d.scan_epoch += 1;
+  e = vbx::launch_integrate_noalloc(m->d, scratch, points_dev, (int)n, pose, m->cfg(stream), &m->hook);
+  if (e != cudaSuccess) return cuda_fail(e, "integrate launch");
+  return VBX_OK;
+}
+
 vbx_status vbx_update_esdf(vbx_map_t m, void* stream) {
   if (!m) return fail(VBX_ERR_INVALID_ARG, "map is NULL");
   cudaStream_t s = (cudaStream_t)stream;

@@ -13,6 +13,8 @@
 // explicitly rounded intrinsics, so the compiler cannot contract or reorder it.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "launch.h"
 #include "vbx_internal.cuh"
 
@@ -457,6 +459,65 @@ cudaError_t launch_import(const DevMap& m, const int* vox, const float* D, const
   k_import_set<<<g, kThreads, 0, s>>>(m, vox, D, W, n);
   hook->end(kKImportSet, s);
   return cudaGetLastError();
+}
+
+
+// -------------------------------------------------------------------------------------------
+// Integration without device allocation.
+//
+// Callers that cannot allocate device memory while they run (a robot's real-time loop, where
+// cudaMalloc/cudaFree synchronise the whole device and can stall for milliseconds past the
+// control deadline; or a process that committed its whole device-memory budget at start-up)
+// integrate scans through this path. vbx_integrate_scan keeps its per-scan scratch (point
+// group table, group list, ray buffer) in map-owned buffers that it grows with cudaMalloc when
+// a scan has more points than before; here the same scratch lives in one file-scope device
+// array instead, sized for at most kNoAllocMaxPoints points, so no call allocates.
+// Every GPU that loads the library holds this array (about 9.3 MiB) until the process exits.
+// All calls share it and it keeps the previous call's contents: the group table is cleared at
+// the start of every call, the other buffers are fully written before they are read. Two calls
+// whose work overlaps on the GPU (different streams, or different maps used concurrently)
+// race on the array; callers serialise them.
+
+namespace {
+constexpr uint32_t kNoAllocGroupEntries = 2u * (uint32_t)kNoAllocMaxPoints;
+constexpr size_t kNoAllocGroupBytes = (size_t)kNoAllocGroupEntries * sizeof(GroupEntry);
+constexpr size_t kNoAllocListBytes = (size_t)kNoAllocMaxPoints * sizeof(uint32_t);
+constexpr size_t kNoAllocRayBytes = (size_t)kNoAllocMaxPoints * sizeof(float4);
+constexpr size_t kNoAllocBytes = kNoAllocGroupBytes + kNoAllocListBytes + kNoAllocRayBytes;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Device address of g_noalloc_scratch, resolved once per device with that device current.
+// In host code the symbol itself is only a host-side stand-in, never a device address.
+constexpr int kMaxDevices = 64;
+void* g_noalloc_ptr[kMaxDevices] = {nullptr};
+std::mutex g_noalloc_mu;
+}  // namespace
+
+cudaError_t noalloc_scratch_setup(int device, void** ptr) {
+  if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[device] = p;
+  }
+  *ptr = g_noalloc_ptr[device];
+  return cudaSuccess;
+}
+
+cudaError_t launch_integrate_noalloc(const DevMap& m, void* scratch, const float* pts, int n, const Pose& T,
+                                     const LaunchCfg& cfg, LaunchHook* hook) {
+  DevMap ms = m;
+  unsigned char* base = static_cast<unsigned char*>(scratch);
+  ms.gtab = reinterpret_cast<GroupEntry*>(base);
+  ms.gmask = kNoAllocGroupEntries - 1;
+  ms.glist = reinterpret_cast<uint32_t*>(base + kNoAllocGroupBytes);
+  ms.rays = reinterpret_cast<float4*>(base + kNoAllocGroupBytes + kNoAllocListBytes);
+  cudaError_t e = launch_init_groups(ms.gtab, kNoAllocGroupEntries, cfg.stream, hook);
+  if (e != cudaSuccess) return e;
+  return launch_integrate(ms, pts, n, T, cfg, hook);
 }
 
 }  // namespace vbx

@@ -43,6 +43,11 @@ extern const char* const kKernelNames[kNumKernels];
 cudaError_t launch_init_groups(GroupEntry* tab, uint32_t entries, cudaStream_t s, LaunchHook* hook);
 cudaError_t launch_integrate(const DevMap& m, const float* pts, int n, const Pose& T, const LaunchCfg& cfg,
                              LaunchHook* hook);
+// Largest scan accepted by the allocation-free integration entry point.
+constexpr int kNoAllocMaxPoints = 1 << 16;
+cudaError_t noalloc_scratch_setup(int device, void** ptr);
+cudaError_t launch_integrate_noalloc(const DevMap& m, void* scratch, const float* pts, int n, const Pose& T,
+                                     const LaunchCfg& cfg, LaunchHook* hook);
 cudaError_t launch_import(const DevMap& m, const int* vox, const float* D, const float* W, int n,
                           const LaunchCfg& cfg, LaunchHook* hook);
 

@@ -82,6 +82,7 @@ _SIGS = {
     ),
     "vbx_destroy_map": (ctypes.c_int, [_vp]),
     "vbx_integrate_scan": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp]),
+    "vbx_integrate_scan_noalloc": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp]),
     "vbx_update_esdf": (ctypes.c_int, [_vp, _vp]),
     "vbx_query_distance_gradient": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, _vp, _vp]),
     "vbx_sync": (ctypes.c_int, [_vp, _vp]),
@@ -219,6 +220,12 @@ class Map:
         p = _dev_f32(points, 3)
         T = np.ascontiguousarray(np.asarray(T_world_sensor, dtype=np.float32).reshape(16))
         _check(self._lib.vbx_integrate_scan(self._h, p.data_ptr(), p.shape[0], T.ctypes.data, _stream_ptr(stream)))
+
+    def integrate_scan_noalloc(self, points, T_world_sensor, stream=None) -> None:
+        """vbx_integrate_scan_noalloc: same result, scratch in a static device array (n <= 65536)."""
+        p = _dev_f32(points, 3)
+        T = np.ascontiguousarray(np.asarray(T_world_sensor, dtype=np.float32).reshape(16))
+        _check(self._lib.vbx_integrate_scan_noalloc(self._h, p.data_ptr(), p.shape[0], T.ctypes.data, _stream_ptr(stream)))
 
     def update_esdf(self, stream=None) -> None:
         _check(self._lib.vbx_update_esdf(self._h, _stream_ptr(stream)))
