@@ -43,8 +43,9 @@
 //      Eq. (3) is applied once per scan per voxel with the summed weight (order-independent);
 //      W is capped at W_max; a voxel is "updated" by a scan iff it received a record.
 //   R6 ESDF classification (Algorithm 1, first loop): isFixed is evaluated on the TSDF voxel,
-//      fixed iff |fl32(D)| < gamma; "v_E.d > v_T.d" is read as a magnitude comparison in the
-//      same sign; the "fixed" flag is set in the fixed branch and cleared where the voxel
+//      fixed iff |fl32(D)| < gamma; its comparison of the ESDF and TSDF distances is read as a
+//      magnitude comparison in the same sign; the "fixed" flag is set in the fixed branch and
+//      cleared where the voxel
 //      leaves the band; a non-fixed observed voxel whose TSDF sign flipped is raised like a
 //      voxel leaving the band.
 //   R7 raise: only non-fixed voxels are reset; a neighbour is a child iff its parent
