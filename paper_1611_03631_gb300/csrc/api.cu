@@ -284,6 +284,7 @@ vbx_status vbx_create_map(float voxel_size, int voxels_per_block, float truncati
   VBX_ALLOC(d.tsdf, V, 0);
   VBX_ALLOC(d.acc, 4 * V, 0);
   VBX_ALLOC(d.touch, V, 0);
+  VBX_ALLOC(d.btouch, (size_t)cap, 0);
   VBX_ALLOC(d.esdf, V, 0);
   VBX_ALLOC(d.vflags, V, 0);
   VBX_ALLOC(d.stamp_r, V, 0);
@@ -332,7 +333,6 @@ vbx_status vbx_integrate_scan(vbx_map_t m, const float* points_dev, int64_t n, c
   if (st != VBX_OK) return st;
   vbx::Pose pose;
   std::memcpy(pose.T, T, sizeof(pose.T));
-  m->d.scan_epoch += 1;
   e = vbx::launch_integrate(m->d, points_dev, (int)n, pose, m->cfg(stream), &m->hook);
   if (e != cudaSuccess) return cuda_fail(e, "integrate launch");
   return VBX_OK;
@@ -360,7 +360,6 @@ vbx_status vbx_integrate_scan_noalloc(vbx_map_t m, const float* points_dev, int6
   if (n == 0) return VBX_OK;
   vbx::Pose pose;
   std::memcpy(pose.T, T, sizeof(pose.T));
-  m->d.scan_epoch += 1;
   e = vbx::launch_integrate_noalloc(m->d, scratch, points_dev, (int)n, pose, m->cfg(stream), &m->hook);
   if (e != cudaSuccess) return cuda_fail(e, "integrate launch");
   return VBX_OK;

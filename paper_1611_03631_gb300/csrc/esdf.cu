@@ -202,8 +202,9 @@ cudaError_t launch_esdf(const DevMap& m, const LaunchCfg& cfg, LaunchHook* hook)
   static int per_sm = -1;
   if (per_sm < 0) {
     per_sm = esdf_max_blocks_per_sm();
-    // resident CTAs per SM of the cooperative grid: 4 by default, VBX_ESDF_CTAS_PER_SM to tune
-    int want = 4;
+    // resident CTAs per SM of the cooperative grid: 2 by default (fastest of 1, 2, 4 on the
+    // room workload), VBX_ESDF_CTAS_PER_SM to tune
+    int want = 2;
     if (const char* e = getenv("VBX_ESDF_CTAS_PER_SM")) want = atoi(e) > 0 ? atoi(e) : want;
     if (per_sm > want) per_sm = want;
   }

@@ -8,15 +8,20 @@
 //                           per-voxel sums of w and w*d in 2^-28 fixed point with integer
 //                           atomics, pre-aggregated across the warp (order-independent, so
 //                           the result does not depend on scheduling)
-//   k_apply          A5     Eq. (3) merge of each updated voxel; queues it for the ESDF
+//   k_apply          A5     Eq. (3) merge of each voxel that received records (found through the
+//                           per-block and per-voxel touch flags); queues it for the ESDF
 // All float32 arithmetic that decides a set (keys, endpoints, visited voxels, w > 0) uses
 // explicitly rounded intrinsics, so the compiler cannot contract or reorder it.
 #include <cuda_runtime.h>
 
 #include <mutex>
 
+#include <cooperative_groups.h>
+
 #include "launch.h"
 #include "vbx_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace vbx {
 
@@ -211,10 +216,10 @@ __global__ void __launch_bounds__(kThreads) k_group_rays(DevMap m, Pose T) {
     // voxel traversal, so it visits exactly the blocks of the traversed voxels
     Dda dda;
     dda.init(g.S, g.E, 16 + m.blog);
-    block_insert(m, dda.c[0], dda.c[1], dda.c[2]);
+    block_insert(m, dda.cx, dda.cy, dda.cz);
     for (int left = dda.steps(); left > 0; --left) {
       dda.step();
-      block_insert(m, dda.c[0], dda.c[1], dda.c[2]);
+      block_insert(m, dda.cx, dda.cy, dda.cz);
     }
   }
 }
@@ -247,14 +252,13 @@ __device__ __forceinline__ void fx_split(float x, long long* hi, long long* lo) 
   *lo = __float2ll_rn(__fmul_rn(__fsub_rn(q, t), kAccLoScale));
 }
 
+// All four parts and the touch flag are fire-and-forget reductions (no returned value), so
+// the ray loop never waits on an atomic.
 __device__ __forceinline__ void accumulate(const DevMap& m, uint32_t vid, const long long v[4]) {
   unsigned long long* a = &m.acc[4 * (size_t)vid];
   for (int j = 0; j < 4; ++j)
     if (v[j] != 0) atomicAdd(&a[j], (unsigned long long)v[j]);
-  if (atomicExch(&m.touch[vid], m.scan_epoch) != m.scan_epoch) {
-    const unsigned i = atomicAdd(&m.ctr->nupdated, 1u);
-    m.updated[i] = vid;
-  }
+  atomicOr(&m.touch[vid], 1u);
 }
 
 __global__ void __launch_bounds__(kThreads) k_integrate_rays(DevMap m, Pose T) {
@@ -272,7 +276,7 @@ __global__ void __launch_bounds__(kThreads) k_integrate_rays(DevMap m, Pose T) {
     float Wg = 0.0f;
     Dda dda;
     int left = 0;
-    int bc[3] = {0, 0, 0};
+    int bcx = 0, bcy = 0, bcz = 0;
     uint32_t slot = kInvalid;
     if (active) {
       const float4 r = m.rays[gi];
@@ -282,8 +286,11 @@ __global__ void __launch_bounds__(kThreads) k_integrate_rays(DevMap m, Pose T) {
       if (active) {
         dda.init(g.S, g.E, 16);
         left = dda.steps();
-        for (int a = 0; a < 3; ++a) bc[a] = dda.c[a] >> blog;
-        slot = block_lookup(m, bc[0], bc[1], bc[2]);
+        bcx = dda.cx >> blog;
+        bcy = dda.cy >> blog;
+        bcz = dda.cz >> blog;
+        slot = block_lookup(m, bcx, bcy, bcz);
+        if (slot != kInvalid) atomicOr(&m.btouch[slot], 1u);
       }
     }
     while (__any_sync(kFull, active)) {
@@ -292,8 +299,10 @@ __global__ void __launch_bounds__(kThreads) k_integrate_rays(DevMap m, Pose T) {
       if (active) {
         // Eq. (1) at the voxel centre, truncated to [-delta, delta]
         float dx[3];
+        const int cc[3] = {dda.cx, dda.cy, dda.cz};
+#pragma unroll
         for (int a = 0; a < 3; ++a) {
-          const float xc = __fmul_rn(__fadd_rn((float)dda.c[a], 0.5f), m.v);
+          const float xc = __fmul_rn(__fadd_rn((float)cc[a], 0.5f), m.v);
           dx[a] = __fsub_rn(g.p[a], xc);
         }
         const float dist = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(dx[0], dx[0]), __fmul_rn(dx[1], dx[1])), __fmul_rn(dx[2], dx[2])));
@@ -310,7 +319,7 @@ __global__ void __launch_bounds__(kThreads) k_integrate_rays(DevMap m, Pose T) {
             w = __fmul_rn(Wg, __fdiv_rn(__fadd_rn(d, m.delta), __fsub_rn(m.delta, m.eps)));
         }
         if (w > 0.0f && slot != kInvalid) {
-          const uint32_t l = (uint32_t)((((dda.c[2] & (B - 1)) << blog | (dda.c[1] & (B - 1))) << blog) | (dda.c[0] & (B - 1)));
+          const uint32_t l = (uint32_t)((((dda.cz & (B - 1)) << blog | (dda.cy & (B - 1))) << blog) | (dda.cx & (B - 1)));
           vid = (slot << m.b3log) | l;
           fx_split(w, &qv[0], &qv[2]);
           fx_split(__fmul_rn(w, d), &qv[1], &qv[3]);
@@ -321,15 +330,30 @@ __global__ void __launch_bounds__(kThreads) k_integrate_rays(DevMap m, Pose T) {
         } else {
           const int ax = dda.step();
           --left;
-          const int nb = dda.c[ax] >> blog;
-          if (nb != bc[ax]) {
-            bc[ax] = nb;
-            if (slot != kInvalid) {
-              const int k = ax == 0 ? (dda.st[0] + 1) * 9 + 4 : (ax == 1 ? 9 + (dda.st[1] + 1) * 3 + 1 : 13 + dda.st[2]);
-              slot = __ldg(&m.nbr[(size_t)slot * 27 + k]);
-            } else {
-              slot = block_lookup(m, bc[0], bc[1], bc[2]);
+          // block transition: a 6-connected step into the face neighbour
+          int k = -1;
+          if (ax == 0) {
+            const int nb = dda.cx >> blog;
+            if (nb != bcx) {
+              bcx = nb;
+              k = (dda.sx + 1) * 9 + 4;
             }
+          } else if (ax == 1) {
+            const int nb = dda.cy >> blog;
+            if (nb != bcy) {
+              bcy = nb;
+              k = 9 + (dda.sy + 1) * 3 + 1;
+            }
+          } else {
+            const int nb = dda.cz >> blog;
+            if (nb != bcz) {
+              bcz = nb;
+              k = 13 + dda.sz;
+            }
+          }
+          if (k >= 0) {
+            slot = slot != kInvalid ? __ldg(&m.nbr[(size_t)slot * 27 + k]) : block_lookup(m, bcx, bcy, bcz);
+            if (slot != kInvalid) atomicOr(&m.btouch[slot], 1u);
           }
         }
       }
@@ -356,28 +380,48 @@ __global__ void __launch_bounds__(kThreads) k_integrate_rays(DevMap m, Pose T) {
 }
 
 // ------------------------------------------------------------------------------------ A5
+// Appends vid to a list with one atomic per coalesced group of lanes.
+__device__ __forceinline__ void append(uint32_t* list, unsigned* count, uint32_t vid) {
+  cg::coalesced_group g = cg::coalesced_threads();
+  unsigned base = 0;
+  if (g.thread_rank() == 0) base = atomicAdd(count, g.size());
+  base = g.shfl(base, 0);
+  list[base + g.thread_rank()] = vid;
+}
+
+// One CTA per touched block: every voxel that received records this scan gets the Eq. (3)
+// merge, its sums and flag are cleared, and it joins the scan's updated list and (once) the
+// queue of the next ESDF update.
 __global__ void __launch_bounds__(kThreads) k_apply(DevMap m) {
-  const unsigned nu = __ldcg(&m.ctr->nupdated);
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < nu; i += gridDim.x * blockDim.x) {
-    const uint32_t vid = m.updated[i];
-    ulonglong2* a = reinterpret_cast<ulonglong2*>(&m.acc[4 * (size_t)vid]);
-    const ulonglong2 hi = a[0], lo = a[1];
-    a[0] = make_ulonglong2(0ull, 0ull);
-    a[1] = make_ulonglong2(0ull, 0ull);
-    const float Sw = __fadd_rn(__fmul_rn(__ll2float_rn((long long)hi.x), kAccInvScale),
-                               __fmul_rn(__ll2float_rn((long long)lo.x), kAccLoInvScale));
-    const float Swd = __fadd_rn(__fmul_rn(__ll2float_rn((long long)hi.y), kAccInvScale),
-                                __fmul_rn(__ll2float_rn((long long)lo.y), kAccLoInvScale));
-    const float2 t = m.tsdf[vid];
-    // Eq. (3): D <- (W D + sum w d) / (W + sum w), W <- min(W + sum w, W_max)
-    const float Wn = __fadd_rn(t.y, Sw);
-    const float D = __fdiv_rn(__fadd_rn(__fmul_rn(t.y, t.x), Swd), Wn);
-    m.tsdf[vid] = make_float2(D, fminf(Wn, m.wmax));
-    if (!(m.vflags[vid] & kQueuedForEsdf)) {
-      m.vflags[vid] |= kQueuedForEsdf;
-      const unsigned j = atomicAdd(&m.ctr->ndirty, 1u);
-      m.dirty[j] = vid;
+  const unsigned nb = min(__ldcg(&m.ctr->blocks), m.cap_blocks);
+  const unsigned B3 = 1u << m.b3log;
+  for (unsigned b = blockIdx.x; b < nb; b += gridDim.x) {
+    if (__ldcg(&m.btouch[b]) == 0u) continue;  // uniform across the CTA
+    for (unsigned l = threadIdx.x; l < B3; l += blockDim.x) {
+      const uint32_t vid = (b << m.b3log) | l;
+      if (m.touch[vid] == 0u) continue;
+      m.touch[vid] = 0u;
+      ulonglong2* a = reinterpret_cast<ulonglong2*>(&m.acc[4 * (size_t)vid]);
+      const ulonglong2 hi = a[0], lo = a[1];
+      a[0] = make_ulonglong2(0ull, 0ull);
+      a[1] = make_ulonglong2(0ull, 0ull);
+      const float Sw = __fadd_rn(__fmul_rn(__ll2float_rn((long long)hi.x), kAccInvScale),
+                                 __fmul_rn(__ll2float_rn((long long)lo.x), kAccLoInvScale));
+      const float Swd = __fadd_rn(__fmul_rn(__ll2float_rn((long long)hi.y), kAccInvScale),
+                                  __fmul_rn(__ll2float_rn((long long)lo.y), kAccLoInvScale));
+      const float2 t = m.tsdf[vid];
+      // Eq. (3): D <- (W D + sum w d) / (W + sum w), W <- min(W + sum w, W_max)
+      const float Wn = __fadd_rn(t.y, Sw);
+      const float D = __fdiv_rn(__fadd_rn(__fmul_rn(t.y, t.x), Swd), Wn);
+      m.tsdf[vid] = make_float2(D, fminf(Wn, m.wmax));
+      append(m.updated, &m.ctr->nupdated, vid);
+      if (!(m.vflags[vid] & kQueuedForEsdf)) {
+        m.vflags[vid] |= kQueuedForEsdf;
+        append(m.dirty, &m.ctr->ndirty, vid);
+      }
     }
+    __syncthreads();
+    if (threadIdx.x == 0) m.btouch[b] = 0u;
   }
 }
 

@@ -2,13 +2,14 @@
 //
 // HBM layout of one map (all arrays indexed by pool slot or by voxel id):
 //   block hash     : hkeys[H] u64 packed block key (EMPTY = ~0), hvals[H] u32 pool slot
-//   per block      : bcoord[slot] int3, nbr[slot*27 + k] u32 slot of the neighbour block in
+//   per block      : btouch[slot] u32 flag: a ray of the current scan entered the block
+//                    bcoord[slot] int3, nbr[slot*27 + k] u32 slot of the neighbour block in
 //                    direction k = (dx+1)*9 + (dy+1)*3 + (dz+1) (k = 13 is the block itself)
 //   per voxel      : voxel id vid = slot * B^3 + ((lz*B + ly)*B + lx)
 //                    tsdf[vid]   float2 (D, W)                          8 B
 //                    acc[4*vid]  i64 sums of w and w*d, each as an exact two-part fixed
 //                                point number (2^-28 part, 2^-60 part)      32 B (zero between scans)
-//                    touch[vid]  u32 epoch of the last scan that updated the voxel
+//                    touch[vid]  u32 flag: the voxel received a record in the current scan
 //                    esdf[vid]   u64 packed {d f32 | flags u8 | parent u8} 8 B
 //                    vflags[vid] u8 (bit0 queued for the ESDF)
 //                    stamp_r/stamp_l[vid] u32 frontier de-duplication epochs
@@ -102,7 +103,7 @@ struct DevMap {
   float2* tsdf;
   unsigned long long* acc;
   uint32_t* touch;
-  uint32_t scan_epoch;
+  uint32_t* btouch;
   unsigned long long* esdf;
   uint8_t* vflags;
   uint32_t* stamp_r;
@@ -257,14 +258,16 @@ __device__ __forceinline__ bool ray_setup(const float pbar[3], const float s[3],
 // C_ab = num_a*den_b - num_b*den_a are kept and updated by additions when an axis steps.
 // Ties go to x, then y, then z.
 struct Dda {
-  int c[3];
-  int st[3];
-  int rem[3];
-  long long inc[3];  // F * den_a
+  int cx, cy, cz;     // current cell
+  int sx, sy, sz;     // step direction per axis (+1 / -1)
+  int rx, ry, rz;     // remaining steps per axis
+  long long ix, iy, iz;  // F * den per axis
   long long cxy, cxz, cyz;
 
   __device__ __forceinline__ void init(const long long S[3], const long long E[3], int log2F) {
     long long num[3], den[3];
+    int c[3], st[3], rem[3];
+#pragma unroll
     for (int a = 0; a < 3; ++a) {
       c[a] = (int)(S[a] >> log2F);
       const int ce = (int)(E[a] >> log2F);
@@ -272,33 +275,38 @@ struct Dda {
       den[a] = E[a] >= S[a] ? E[a] - S[a] : S[a] - E[a];
       rem[a] = ce >= c[a] ? ce - c[a] : c[a] - ce;
       num[a] = st[a] > 0 ? (((long long)c[a] + 1) << log2F) - S[a] : S[a] - ((long long)c[a] << log2F);
-      inc[a] = den[a] << log2F;
     }
+    cx = c[0], cy = c[1], cz = c[2];
+    sx = st[0], sy = st[1], sz = st[2];
+    rx = rem[0], ry = rem[1], rz = rem[2];
+    ix = den[0] << log2F, iy = den[1] << log2F, iz = den[2] << log2F;
     cxy = num[0] * den[1] - num[1] * den[0];
     cxz = num[0] * den[2] - num[2] * den[0];
     cyz = num[1] * den[2] - num[2] * den[1];
   }
-  __device__ __forceinline__ int steps() const { return rem[0] + rem[1] + rem[2]; }
-  // Advances one cell; returns the axis stepped.
+  __device__ __forceinline__ int steps() const { return rx + ry + rz; }
+  // Advances one cell; returns the axis stepped (0, 1, 2).
   __device__ __forceinline__ int step() {
-    const bool vx = rem[0] > 0, vy = rem[1] > 0, vz = rem[2] > 0;
-    int a;
+    const bool vx = rx > 0, vy = ry > 0, vz = rz > 0;
     if (vx && (!vy || cxy <= 0) && (!vz || cxz <= 0)) {
-      a = 0;
-      cxy += inc[1];
-      cxz += inc[2];
-    } else if (vy && (!vz || cyz <= 0)) {
-      a = 1;
-      cxy -= inc[0];
-      cyz += inc[2];
-    } else {
-      a = 2;
-      cxz -= inc[0];
-      cyz -= inc[1];
+      cxy += iy;
+      cxz += iz;
+      cx += sx;
+      rx -= 1;
+      return 0;
     }
-    c[a] += st[a];
-    rem[a] -= 1;
-    return a;
+    if (vy && (!vz || cyz <= 0)) {
+      cxy -= ix;
+      cyz += iz;
+      cy += sy;
+      ry -= 1;
+      return 1;
+    }
+    cxz -= ix;
+    cyz -= iy;
+    cz += sz;
+    rz -= 1;
+    return 2;
   }
 };
 
