@@ -62,10 +62,10 @@ typedef struct {
 vbx_status vbx_default_options(vbx_map_options* opt);
 
 /* Creates a map of voxel size v (> 0, metres), blocks of voxels_per_block^3 voxels
- * (4, 8, 16 or 32), truncation distance delta (>= v) and ESDF maximum distance d_max (> 0).
+ * (4, 8 or 16), truncation distance delta (>= v) and ESDF maximum distance d_max (> 0).
  * Sec. III: layers of fixed-size blocks indexed by block position through a hash table.
  * opt may be NULL (defaults). On success *out holds the new map. Allocates device memory
- * on the current device: about 85 bytes per pool voxel plus per-scan scratch. */
+ * on the current device: about 62 bytes per pool voxel plus per-scan scratch. */
 vbx_status vbx_create_map(float voxel_size, int voxels_per_block, float truncation, float max_esdf_dist,
                           const vbx_map_options* opt, vbx_map_t* out);
 
@@ -100,7 +100,8 @@ vbx_status vbx_integrate_scan_noalloc(vbx_map_t map, const float* points_dev, in
 /* Updates the ESDF incrementally from the TSDF voxels updated since the last call
  * (Sec. V-A, Algorithm 1): fixed band |D| < gamma, raise wavefront, then lower wavefront over
  * 26-connected neighbours with quasi-Euclidean steps v, v*sqrt(2), v*sqrt(3), capped at
- * d_max. Runs as one cooperative persistent kernel on `stream`. */
+ * d_max. Runs as one cooperative persistent kernel on `stream`: each round stages the active
+ * blocks with their one-voxel halos in shared memory and relaxes them to local convergence. */
 vbx_status vbx_update_esdf(vbx_map_t map, void* stream);
 
 /* Distance and gradient queries (the planner's interface, Sec. VII; trilinear interpolation

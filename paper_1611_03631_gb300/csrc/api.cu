@@ -125,9 +125,12 @@ struct vbx_map_s {
   vbx_map_options opt{};
   float voxel_size = 0, truncation = 0, max_esdf_dist = 0;
   int B = 0;
+  vbx::DevMap* d_dev = nullptr;   // device copy of d (kernels that take map arrays read it)
+  vbx::EsdfCtl* ctl_dev = nullptr;  // ESDF control block of this map's own updates
   int64_t pts_cap = 0;
   int64_t last_points_in = 0;
   uint32_t gtab_entries = 0;
+  uint64_t version = 0;  // bumped whenever d (and so d_dev) changes
   std::vector<void*> allocs;
   MapHook hook;
 
@@ -192,6 +195,11 @@ vbx_status ensure_scratch(vbx_map_t m, int64_t n, cudaStream_t s) {
   m->pts_cap = cap;
   e = vbx::launch_init_groups(m->d.gtab, entries, s, &m->hook);
   if (e != cudaSuccess) return cuda_fail(e, "group table init");
+  if (m->d_dev) {
+    e = cudaMemcpy(m->d_dev, &m->d, sizeof(vbx::DevMap), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "device map descriptor");
+  }
+  m->version += 1;
   return VBX_OK;
 }
 
@@ -213,8 +221,8 @@ vbx_status vbx_create_map(float voxel_size, int voxels_per_block, float truncati
   *out = nullptr;
   if (!(voxel_size > 0.0f) || !std::isfinite(voxel_size))
     return fail(VBX_ERR_INVALID_ARG, "voxel_size must be a positive finite number");
-  if (voxels_per_block != 4 && voxels_per_block != 8 && voxels_per_block != 16 && voxels_per_block != 32)
-    return fail(VBX_ERR_INVALID_ARG, "voxels_per_block must be 4, 8, 16 or 32");
+  if (voxels_per_block != 4 && voxels_per_block != 8 && voxels_per_block != 16)
+    return fail(VBX_ERR_INVALID_ARG, "voxels_per_block must be 4, 8 or 16");
   if (!(truncation >= voxel_size) || !(truncation <= 64.0f * voxel_size))
     return fail(VBX_ERR_INVALID_ARG, "truncation must lie in [voxel_size, 64 * voxel_size]");
   if (!(max_esdf_dist > 0.0f) || !std::isfinite(max_esdf_dist))
@@ -287,21 +295,39 @@ vbx_status vbx_create_map(float voxel_size, int voxels_per_block, float truncati
   VBX_ALLOC(d.btouch, (size_t)cap, 0);
   VBX_ALLOC(d.esdf, V, 0);
   VBX_ALLOC(d.vflags, V, 0);
-  VBX_ALLOC(d.stamp_r, V, 0);
-  VBX_ALLOC(d.stamp_l, V, 0);
+  VBX_ALLOC(d.rbits0, V / 32, 0);
+  VBX_ALLOC(d.rbits1, V / 32, 0);
+  VBX_ALLOC(d.lbits0, V / 32, 0);
+  VBX_ALLOC(d.lbits1, V / 32, 0);
+  VBX_ALLOC(d.bstamp_r, (size_t)cap, 0);
+  VBX_ALLOC(d.bstamp_l, (size_t)cap, 0);
   VBX_ALLOC(d.updated, V, 0);
   VBX_ALLOC(d.dirty, V, 0);
   VBX_ALLOC(d.newblk, (size_t)cap, 0);
-  VBX_ALLOC(d.rfront0, V, 0);
-  VBX_ALLOC(d.rfront1, V, 0);
-  VBX_ALLOC(d.lfront0, V, 0);
-  VBX_ALLOC(d.lfront1, V, 0);
   VBX_ALLOC(d.ctr, 1, 0);
+  VBX_ALLOC(m->d_dev, 1, 0);
+  VBX_ALLOC(m->ctl_dev, 1, 0);
+  {
+    vbx::EsdfCtl ctl{};
+    ctl.cap = (unsigned)cap;
+    VBX_ALLOC(ctl.ract0, (size_t)cap, 0);
+    VBX_ALLOC(ctl.ract1, (size_t)cap, 0);
+    VBX_ALLOC(ctl.lact0, (size_t)cap, 0);
+    VBX_ALLOC(ctl.lact1, (size_t)cap, 0);
+    if ((e = cudaMemcpy(m->ctl_dev, &ctl, sizeof(ctl), cudaMemcpyHostToDevice)) != cudaSuccess) {
+      delete m;
+      return cuda_fail(e, "esdf control block");
+    }
+  }
 #undef VBX_ALLOC
   vbx_status st = ensure_scratch(m, opt.max_points > 0 ? opt.max_points : (int64_t(1) << 20), 0);
   if (st != VBX_OK) {
     delete m;
     return st;
+  }
+  if ((e = cudaMemcpy(m->d_dev, &m->d, sizeof(vbx::DevMap), cudaMemcpyHostToDevice)) != cudaSuccess) {
+    delete m;
+    return cuda_fail(e, "device map descriptor");
   }
   e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
@@ -368,10 +394,12 @@ vbx_status vbx_integrate_scan_noalloc(vbx_map_t m, const float* points_dev, int6
 vbx_status vbx_update_esdf(vbx_map_t m, void* stream) {
   if (!m) return fail(VBX_ERR_INVALID_ARG, "map is NULL");
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t off = offsetof(vbx::Counters, rc);
+  const size_t off = offsetof(vbx::Counters, raise_rounds);
   cudaError_t e = cudaMemsetAsync((char*)m->d.ctr + off, 0, sizeof(vbx::Counters) - off, s);
   if (e != cudaSuccess) return cuda_fail(e, "reset esdf counters");
-  e = vbx::launch_esdf(m->d, m->cfg(stream), &m->hook);
+  e = cudaMemsetAsync(m->ctl_dev, 0, offsetof(vbx::EsdfCtl, cap), s);
+  if (e != cudaSuccess) return cuda_fail(e, "reset esdf control");
+  e = vbx::launch_esdf(m->d_dev, 1, m->B, m->ctl_dev, m->cfg(stream), &m->hook);
   if (e != cudaSuccess) return cuda_fail(e, "esdf cooperative launch");
   return VBX_OK;
 }

@@ -1,22 +1,23 @@
 // esdf.cu -- incremental ESDF update from the updated TSDF voxels (Sec. V-A, Algorithm 1 of
-// Oleynikova et al. 2017), as one cooperative persistent kernel:
+// Oleynikova et al. 2017), as one cooperative persistent kernel over a group of maps:
 //   A6 classify : every TSDF voxel updated since the last call takes one branch of the first
 //                 loop of Algorithm 1 (fixed band |D| < gamma, leaving the band, new voxel,
 //                 sign flip) and seeds the raise and lower frontiers
-//   A7 raise    : synchronous rounds (one warp per popped voxel, one lane per direction);
-//                 a popped non-fixed voxel is reset to +-d_max, its
-//                 children (neighbours whose parent direction points back at it) form the
-//                 next raise frontier and all other observed neighbours join the lower frontier
-//   A8 lower    : synchronous rounds; each popped voxel (one warp, one lane per direction)
-//                 relaxes its observed, non-fixed,
-//                 same-sign 26-neighbours with quasi-Euclidean steps; the neighbour's
-//                 {distance, parent} word is lowered with a 64-bit atomicMin whose high half
-//                 is the float's bit pattern (monotone in |d| for a fixed sign)
-// The paper processes the open set with a priority queue or a FIFO; synchronous frontier
-// rounds reach the same fixpoint (the lower wave computes the greatest fixpoint below the
-// post-raise values of a monotone relaxation, which does not depend on the processing
-// order). Frontier pushes are de-duplicated per round with monotone epoch stamps and
-// appended with one atomic per coalesced warp group.
+//   A7 raise    : global rounds over active blocks; a CTA stages one block and its one-voxel
+//                 halo in shared memory and raises within the block until no child is left
+//                 there: a raised non-fixed voxel is reset to +-d_max, neighbours whose parent
+//                 direction points back at it are raised next, all other observed neighbours
+//                 join the lower frontier; children in the halo are raised in the next round
+//   A8 lower    : global rounds over active blocks; the CTA relaxes the staged block to local
+//                 convergence (observed, non-fixed, same-sign 26-neighbours, quasi-Euclidean
+//                 steps, 64-bit atomicMin on {distance bits, flags, parent} in shared memory),
+//                 then writes every changed voxel back with a global 64-bit atomicMin; halo
+//                 voxels that improved are pushed to their own block for the next round
+// Frontiers are per-voxel bitmasks (current / next) plus lists of active (map, block) pairs
+// de-duplicated per round with monotone epoch stamps. The paper processes the open set with a
+// priority queue or a FIFO; any processing order reaches the same fixpoint (after the raise
+// phase the lower wave computes the greatest fixpoint below the current values of a monotone
+// relaxation), so the block-staged rounds give the batch-recompute result.
 #include <cooperative_groups.h>
 #include <cstdlib>
 #include <cuda_runtime.h>
@@ -32,15 +33,44 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr unsigned kMaxRounds = 1u << 16;
+constexpr int kMaxLocalIters = 1 << 15;
 
-// Appends vid to a frontier unless it is already in the frontier of this epoch.
-__device__ __forceinline__ void push(uint32_t* buf, unsigned* count, uint32_t* stamps, uint32_t vid, unsigned epoch) {
-  if (atomicMax(&stamps[vid], epoch) >= epoch) return;
-  cg::coalesced_group g = cg::coalesced_threads();
-  unsigned base = 0;
-  if (g.thread_rank() == 0) base = atomicAdd(count, g.size());
-  base = g.shfl(base, 0);
-  buf[base + g.thread_rank()] = vid;
+// Shared-memory layout of one staged block of edge B (tile edge T = B + 2).
+struct Tile {
+  unsigned long long* w;  // T^3 ESDF words, halo included
+  uint16_t* a;            // active interior voxels (local index), current
+  uint16_t* b;            // active interior voxels, next
+  uint32_t* in;           // B^3 bits: already queued for the next local iteration
+  uint32_t* chg;          // T^3 bits: word changed in this block-round
+  uint32_t* nslot;        // 27 pool slots of the block and its neighbours
+  unsigned* cnt;          // [0] current count, [1] next count
+};
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+__host__ __device__ inline size_t tile_bytes(int B) {
+  const size_t T = B + 2, T3 = T * T * T, B3 = (size_t)B * B * B;
+  return align16(T3 * 8) + align16(B3 * 2) * 2 + align16(B3 / 8) + align16((T3 + 31) / 32 * 4) + align16(27 * 4) + 16;
+}
+
+__device__ inline Tile carve(unsigned char* base, int B) {
+  const size_t T = B + 2, T3 = T * T * T, B3 = (size_t)B * B * B;
+  Tile t;
+  size_t off = 0;
+  t.w = reinterpret_cast<unsigned long long*>(base + off);
+  off += align16(T3 * 8);
+  t.a = reinterpret_cast<uint16_t*>(base + off);
+  off += align16(B3 * 2);
+  t.b = reinterpret_cast<uint16_t*>(base + off);
+  off += align16(B3 * 2);
+  t.in = reinterpret_cast<uint32_t*>(base + off);
+  off += align16(B3 / 8);
+  t.chg = reinterpret_cast<uint32_t*>(base + off);
+  off += align16((T3 + 31) / 32 * 4);
+  t.nslot = reinterpret_cast<uint32_t*>(base + off);
+  off += align16(27 * 4);
+  t.cnt = reinterpret_cast<unsigned*>(base + off);
+  return t;
 }
 
 __device__ __forceinline__ float step_len(const DevMap& m, int k) {
@@ -48,23 +78,274 @@ __device__ __forceinline__ float step_len(const DevMap& m, int k) {
   return n1 == 1 ? m.L1 : (n1 == 2 ? m.L2 : m.L3);
 }
 
-__global__ void __launch_bounds__(kThreads) k_esdf(DevMap m) {
-  Counters* c = m.ctr;
+__device__ __forceinline__ void set_bit(uint32_t* bits, uint32_t i) { atomicOr(&bits[i >> 5], 1u << (i & 31)); }
+
+// Puts (map, block) on an active list unless it is already there for this epoch.
+__device__ __forceinline__ void activate(uint2* list, unsigned* count, uint32_t* stamps, uint32_t slot, unsigned epoch,
+                                         unsigned mi) {
+  if (atomicMax(&stamps[slot], epoch) >= epoch) return;
+  const unsigned i = atomicAdd(count, 1u);
+  list[i] = make_uint2(mi, slot);
+}
+
+// Voxel id of tile cell c (coordinates -1..B per axis); kInvalid if its block does not exist.
+__device__ __forceinline__ uint32_t cell_vid(const DevMap& m, const Tile& t, int c, uint32_t* slot_out) {
+  const int B = m.B, T = B + 2;
+  int x = c % T - 1, y = (c / T) % T - 1, z = c / (T * T) - 1;
+  const int bx = x < 0 ? -1 : (x >= B ? 1 : 0);
+  const int by = y < 0 ? -1 : (y >= B ? 1 : 0);
+  const int bz = z < 0 ? -1 : (z >= B ? 1 : 0);
+  const uint32_t s = t.nslot[(bx + 1) * 9 + (by + 1) * 3 + (bz + 1)];
+  *slot_out = s;
+  if (s == kInvalid) return kInvalid;
+  x -= bx * B;
+  y -= by * B;
+  z -= bz * B;
+  return (s << m.b3log) | (uint32_t)((((z << m.blog) | y) << m.blog) | x);
+}
+
+__device__ __forceinline__ bool cell_interior(int c, int B) {
+  const int T = B + 2;
+  const int x = c % T - 1, y = (c / T) % T - 1, z = c / (T * T) - 1;
+  return x >= 0 && x < B && y >= 0 && y < B && z >= 0 && z < B;
+}
+
+__device__ __forceinline__ int interior_cell(int l, int B) {
+  const int T = B + 2;
+  const int x = l % B, y = (l / B) % B, z = l / (B * B);
+  return ((z + 1) * T + (y + 1)) * T + (x + 1);
+}
+
+__device__ __forceinline__ int interior_local(int c, int B) {
+  const int T = B + 2;
+  const int x = c % T - 1, y = (c / T) % T - 1, z = c / (T * T) - 1;
+  return (z * B + y) * B + x;
+}
+
+__device__ __forceinline__ int dir_offset(int k, int T) { return (k % 3 - 1) * T * T + ((k / 3) % 3 - 1) * T + (k / 9 - 1); }
+
+// Stages block `slot` of map m: its words with the one-voxel halo, and the current frontier
+// bits of its interior (cleared in global memory, appended to the active list).
+__device__ void stage_block(const DevMap& m, uint32_t slot, uint32_t* cur_bits, const Tile& t) {
+  const int B = m.B, T = B + 2, T3 = T * T * T, B3 = B * B * B;
+  if (threadIdx.x < 27) t.nslot[threadIdx.x] = threadIdx.x == 13 ? slot : __ldcg(&m.nbr[(size_t)slot * 27 + threadIdx.x]);
+  if (threadIdx.x < 2) t.cnt[threadIdx.x] = 0u;
+  for (int i = threadIdx.x; i < (T3 + 31) / 32; i += blockDim.x) t.chg[i] = 0u;
+  for (int i = threadIdx.x; i < B3 / 32; i += blockDim.x) t.in[i] = 0u;
+  __syncthreads();
+  for (int c = threadIdx.x; c < T3; c += blockDim.x) {
+    uint32_t s;
+    const uint32_t vid = cell_vid(m, t, c, &s);
+    t.w[c] = vid == kInvalid ? 0ull : __ldcg(&m.esdf[vid]);
+  }
+  uint32_t* bits = cur_bits + ((size_t)slot << m.b3log) / 32;
+  for (int j = threadIdx.x; j < B3 / 32; j += blockDim.x) {
+    uint32_t w = __ldcg(&bits[j]);
+    if (!w) continue;
+    bits[j] = 0u;
+    while (w) {
+      const int bit = __ffs(w) - 1;
+      w &= w - 1;
+      const unsigned i = atomicAdd(&t.cnt[0], 1u);
+      t.a[i] = (uint16_t)(j * 32 + bit);
+    }
+  }
+  __syncthreads();
+}
+
+struct RoundArgs {
+  unsigned mi;       // map index in the group
+  unsigned ep_next;  // activation epoch of the next round
+  unsigned e0;       // epoch of the frontiers seeded by classification
+  uint32_t* nxt_bits;
+  uint2* nxt_list;
+  unsigned* nxt_cnt;
+};
+
+// A7 for one staged block (all threads of the CTA).
+__device__ void raise_block(const DevMap& m, uint32_t slot, uint32_t* cur_bits, const RoundArgs& ra, EsdfCtl* ctl,
+                            unsigned char* smem, unsigned long long* pops) {
+  const int B = m.B, T = B + 2, T3 = T * T * T;
+  const Tile t = carve(smem, B);
+  stage_block(m, slot, cur_bits, t);
+  uint16_t* cur = t.a;
+  uint16_t* nxt = t.b;
+  const float dmax = m.dmax;
+  for (int it = 0;; ++it) {
+    const unsigned na = t.cnt[0];
+    if (na == 0) break;
+    if (it > kMaxLocalIters) {
+      if (threadIdx.x == 0) atomicOr(&ctl->error, kErrTimeout);
+      break;
+    }
+    for (unsigned i = threadIdx.x; i < na; i += blockDim.x) {
+      const int c = interior_cell(cur[i], B);
+      const unsigned long long w = t.w[c];
+      const unsigned fl = ew_flags(w);
+      if (!(fl & kFixed)) {
+        t.w[c] = ew_pack(ew_d(w) < 0.0f ? -dmax : dmax, fl, kNoParent);
+        atomicOr(&t.chg[c >> 5], 1u << (c & 31));
+      }
+    }
+    if (threadIdx.x == 0) *pops += na;
+    __syncthreads();
+    for (unsigned p = threadIdx.x; p < na * 26u; p += blockDim.x) {
+      const unsigned i = p / 26u;
+      const int kk = (int)(p % 26u);
+      const int k = kk < 13 ? kk : kk + 1;
+      const int c = interior_cell(cur[i], B);
+      const int nc = c + dir_offset(k, T);
+      const unsigned long long nw = t.w[nc];
+      const unsigned nfl = ew_flags(nw);
+      if (!(nfl & kObserved)) continue;
+      if (!(nfl & kFixed) && ew_parent(nw) == (unsigned)(26 - k)) {  // a child: raise it
+        if (cell_interior(nc, B)) {
+          const int nl = interior_local(nc, B);
+          const uint32_t bit = 1u << (nl & 31);
+          if (!(atomicOr(&t.in[nl >> 5], bit) & bit)) nxt[atomicAdd(&t.cnt[1], 1u)] = (uint16_t)nl;
+        } else {
+          uint32_t s;
+          const uint32_t nvid = cell_vid(m, t, nc, &s);
+          set_bit(ra.nxt_bits, nvid);
+          activate(ra.nxt_list, ra.nxt_cnt, m.bstamp_r, s, ra.ep_next, ra.mi);
+        }
+      } else {  // any other observed neighbour re-seeds the lower wave
+        uint32_t s;
+        const uint32_t nvid = cell_vid(m, t, nc, &s);
+        set_bit(m.lbits0, nvid);
+        activate(ctl->lact0, &ctl->lcnt[0], m.bstamp_l, s, ra.e0, ra.mi);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      t.cnt[0] = t.cnt[1];
+      t.cnt[1] = 0u;
+    }
+    uint16_t* tmp = cur;
+    cur = nxt;
+    nxt = tmp;
+    __syncthreads();
+  }
+  // write back the raised voxels (raise rounds never lower words, plain stores suffice)
+  for (int c = threadIdx.x; c < T3; c += blockDim.x) {
+    if (!(t.chg[c >> 5] & (1u << (c & 31)))) continue;
+    uint32_t s;
+    const uint32_t vid = cell_vid(m, t, c, &s);
+    m.esdf[vid] = t.w[c];
+  }
+  __syncthreads();
+}
+
+// A8 for one staged block (all threads of the CTA).
+__device__ void lower_block(const DevMap& m, uint32_t slot, uint32_t* cur_bits, const RoundArgs& ra, EsdfCtl* ctl,
+                            unsigned char* smem, unsigned long long* pops) {
+  const int B = m.B, T = B + 2, T3 = T * T * T, B3 = B * B * B;
+  const Tile t = carve(smem, B);
+  stage_block(m, slot, cur_bits, t);
+  uint16_t* cur = t.a;
+  uint16_t* nxt = t.b;
+  for (int it = 0;; ++it) {
+    const unsigned na = t.cnt[0];
+    if (na == 0) break;
+    if (it > kMaxLocalIters) {
+      if (threadIdx.x == 0) atomicOr(&ctl->error, kErrTimeout);
+      break;
+    }
+    if (threadIdx.x == 0) *pops += na;
+    for (unsigned p = threadIdx.x; p < na * 26u; p += blockDim.x) {
+      const unsigned i = p / 26u;
+      const int kk = (int)(p % 26u);
+      const int k = kk < 13 ? kk : kk + 1;
+      const int c = interior_cell(cur[i], B);
+      const unsigned long long w = t.w[c];
+      if (!(ew_flags(w) & kObserved)) continue;
+      const float dv = ew_d(w);
+      const bool neg = dv < 0.0f;
+      const int nc = c + dir_offset(k, T);
+      const unsigned long long nw = t.w[nc];
+      const unsigned nfl = ew_flags(nw);
+      if ((nfl & (kObserved | kFixed)) != kObserved) continue;
+      const float dn = ew_d(nw);
+      if ((dn < 0.0f) != neg) continue;
+      const float cand = __fadd_rn(fabsf(dv), step_len(m, k));
+      if (!(cand < fabsf(dn))) continue;
+      const unsigned long long old = atomicMin(&t.w[nc], ew_pack(neg ? -cand : cand, nfl, (unsigned)(26 - k)));
+      if (!(fabsf(ew_d(old)) > cand)) continue;
+      atomicOr(&t.chg[nc >> 5], 1u << (nc & 31));
+      if (cell_interior(nc, B)) {
+        const int nl = interior_local(nc, B);
+        const uint32_t bit = 1u << (nl & 31);
+        if (!(atomicOr(&t.in[nl >> 5], bit) & bit)) nxt[atomicAdd(&t.cnt[1], 1u)] = (uint16_t)nl;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      t.cnt[0] = t.cnt[1];
+      t.cnt[1] = 0u;
+    }
+    for (int j = threadIdx.x; j < B3 / 32; j += blockDim.x) t.in[j] = 0u;
+    uint16_t* tmp = cur;
+    cur = nxt;
+    nxt = tmp;
+    __syncthreads();
+  }
+  // write back: the global word keeps the smaller value; a halo voxel that improved is pushed
+  // to its own block for the next round
+  for (int c = threadIdx.x; c < T3; c += blockDim.x) {
+    if (!(t.chg[c >> 5] & (1u << (c & 31)))) continue;
+    uint32_t s;
+    const uint32_t vid = cell_vid(m, t, c, &s);
+    const unsigned long long nw = t.w[c];
+    const unsigned long long old = atomicMin(&m.esdf[vid], nw);
+    if (!cell_interior(c, B) && fabsf(ew_d(old)) > fabsf(ew_d(nw))) {
+      set_bit(ra.nxt_bits, vid);
+      activate(ra.nxt_list, ra.nxt_cnt, m.bstamp_l, s, ra.ep_next, ra.mi);
+    }
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ unsigned upper_index(const unsigned* pfx, int n, unsigned i) {
+  // largest mi with pfx[mi] <= i
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pfx[mid] <= i)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return (unsigned)lo;
+}
+
+__global__ void __launch_bounds__(kThreads) k_esdf(const DevMap* __restrict__ maps, int nmaps, EsdfCtl* ctl) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ unsigned pfx[kMaxBatch + 1];
+  __shared__ unsigned long long cta_pops;
   const unsigned tid = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned nthreads = gridDim.x * blockDim.x;
-  const unsigned lane = threadIdx.x & 31u;
-  const unsigned gwarp = tid >> 5, nwarps = nthreads >> 5;
-  const int kdir = lane < 13 ? (int)lane : (int)lane + 1;  // lanes 0..25 -> the 26 directions
-  const float klen = lane < 26 ? step_len(m, kdir) : 0.0f;
-  const unsigned base = __ldcg(&c->epoch);
-  const unsigned e0 = base + 1;  // epoch of the frontiers seeded by classification
-  const float dmax = m.dmax;
 
   // ---------------------------------------------------------------- A6: classification
-  const unsigned nd = __ldcg(&c->ndirty);
-  unsigned seeds = 0;
-  for (unsigned i = tid; i < nd; i += nthreads) {
-    const uint32_t vid = m.dirty[i];
+  // exclusive prefix of the maps' dirty counts (Hillis-Steele scan in shared memory)
+  {
+    const unsigned v = (int)threadIdx.x < nmaps ? __ldcg(&maps[threadIdx.x].ctr->ndirty) : 0u;
+    pfx[threadIdx.x + 1] = v;
+    if (threadIdx.x == 0) pfx[0] = 0u;
+    __syncthreads();
+    for (int off = 1; off < kMaxBatch; off <<= 1) {
+      const unsigned add = (int)threadIdx.x >= off ? pfx[threadIdx.x + 1 - off] : 0u;
+      __syncthreads();
+      pfx[threadIdx.x + 1] += add;
+      __syncthreads();
+    }
+  }
+  const unsigned total = pfx[nmaps];
+  for (unsigned i = tid; i < total; i += nthreads) {
+    const unsigned mi = upper_index(pfx, nmaps, i);
+    const DevMap& m = maps[mi];
+    const uint32_t vid = m.dirty[i - pfx[mi]];
+    const unsigned e0 = __ldcg(&m.ctr->epoch) + 1;
+    const float dmax = m.dmax;
     m.vflags[vid] = (uint8_t)(m.vflags[vid] & ~kQueuedForEsdf);
     const float2 t = m.tsdf[vid];
     if (!(t.y > 0.0f)) continue;
@@ -75,145 +356,132 @@ __global__ void __launch_bounds__(kThreads) k_esdf(DevMap m) {
     const unsigned fl = ew_flags(w);
     const bool obs = (fl & kObserved) != 0;
     const float de = ew_d(w);
+    const uint32_t slot = vid >> m.b3log;
     if (fabsf(Df) < m.gamma) {  // isFixed, evaluated on the TSDF voxel
-      ++seeds;
+      atomicAdd(&m.ctr->seeds, 1u);
       const bool lower_only = !obs || (((de < 0.0f) == neg) && fabsf(Df) <= fabsf(de));
       m.esdf[vid] = ew_pack(Df, kObserved | kFixed, kNoParent);
-      if (!lower_only) push(m.rfront0, &c->rc[0], m.stamp_r, vid, e0);
-      push(m.lfront0, &c->lc[0], m.stamp_l, vid, e0);
+      if (!lower_only) {
+        set_bit(m.rbits0, vid);
+        activate(ctl->ract0, &ctl->rcnt[0], m.bstamp_r, slot, e0, mi);
+      }
+      set_bit(m.lbits0, vid);
+      activate(ctl->lact0, &ctl->lcnt[0], m.bstamp_l, slot, e0, mi);
     } else if (fl & kFixed) {  // leaves the fixed band
       m.esdf[vid] = ew_pack(sdmax, kObserved, kNoParent);
-      push(m.rfront0, &c->rc[0], m.stamp_r, vid, e0);
+      set_bit(m.rbits0, vid);
+      activate(ctl->ract0, &ctl->rcnt[0], m.bstamp_r, slot, e0, mi);
     } else if (!obs) {  // newly observed: its observed neighbours will lower it
       m.esdf[vid] = ew_pack(sdmax, kObserved, kNoParent);
       for (int k = 0; k < 27; ++k) {
         if (k == 13) continue;
         const uint32_t n = neighbor_vid(m, vid, k);
         if (n == kInvalid) continue;
-        if (ew_flags(__ldcg(&m.esdf[n])) & kObserved) push(m.lfront0, &c->lc[0], m.stamp_l, n, e0);
+        if (ew_flags(__ldcg(&m.esdf[n])) & kObserved) {
+          set_bit(m.lbits0, n);
+          activate(ctl->lact0, &ctl->lcnt[0], m.bstamp_l, n >> m.b3log, e0, mi);
+        }
       }
     } else if ((de < 0.0f) != neg) {  // sign flip of a propagated voxel
       m.esdf[vid] = ew_pack(sdmax, kObserved, kNoParent);
-      push(m.rfront0, &c->rc[0], m.stamp_r, vid, e0);
+      set_bit(m.rbits0, vid);
+      activate(ctl->ract0, &ctl->rcnt[0], m.bstamp_r, slot, e0, mi);
     }
   }
-  if (seeds) atomicAdd(&c->seeds, seeds);
-  if (!grid_barrier(&c->bar, gridDim.x, &c->error)) return;
+  if (!grid_barrier(&ctl->bar, gridDim.x, &ctl->error)) return;
 
   // ------------------------------------------------------------------------ A7: raise
-  unsigned long long pops = 0;
   unsigned r = 0;
   for (;; ++r) {
-    const unsigned cnt = __ldcg(&c->rc[r % 3]);
-    if (cnt == 0 || (__ldcg(&c->error) & kErrTimeout)) break;
+    const unsigned cnt = __ldcg(&ctl->rcnt[r % 3]);
+    if (cnt == 0 || __ldcg(&ctl->error)) break;
     if (r >= kMaxRounds) {
-      if (tid == 0) atomicOr(&c->error, kErrTimeout);
+      if (tid == 0) atomicOr(&ctl->error, kErrTimeout);
       break;
     }
-    if (tid == 0) c->rc[(r + 2) % 3] = 0;
-    const uint32_t* cur = (r & 1) ? m.rfront1 : m.rfront0;
-    uint32_t* nxt = (r & 1) ? m.rfront0 : m.rfront1;
-    unsigned* ncnt = &c->rc[(r + 1) % 3];
-    const unsigned ep = base + 2 + r;
-    for (unsigned i = gwarp; i < cnt; i += nwarps) {  // one warp per voxel, one lane per direction
-      const uint32_t vid = cur[i];
-      const unsigned long long w = __ldcg(&m.esdf[vid]);
-      const unsigned fl = ew_flags(w);
-      if (lane == 0) {
-        ++pops;
-        if (!(fl & kFixed)) m.esdf[vid] = ew_pack(ew_d(w) < 0.0f ? -dmax : dmax, fl, kNoParent);
-      }
-      if (lane < 26) {
-        const uint32_t n = neighbor_vid(m, vid, kdir);
-        if (n != kInvalid) {
-          const unsigned long long nw = __ldcg(&m.esdf[n]);
-          const unsigned nfl = ew_flags(nw);
-          if (nfl & kObserved) {
-            if (!(nfl & kFixed) && ew_parent(nw) == (unsigned)(26 - kdir))
-              push(nxt, ncnt, m.stamp_r, n, ep);
-            else
-              push(m.lfront0, &c->lc[0], m.stamp_l, n, e0);
-          }
-        }
-      }
+    if (tid == 0) ctl->rcnt[(r + 2) % 3] = 0;
+    const uint2* cur = (r & 1) ? ctl->ract1 : ctl->ract0;
+    for (unsigned item = blockIdx.x; item < cnt; item += gridDim.x) {
+      const uint2 e = cur[item];
+      const DevMap& m = maps[e.x];
+      RoundArgs ra;
+      ra.mi = e.x;
+      ra.e0 = __ldcg(&m.ctr->epoch) + 1;
+      ra.ep_next = ra.e0 + 1 + r;
+      ra.nxt_bits = (r & 1) ? m.rbits0 : m.rbits1;
+      ra.nxt_list = (r & 1) ? ctl->ract0 : ctl->ract1;
+      ra.nxt_cnt = &ctl->rcnt[(r + 1) % 3];
+      if (threadIdx.x == 0) cta_pops = 0;
+      raise_block(m, e.y, (r & 1) ? m.rbits1 : m.rbits0, ra, ctl, dsm, &cta_pops);
+      if (threadIdx.x == 0 && cta_pops) atomicAdd(&m.ctr->raise_pops, cta_pops);
     }
-    if (!grid_barrier(&c->bar, gridDim.x, &c->error)) return;
+    if (!grid_barrier(&ctl->bar, gridDim.x, &ctl->error)) return;
   }
   const unsigned raise_rounds = r;
-  if (pops) atomicAdd(&c->raise_pops, pops);
 
   // ------------------------------------------------------------------------ A8: lower
-  pops = 0;
   unsigned l = 0;
   for (;; ++l) {
-    const unsigned cnt = __ldcg(&c->lc[l % 3]);
-    if (cnt == 0 || (__ldcg(&c->error) & kErrTimeout)) break;
+    const unsigned cnt = __ldcg(&ctl->lcnt[l % 3]);
+    if (cnt == 0 || __ldcg(&ctl->error)) break;
     if (l >= kMaxRounds) {
-      if (tid == 0) atomicOr(&c->error, kErrTimeout);
+      if (tid == 0) atomicOr(&ctl->error, kErrTimeout);
       break;
     }
-    if (tid == 0) c->lc[(l + 2) % 3] = 0;
-    const uint32_t* cur = (l & 1) ? m.lfront1 : m.lfront0;
-    uint32_t* nxt = (l & 1) ? m.lfront0 : m.lfront1;
-    unsigned* ncnt = &c->lc[(l + 1) % 3];
-    const unsigned ep = base + 2 + l;
-    for (unsigned i = gwarp; i < cnt; i += nwarps) {  // one warp per voxel, one lane per direction
-      const uint32_t vid = cur[i];
-      const unsigned long long w = __ldcg(&m.esdf[vid]);
-      if (!(ew_flags(w) & kObserved)) continue;
-      if (lane == 0) ++pops;
-      if (lane >= 26) continue;
-      const float dv = ew_d(w);
-      const bool neg = dv < 0.0f;
-      const uint32_t n = neighbor_vid(m, vid, kdir);
-      if (n == kInvalid) continue;
-      const unsigned long long nw = __ldcg(&m.esdf[n]);
-      const unsigned nfl = ew_flags(nw);
-      if ((nfl & (kObserved | kFixed)) != kObserved) continue;
-      const float dn = ew_d(nw);
-      if ((dn < 0.0f) != neg) continue;
-      const float cand = __fadd_rn(fabsf(dv), klen);
-      if (cand < fabsf(dn)) {
-        const unsigned long long old = atomicMin(&m.esdf[n], ew_pack(neg ? -cand : cand, nfl, (unsigned)(26 - kdir)));
-        if (fabsf(ew_d(old)) > cand) push(nxt, ncnt, m.stamp_l, n, ep);
-      }
+    if (tid == 0) ctl->lcnt[(l + 2) % 3] = 0;
+    const uint2* cur = (l & 1) ? ctl->lact1 : ctl->lact0;
+    for (unsigned item = blockIdx.x; item < cnt; item += gridDim.x) {
+      const uint2 e = cur[item];
+      const DevMap& m = maps[e.x];
+      RoundArgs ra;
+      ra.mi = e.x;
+      ra.e0 = __ldcg(&m.ctr->epoch) + 1;
+      ra.ep_next = ra.e0 + 1 + l;
+      ra.nxt_bits = (l & 1) ? m.lbits0 : m.lbits1;
+      ra.nxt_list = (l & 1) ? ctl->lact0 : ctl->lact1;
+      ra.nxt_cnt = &ctl->lcnt[(l + 1) % 3];
+      if (threadIdx.x == 0) cta_pops = 0;
+      lower_block(m, e.y, (l & 1) ? m.lbits1 : m.lbits0, ra, ctl, dsm, &cta_pops);
+      if (threadIdx.x == 0 && cta_pops) atomicAdd(&m.ctr->lower_pops, cta_pops);
     }
-    if (!grid_barrier(&c->bar, gridDim.x, &c->error)) return;
+    if (!grid_barrier(&ctl->bar, gridDim.x, &ctl->error)) return;
   }
-  if (pops) atomicAdd(&c->lower_pops, pops);
-  if (tid == 0) {
-    c->esdf_in = nd;
+  for (unsigned i = tid; i < (unsigned)nmaps; i += nthreads) {
+    Counters* c = maps[i].ctr;
+    c->esdf_in = pfx[i + 1] - pfx[i];
     c->raise_rounds = raise_rounds;
     c->lower_rounds = l;
-    c->epoch = base + 3 + (raise_rounds > l ? raise_rounds : l);
+    c->epoch = c->epoch + 3 + (raise_rounds > l ? raise_rounds : l);
     c->ndirty = 0;
+    if (__ldcg(&ctl->error) & kErrTimeout) atomicOr(&c->error, kErrTimeout);
   }
 }
 
 }  // namespace
 
-int esdf_max_blocks_per_sm() {
+size_t esdf_smem_bytes(int max_B) { return tile_bytes(max_B); }
+
+int esdf_grid(int num_sms, int max_B) {
+  const size_t smem = tile_bytes(max_B);
+  if (cudaFuncSetAttribute(k_esdf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_esdf, kThreads, 0) != cudaSuccess) return 0;
-  return nb;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_esdf, kThreads, smem) != cudaSuccess) return 0;
+  // resident CTAs per SM of the cooperative grid: 2 by default, VBX_ESDF_CTAS_PER_SM to tune
+  int want = 2;
+  if (const char* e = getenv("VBX_ESDF_CTAS_PER_SM")) want = atoi(e) > 0 ? atoi(e) : want;
+  if (nb > want) nb = want;
+  return nb * num_sms;
 }
 
-cudaError_t launch_esdf(const DevMap& m, const LaunchCfg& cfg, LaunchHook* hook) {
-  static int per_sm = -1;
-  if (per_sm < 0) {
-    per_sm = esdf_max_blocks_per_sm();
-    // resident CTAs per SM of the cooperative grid: 2 by default (fastest of 1, 2, 4 on the
-    // room workload), VBX_ESDF_CTAS_PER_SM to tune
-    int want = 2;
-    if (const char* e = getenv("VBX_ESDF_CTAS_PER_SM")) want = atoi(e) > 0 ? atoi(e) : want;
-    if (per_sm > want) per_sm = want;
-  }
-  if (per_sm <= 0) return cudaErrorCooperativeLaunchTooLarge;
-  dim3 grid(cfg.num_sms * per_sm), block(kThreads);
-  DevMap arg = m;
-  void* args[] = {&arg};
+cudaError_t launch_esdf(const DevMap* maps_dev, int nmaps, int max_B, EsdfCtl* ctl, const LaunchCfg& cfg,
+                        LaunchHook* hook) {
+  if (nmaps <= 0 || nmaps > kMaxBatch) return cudaErrorInvalidValue;
+  const int grid = esdf_grid(cfg.num_sms, max_B);
+  if (grid <= 0) return cudaErrorCooperativeLaunchTooLarge;
+  const size_t smem = tile_bytes(max_B);
+  void* args[] = {(void*)&maps_dev, (void*)&nmaps, (void*)&ctl};
   hook->begin(kKEsdf, cfg.stream);
-  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_esdf, grid, block, args, 0, cfg.stream);
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_esdf, dim3(grid), dim3(kThreads), args, smem, cfg.stream);
   hook->end(kKEsdf, cfg.stream);
   return e;
 }

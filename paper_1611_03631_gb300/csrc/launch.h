@@ -51,8 +51,12 @@ cudaError_t launch_integrate_noalloc(const DevMap& m, void* scratch, const float
 cudaError_t launch_import(const DevMap& m, const int* vox, const float* D, const float* W, int n,
                           const LaunchCfg& cfg, LaunchHook* hook);
 
-// esdf.cu
-cudaError_t launch_esdf(const DevMap& m, const LaunchCfg& cfg, LaunchHook* hook);
+// esdf.cu: one cooperative launch updates the ESDF of nmaps maps (device array of DevMap)
+constexpr int kMaxBatch = 256;  // maps per ESDF launch (one prefix entry per thread)
+size_t esdf_smem_bytes(int max_B);
+int esdf_grid(int num_sms, int max_B);
+cudaError_t launch_esdf(const DevMap* maps_dev, int nmaps, int max_B, EsdfCtl* ctl, const LaunchCfg& cfg,
+                        LaunchHook* hook);
 
 // query.cu
 cudaError_t launch_query(const DevMap& m, const float* q, int n, float* dist, float* grad, unsigned char* status,

@@ -12,8 +12,10 @@
 //                    touch[vid]  u32 flag: the voxel received a record in the current scan
 //                    esdf[vid]   u64 packed {d f32 | flags u8 | parent u8} 8 B
 //                    vflags[vid] u8 (bit0 queued for the ESDF)
-//                    stamp_r/stamp_l[vid] u32 frontier de-duplication epochs
-//   lists          : updated (last scan), dirty (since last ESDF), 2+2 frontier buffers
+//                    rbits/lbits[2][vid/32] u32 raise / lower frontier bitmasks (current, next)
+//   per block      : bstamp_r/bstamp_l[slot] u32 epochs de-duplicating block activations
+//   lists          : updated (last scan), dirty (since last ESDF); the ESDF's active
+//                    (map, block) lists live in the launch group's EsdfCtl
 //   per-scan scratch: group hash table (64 B entries), group list, rays (float4)
 #pragma once
 
@@ -73,15 +75,28 @@ struct Counters {
   unsigned int ndirty;
   unsigned int epoch;
   // ---- per ESDF update (cleared by vbx_update_esdf)
-  unsigned int rc[3];
-  unsigned int lc[3];
   unsigned int raise_rounds;
   unsigned int lower_rounds;
   unsigned long long raise_pops;
   unsigned long long lower_pops;
   unsigned int seeds;
   unsigned int esdf_in;
+};
+
+// Control block of one ESDF launch: one map, or a batch of maps updated by the same
+// cooperative kernel. Active lists hold (map index, block slot) pairs; counts rotate over
+// three slots so that the count of the next round can be cleared while the current one is
+// read.
+struct EsdfCtl {
   GridBarrier bar;
+  unsigned int rcnt[3];
+  unsigned int lcnt[3];
+  unsigned int error;
+  unsigned int cap;  // capacity of each active list
+  uint2* ract0;
+  uint2* ract1;
+  uint2* lact0;
+  uint2* lact1;
 };
 
 struct DevMap {
@@ -106,16 +121,16 @@ struct DevMap {
   uint32_t* btouch;
   unsigned long long* esdf;
   uint8_t* vflags;
-  uint32_t* stamp_r;
-  uint32_t* stamp_l;
+  uint32_t* rbits0;
+  uint32_t* rbits1;
+  uint32_t* lbits0;
+  uint32_t* lbits1;
+  uint32_t* bstamp_r;
+  uint32_t* bstamp_l;
   // lists
   uint32_t* updated;
   uint32_t* dirty;
   uint32_t* newblk;
-  uint32_t* rfront0;
-  uint32_t* rfront1;
-  uint32_t* lfront0;
-  uint32_t* lfront1;
   // per-scan scratch
   GroupEntry* gtab;
   uint32_t gmask;
