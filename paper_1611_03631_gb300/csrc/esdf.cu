@@ -73,11 +73,6 @@ __device__ inline Tile carve(unsigned char* base, int B) {
   return t;
 }
 
-__device__ __forceinline__ float step_len(const DevMap& m, int k) {
-  const int n1 = (k / 9 != 1) + ((k / 3) % 3 != 1) + (k % 3 != 1);
-  return n1 == 1 ? m.L1 : (n1 == 2 ? m.L2 : m.L3);
-}
-
 __device__ __forceinline__ void set_bit(uint32_t* bits, uint32_t i) { atomicOr(&bits[i >> 5], 1u << (i & 31)); }
 
 // Puts (map, block) on an active list unless it is already there for this epoch.
@@ -88,10 +83,26 @@ __device__ __forceinline__ void activate(uint2* list, unsigned* count, uint32_t*
   list[i] = make_uint2(mi, slot);
 }
 
+// ---- block-local helpers, templated on the block edge B (tile edge T = B + 2) so that all
+// index arithmetic is by compile-time constants
+
+template <int B>
+struct Geo {
+  static constexpr int T = B + 2;
+  static constexpr int T3 = T * T * T;
+  static constexpr int B3 = B * B * B;
+  static constexpr int LOG = B == 4 ? 2 : (B == 8 ? 3 : 4);
+  __device__ static __forceinline__ int cell_of_local(int l) {
+    return (((l >> (2 * LOG)) + 1) * T + (((l >> LOG) & (B - 1)) + 1)) * T + ((l & (B - 1)) + 1);
+  }
+  __device__ static __forceinline__ int off(int k) { return (k % 3 - 1) * T * T + ((k / 3) % 3 - 1) * T + (k / 9 - 1); }
+};
+
 // Voxel id of tile cell c (coordinates -1..B per axis); kInvalid if its block does not exist.
-__device__ __forceinline__ uint32_t cell_vid(const DevMap& m, const Tile& t, int c, uint32_t* slot_out) {
-  const int B = m.B, T = B + 2;
-  int x = c % T - 1, y = (c / T) % T - 1, z = c / (T * T) - 1;
+template <int B>
+__device__ __forceinline__ uint32_t cell_vid(const Tile& t, int c, uint32_t* slot_out) {
+  using G = Geo<B>;
+  int x = c % G::T - 1, y = (c / G::T) % G::T - 1, z = c / (G::T * G::T) - 1;
   const int bx = x < 0 ? -1 : (x >= B ? 1 : 0);
   const int by = y < 0 ? -1 : (y >= B ? 1 : 0);
   const int bz = z < 0 ? -1 : (z >= B ? 1 : 0);
@@ -101,53 +112,50 @@ __device__ __forceinline__ uint32_t cell_vid(const DevMap& m, const Tile& t, int
   x -= bx * B;
   y -= by * B;
   z -= bz * B;
-  return (s << m.b3log) | (uint32_t)((((z << m.blog) | y) << m.blog) | x);
+  return (s << (3 * G::LOG)) | (uint32_t)((((z << G::LOG) | y) << G::LOG) | x);
 }
 
-__device__ __forceinline__ bool cell_interior(int c, int B) {
-  const int T = B + 2;
-  const int x = c % T - 1, y = (c / T) % T - 1, z = c / (T * T) - 1;
-  return x >= 0 && x < B && y >= 0 && y < B && z >= 0 && z < B;
+template <int B>
+__device__ __forceinline__ bool cell_interior(int c) {
+  using G = Geo<B>;
+  const int x = c % G::T - 1, y = (c / G::T) % G::T - 1, z = c / (G::T * G::T) - 1;
+  return (unsigned)x < (unsigned)B && (unsigned)y < (unsigned)B && (unsigned)z < (unsigned)B;
 }
 
-__device__ __forceinline__ int interior_cell(int l, int B) {
-  const int T = B + 2;
-  const int x = l % B, y = (l / B) % B, z = l / (B * B);
-  return ((z + 1) * T + (y + 1)) * T + (x + 1);
+template <int B>
+__device__ __forceinline__ int interior_local(int c) {
+  using G = Geo<B>;
+  const int x = c % G::T - 1, y = (c / G::T) % G::T - 1, z = c / (G::T * G::T) - 1;
+  return (((z << G::LOG) | y) << G::LOG) | x;
 }
-
-__device__ __forceinline__ int interior_local(int c, int B) {
-  const int T = B + 2;
-  const int x = c % T - 1, y = (c / T) % T - 1, z = c / (T * T) - 1;
-  return (z * B + y) * B + x;
-}
-
-__device__ __forceinline__ int dir_offset(int k, int T) { return (k % 3 - 1) * T * T + ((k / 3) % 3 - 1) * T + (k / 9 - 1); }
 
 // Stages block `slot` of map m: its words with the one-voxel halo, and the current frontier
 // bits of its interior (cleared in global memory, appended to the active list).
+template <int B>
 __device__ void stage_block(const DevMap& m, uint32_t slot, uint32_t* cur_bits, const Tile& t) {
-  const int B = m.B, T = B + 2, T3 = T * T * T, B3 = B * B * B;
+  using G = Geo<B>;
   if (threadIdx.x < 27) t.nslot[threadIdx.x] = threadIdx.x == 13 ? slot : __ldcg(&m.nbr[(size_t)slot * 27 + threadIdx.x]);
   if (threadIdx.x < 2) t.cnt[threadIdx.x] = 0u;
-  for (int i = threadIdx.x; i < (T3 + 31) / 32; i += blockDim.x) t.chg[i] = 0u;
-  for (int i = threadIdx.x; i < B3 / 32; i += blockDim.x) t.in[i] = 0u;
+  for (int i = threadIdx.x; i < (G::T3 + 31) / 32; i += blockDim.x) t.chg[i] = 0u;
+  for (int i = threadIdx.x; i < G::B3 / 32; i += blockDim.x) t.in[i] = 0u;
   __syncthreads();
-  for (int c = threadIdx.x; c < T3; c += blockDim.x) {
+#pragma unroll 4
+  for (int c = threadIdx.x; c < G::T3; c += kThreads) {
     uint32_t s;
-    const uint32_t vid = cell_vid(m, t, c, &s);
+    const uint32_t vid = cell_vid<B>(t, c, &s);
     t.w[c] = vid == kInvalid ? 0ull : __ldcg(&m.esdf[vid]);
   }
-  uint32_t* bits = cur_bits + ((size_t)slot << m.b3log) / 32;
-  for (int j = threadIdx.x; j < B3 / 32; j += blockDim.x) {
+  uint32_t* bits = cur_bits + ((size_t)slot << (3 * G::LOG)) / 32;
+  for (int j = threadIdx.x; j < G::B3 / 32; j += blockDim.x) {
     uint32_t w = __ldcg(&bits[j]);
     if (!w) continue;
     bits[j] = 0u;
+    const unsigned base = atomicAdd(&t.cnt[0], (unsigned)__popc(w));
+    unsigned i = base;
     while (w) {
       const int bit = __ffs(w) - 1;
       w &= w - 1;
-      const unsigned i = atomicAdd(&t.cnt[0], 1u);
-      t.a[i] = (uint16_t)(j * 32 + bit);
+      t.a[i++] = (uint16_t)(j * 32 + bit);
     }
   }
   __syncthreads();
@@ -162,12 +170,13 @@ struct RoundArgs {
   unsigned* nxt_cnt;
 };
 
-// A7 for one staged block (all threads of the CTA).
+// A7 for one staged block (all threads of the CTA; one thread per active voxel).
+template <int B>
 __device__ void raise_block(const DevMap& m, uint32_t slot, uint32_t* cur_bits, const RoundArgs& ra, EsdfCtl* ctl,
                             unsigned char* smem, unsigned long long* pops) {
-  const int B = m.B, T = B + 2, T3 = T * T * T;
+  using G = Geo<B>;
   const Tile t = carve(smem, B);
-  stage_block(m, slot, cur_bits, t);
+  stage_block<B>(m, slot, cur_bits, t);
   uint16_t* cur = t.a;
   uint16_t* nxt = t.b;
   const float dmax = m.dmax;
@@ -178,8 +187,10 @@ __device__ void raise_block(const DevMap& m, uint32_t slot, uint32_t* cur_bits, 
       if (threadIdx.x == 0) atomicOr(&ctl->error, kErrTimeout);
       break;
     }
-    for (unsigned i = threadIdx.x; i < na; i += blockDim.x) {
-      const int c = interior_cell(cur[i], B);
+    if (threadIdx.x == 0) *pops += na;
+    // reset the raised voxels first, so that no child test below sees a stale parent
+    for (unsigned i = threadIdx.x; i < na; i += kThreads) {
+      const int c = G::cell_of_local(cur[i]);
       const unsigned long long w = t.w[c];
       const unsigned fl = ew_flags(w);
       if (!(fl & kFixed)) {
@@ -187,33 +198,33 @@ __device__ void raise_block(const DevMap& m, uint32_t slot, uint32_t* cur_bits, 
         atomicOr(&t.chg[c >> 5], 1u << (c & 31));
       }
     }
-    if (threadIdx.x == 0) *pops += na;
     __syncthreads();
-    for (unsigned p = threadIdx.x; p < na * 26u; p += blockDim.x) {
-      const unsigned i = p / 26u;
-      const int kk = (int)(p % 26u);
-      const int k = kk < 13 ? kk : kk + 1;
-      const int c = interior_cell(cur[i], B);
-      const int nc = c + dir_offset(k, T);
-      const unsigned long long nw = t.w[nc];
-      const unsigned nfl = ew_flags(nw);
-      if (!(nfl & kObserved)) continue;
-      if (!(nfl & kFixed) && ew_parent(nw) == (unsigned)(26 - k)) {  // a child: raise it
-        if (cell_interior(nc, B)) {
-          const int nl = interior_local(nc, B);
-          const uint32_t bit = 1u << (nl & 31);
-          if (!(atomicOr(&t.in[nl >> 5], bit) & bit)) nxt[atomicAdd(&t.cnt[1], 1u)] = (uint16_t)nl;
-        } else {
+    for (unsigned i = threadIdx.x; i < na; i += kThreads) {
+      const int c = G::cell_of_local(cur[i]);
+#pragma unroll
+      for (int kk = 0; kk < 26; ++kk) {
+        const int k = kk < 13 ? kk : kk + 1;
+        const int nc = c + G::off(k);
+        const unsigned long long nw = t.w[nc];
+        const unsigned nfl = ew_flags(nw);
+        if (!(nfl & kObserved)) continue;
+        if (!(nfl & kFixed) && ew_parent(nw) == (unsigned)(26 - k)) {  // a child: raise it
+          if (cell_interior<B>(nc)) {
+            const int nl = interior_local<B>(nc);
+            const uint32_t bit = 1u << (nl & 31);
+            if (!(atomicOr(&t.in[nl >> 5], bit) & bit)) nxt[atomicAdd(&t.cnt[1], 1u)] = (uint16_t)nl;
+          } else {
+            uint32_t s;
+            const uint32_t nvid = cell_vid<B>(t, nc, &s);
+            set_bit(ra.nxt_bits, nvid);
+            activate(ra.nxt_list, ra.nxt_cnt, m.bstamp_r, s, ra.ep_next, ra.mi);
+          }
+        } else {  // any other observed neighbour re-seeds the lower wave
           uint32_t s;
-          const uint32_t nvid = cell_vid(m, t, nc, &s);
-          set_bit(ra.nxt_bits, nvid);
-          activate(ra.nxt_list, ra.nxt_cnt, m.bstamp_r, s, ra.ep_next, ra.mi);
+          const uint32_t nvid = cell_vid<B>(t, nc, &s);
+          set_bit(m.lbits0, nvid);
+          activate(ctl->lact0, &ctl->lcnt[0], m.bstamp_l, s, ra.e0, ra.mi);
         }
-      } else {  // any other observed neighbour re-seeds the lower wave
-        uint32_t s;
-        const uint32_t nvid = cell_vid(m, t, nc, &s);
-        set_bit(m.lbits0, nvid);
-        activate(ctl->lact0, &ctl->lcnt[0], m.bstamp_l, s, ra.e0, ra.mi);
       }
     }
     __syncthreads();
@@ -227,23 +238,25 @@ __device__ void raise_block(const DevMap& m, uint32_t slot, uint32_t* cur_bits, 
     __syncthreads();
   }
   // write back the raised voxels (raise rounds never lower words, plain stores suffice)
-  for (int c = threadIdx.x; c < T3; c += blockDim.x) {
+  for (int c = threadIdx.x; c < G::T3; c += kThreads) {
     if (!(t.chg[c >> 5] & (1u << (c & 31)))) continue;
     uint32_t s;
-    const uint32_t vid = cell_vid(m, t, c, &s);
+    const uint32_t vid = cell_vid<B>(t, c, &s);
     m.esdf[vid] = t.w[c];
   }
   __syncthreads();
 }
 
-// A8 for one staged block (all threads of the CTA).
+// A8 for one staged block (all threads of the CTA; one thread per active voxel).
+template <int B>
 __device__ void lower_block(const DevMap& m, uint32_t slot, uint32_t* cur_bits, const RoundArgs& ra, EsdfCtl* ctl,
                             unsigned char* smem, unsigned long long* pops) {
-  const int B = m.B, T = B + 2, T3 = T * T * T, B3 = B * B * B;
+  using G = Geo<B>;
   const Tile t = carve(smem, B);
-  stage_block(m, slot, cur_bits, t);
+  stage_block<B>(m, slot, cur_bits, t);
   uint16_t* cur = t.a;
   uint16_t* nxt = t.b;
+  const float L1 = m.L1, L2 = m.L2, L3 = m.L3;
   for (int it = 0;; ++it) {
     const unsigned na = t.cnt[0];
     if (na == 0) break;
@@ -252,30 +265,33 @@ __device__ void lower_block(const DevMap& m, uint32_t slot, uint32_t* cur_bits, 
       break;
     }
     if (threadIdx.x == 0) *pops += na;
-    for (unsigned p = threadIdx.x; p < na * 26u; p += blockDim.x) {
-      const unsigned i = p / 26u;
-      const int kk = (int)(p % 26u);
-      const int k = kk < 13 ? kk : kk + 1;
-      const int c = interior_cell(cur[i], B);
+    for (unsigned i = threadIdx.x; i < na; i += kThreads) {
+      const int c = G::cell_of_local(cur[i]);
       const unsigned long long w = t.w[c];
       if (!(ew_flags(w) & kObserved)) continue;
       const float dv = ew_d(w);
       const bool neg = dv < 0.0f;
-      const int nc = c + dir_offset(k, T);
-      const unsigned long long nw = t.w[nc];
-      const unsigned nfl = ew_flags(nw);
-      if ((nfl & (kObserved | kFixed)) != kObserved) continue;
-      const float dn = ew_d(nw);
-      if ((dn < 0.0f) != neg) continue;
-      const float cand = __fadd_rn(fabsf(dv), step_len(m, k));
-      if (!(cand < fabsf(dn))) continue;
-      const unsigned long long old = atomicMin(&t.w[nc], ew_pack(neg ? -cand : cand, nfl, (unsigned)(26 - k)));
-      if (!(fabsf(ew_d(old)) > cand)) continue;
-      atomicOr(&t.chg[nc >> 5], 1u << (nc & 31));
-      if (cell_interior(nc, B)) {
-        const int nl = interior_local(nc, B);
-        const uint32_t bit = 1u << (nl & 31);
-        if (!(atomicOr(&t.in[nl >> 5], bit) & bit)) nxt[atomicAdd(&t.cnt[1], 1u)] = (uint16_t)nl;
+      const float av = fabsf(dv);
+#pragma unroll
+      for (int kk = 0; kk < 26; ++kk) {
+        const int k = kk < 13 ? kk : kk + 1;
+        const int n1 = (k / 9 != 1) + ((k / 3) % 3 != 1) + (k % 3 != 1);
+        const int nc = c + G::off(k);
+        const unsigned long long nw = t.w[nc];
+        const unsigned nfl = ew_flags(nw);
+        if ((nfl & (kObserved | kFixed)) != kObserved) continue;
+        const float dn = ew_d(nw);
+        if ((dn < 0.0f) != neg) continue;
+        const float cand = __fadd_rn(av, n1 == 1 ? L1 : (n1 == 2 ? L2 : L3));
+        if (!(cand < fabsf(dn))) continue;
+        const unsigned long long old = atomicMin(&t.w[nc], ew_pack(neg ? -cand : cand, nfl, (unsigned)(26 - k)));
+        if (!(fabsf(ew_d(old)) > cand)) continue;
+        atomicOr(&t.chg[nc >> 5], 1u << (nc & 31));
+        if (cell_interior<B>(nc)) {
+          const int nl = interior_local<B>(nc);
+          const uint32_t bit = 1u << (nl & 31);
+          if (!(atomicOr(&t.in[nl >> 5], bit) & bit)) nxt[atomicAdd(&t.cnt[1], 1u)] = (uint16_t)nl;
+        }
       }
     }
     __syncthreads();
@@ -283,7 +299,7 @@ __device__ void lower_block(const DevMap& m, uint32_t slot, uint32_t* cur_bits, 
       t.cnt[0] = t.cnt[1];
       t.cnt[1] = 0u;
     }
-    for (int j = threadIdx.x; j < B3 / 32; j += blockDim.x) t.in[j] = 0u;
+    for (int j = threadIdx.x; j < G::B3 / 32; j += kThreads) t.in[j] = 0u;
     uint16_t* tmp = cur;
     cur = nxt;
     nxt = tmp;
@@ -291,18 +307,36 @@ __device__ void lower_block(const DevMap& m, uint32_t slot, uint32_t* cur_bits, 
   }
   // write back: the global word keeps the smaller value; a halo voxel that improved is pushed
   // to its own block for the next round
-  for (int c = threadIdx.x; c < T3; c += blockDim.x) {
+  for (int c = threadIdx.x; c < G::T3; c += kThreads) {
     if (!(t.chg[c >> 5] & (1u << (c & 31)))) continue;
     uint32_t s;
-    const uint32_t vid = cell_vid(m, t, c, &s);
+    const uint32_t vid = cell_vid<B>(t, c, &s);
     const unsigned long long nw = t.w[c];
     const unsigned long long old = atomicMin(&m.esdf[vid], nw);
-    if (!cell_interior(c, B) && fabsf(ew_d(old)) > fabsf(ew_d(nw))) {
+    if (!cell_interior<B>(c) && fabsf(ew_d(old)) > fabsf(ew_d(nw))) {
       set_bit(ra.nxt_bits, vid);
       activate(ra.nxt_list, ra.nxt_cnt, m.bstamp_l, s, ra.ep_next, ra.mi);
     }
   }
   __syncthreads();
+}
+
+__device__ __forceinline__ void raise_dispatch(const DevMap& m, uint32_t slot, uint32_t* cur_bits, const RoundArgs& ra,
+                                               EsdfCtl* ctl, unsigned char* smem, unsigned long long* pops) {
+  switch (m.B) {
+    case 4: raise_block<4>(m, slot, cur_bits, ra, ctl, smem, pops); break;
+    case 8: raise_block<8>(m, slot, cur_bits, ra, ctl, smem, pops); break;
+    default: raise_block<16>(m, slot, cur_bits, ra, ctl, smem, pops); break;
+  }
+}
+
+__device__ __forceinline__ void lower_dispatch(const DevMap& m, uint32_t slot, uint32_t* cur_bits, const RoundArgs& ra,
+                                               EsdfCtl* ctl, unsigned char* smem, unsigned long long* pops) {
+  switch (m.B) {
+    case 4: lower_block<4>(m, slot, cur_bits, ra, ctl, smem, pops); break;
+    case 8: lower_block<8>(m, slot, cur_bits, ra, ctl, smem, pops); break;
+    default: lower_block<16>(m, slot, cur_bits, ra, ctl, smem, pops); break;
+  }
 }
 
 __device__ __forceinline__ unsigned upper_index(const unsigned* pfx, int n, unsigned i) {
@@ -412,7 +446,7 @@ __global__ void __launch_bounds__(kThreads) k_esdf(const DevMap* __restrict__ ma
       ra.nxt_list = (r & 1) ? ctl->ract0 : ctl->ract1;
       ra.nxt_cnt = &ctl->rcnt[(r + 1) % 3];
       if (threadIdx.x == 0) cta_pops = 0;
-      raise_block(m, e.y, (r & 1) ? m.rbits1 : m.rbits0, ra, ctl, dsm, &cta_pops);
+      raise_dispatch(m, e.y, (r & 1) ? m.rbits1 : m.rbits0, ra, ctl, dsm, &cta_pops);
       if (threadIdx.x == 0 && cta_pops) atomicAdd(&m.ctr->raise_pops, cta_pops);
     }
     if (!grid_barrier(&ctl->bar, gridDim.x, &ctl->error)) return;
@@ -441,7 +475,7 @@ __global__ void __launch_bounds__(kThreads) k_esdf(const DevMap* __restrict__ ma
       ra.nxt_list = (l & 1) ? ctl->lact0 : ctl->lact1;
       ra.nxt_cnt = &ctl->lcnt[(l + 1) % 3];
       if (threadIdx.x == 0) cta_pops = 0;
-      lower_block(m, e.y, (l & 1) ? m.lbits1 : m.lbits0, ra, ctl, dsm, &cta_pops);
+      lower_dispatch(m, e.y, (l & 1) ? m.lbits1 : m.lbits0, ra, ctl, dsm, &cta_pops);
       if (threadIdx.x == 0 && cta_pops) atomicAdd(&m.ctr->lower_pops, cta_pops);
     }
     if (!grid_barrier(&ctl->bar, gridDim.x, &ctl->error)) return;
