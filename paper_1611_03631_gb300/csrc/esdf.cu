@@ -43,7 +43,9 @@ struct Tile {
   uint32_t* in;           // B^3 bits: already queued for the next local iteration
   uint32_t* chg;          // T^3 bits: word changed in this block-round
   uint32_t* nslot;        // 27 pool slots of the block and its neighbours
-  unsigned* cnt;          // [0] current count, [1] next count
+  unsigned* cnt;          // [0] current count, [1] next count, [2] blocks to activate in the
+                          // next-round list, [3] blocks whose lower frontier was seeded (bit k =
+                          // neighbour direction k)
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -51,6 +53,15 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(
 __host__ __device__ inline size_t tile_bytes(int B) {
   const size_t T = B + 2, T3 = T * T * T, B3 = (size_t)B * B * B;
   return align16(T3 * 8) + align16(B3 * 2) * 2 + align16(B3 / 8) + align16((T3 + 31) / 32 * 4) + align16(27 * 4) + 16;
+}
+
+// Appends v to a shared-memory list with one atomic per coalesced group of lanes.
+__device__ __forceinline__ void smem_append(uint16_t* list, unsigned* count, uint16_t v) {
+  cg::coalesced_group g = cg::coalesced_threads();
+  unsigned base = 0;
+  if (g.thread_rank() == 0) base = atomicAdd(count, g.size());
+  base = g.shfl(base, 0);
+  list[base + g.thread_rank()] = v;
 }
 
 __device__ inline Tile carve(unsigned char* base, int B) {
@@ -78,6 +89,7 @@ __device__ __forceinline__ void set_bit(uint32_t* bits, uint32_t i) { atomicOr(&
 // Puts (map, block) on an active list unless it is already there for this epoch.
 __device__ __forceinline__ void activate(uint2* list, unsigned* count, uint32_t* stamps, uint32_t slot, unsigned epoch,
                                          unsigned mi) {
+  if (__ldcg(&stamps[slot]) >= epoch) return;
   if (atomicMax(&stamps[slot], epoch) >= epoch) return;
   const unsigned i = atomicAdd(count, 1u);
   list[i] = make_uint2(mi, slot);
@@ -116,6 +128,16 @@ __device__ __forceinline__ uint32_t cell_vid(const Tile& t, int c, uint32_t* slo
 }
 
 template <int B>
+__device__ __forceinline__ int cell_block_dir(int c) {
+  using G = Geo<B>;
+  const int x = c % G::T - 1, y = (c / G::T) % G::T - 1, z = c / (G::T * G::T) - 1;
+  const int bx = x < 0 ? -1 : (x >= B ? 1 : 0);
+  const int by = y < 0 ? -1 : (y >= B ? 1 : 0);
+  const int bz = z < 0 ? -1 : (z >= B ? 1 : 0);
+  return (bx + 1) * 9 + (by + 1) * 3 + (bz + 1);
+}
+
+template <int B>
 __device__ __forceinline__ bool cell_interior(int c) {
   using G = Geo<B>;
   const int x = c % G::T - 1, y = (c / G::T) % G::T - 1, z = c / (G::T * G::T) - 1;
@@ -135,7 +157,7 @@ template <int B>
 __device__ void stage_block(const DevMap& m, uint32_t slot, uint32_t* cur_bits, const Tile& t) {
   using G = Geo<B>;
   if (threadIdx.x < 27) t.nslot[threadIdx.x] = threadIdx.x == 13 ? slot : __ldcg(&m.nbr[(size_t)slot * 27 + threadIdx.x]);
-  if (threadIdx.x < 2) t.cnt[threadIdx.x] = 0u;
+  if (threadIdx.x < 4) t.cnt[threadIdx.x] = 0u;
   for (int i = threadIdx.x; i < (G::T3 + 31) / 32; i += blockDim.x) t.chg[i] = 0u;
   for (int i = threadIdx.x; i < G::B3 / 32; i += blockDim.x) t.in[i] = 0u;
   __syncthreads();
@@ -212,18 +234,18 @@ __device__ void raise_block(const DevMap& m, uint32_t slot, uint32_t* cur_bits, 
           if (cell_interior<B>(nc)) {
             const int nl = interior_local<B>(nc);
             const uint32_t bit = 1u << (nl & 31);
-            if (!(atomicOr(&t.in[nl >> 5], bit) & bit)) nxt[atomicAdd(&t.cnt[1], 1u)] = (uint16_t)nl;
+            if (!(atomicOr(&t.in[nl >> 5], bit) & bit)) smem_append(nxt, &t.cnt[1], (uint16_t)nl);
           } else {
             uint32_t s;
             const uint32_t nvid = cell_vid<B>(t, nc, &s);
             set_bit(ra.nxt_bits, nvid);
-            activate(ra.nxt_list, ra.nxt_cnt, m.bstamp_r, s, ra.ep_next, ra.mi);
+            atomicOr(&t.cnt[2], 1u << cell_block_dir<B>(nc));
           }
         } else {  // any other observed neighbour re-seeds the lower wave
           uint32_t s;
           const uint32_t nvid = cell_vid<B>(t, nc, &s);
           set_bit(m.lbits0, nvid);
-          activate(ctl->lact0, &ctl->lcnt[0], m.bstamp_l, s, ra.e0, ra.mi);
+          atomicOr(&t.cnt[3], 1u << cell_block_dir<B>(nc));
         }
       }
     }
@@ -243,6 +265,12 @@ __device__ void raise_block(const DevMap& m, uint32_t slot, uint32_t* cur_bits, 
     uint32_t s;
     const uint32_t vid = cell_vid<B>(t, c, &s);
     m.esdf[vid] = t.w[c];
+  }
+  // activate the blocks that received raise (next round) or lower (seed) frontier bits
+  if (threadIdx.x < 27) {
+    const uint32_t s = t.nslot[threadIdx.x];
+    if (s != kInvalid && (t.cnt[2] >> threadIdx.x & 1u)) activate(ra.nxt_list, ra.nxt_cnt, m.bstamp_r, s, ra.ep_next, ra.mi);
+    if (s != kInvalid && (t.cnt[3] >> threadIdx.x & 1u)) activate(ctl->lact0, &ctl->lcnt[0], m.bstamp_l, s, ra.e0, ra.mi);
   }
   __syncthreads();
 }
@@ -290,7 +318,7 @@ __device__ void lower_block(const DevMap& m, uint32_t slot, uint32_t* cur_bits, 
         if (cell_interior<B>(nc)) {
           const int nl = interior_local<B>(nc);
           const uint32_t bit = 1u << (nl & 31);
-          if (!(atomicOr(&t.in[nl >> 5], bit) & bit)) nxt[atomicAdd(&t.cnt[1], 1u)] = (uint16_t)nl;
+          if (!(atomicOr(&t.in[nl >> 5], bit) & bit)) smem_append(nxt, &t.cnt[1], (uint16_t)nl);
         }
       }
     }
@@ -305,18 +333,23 @@ __device__ void lower_block(const DevMap& m, uint32_t slot, uint32_t* cur_bits, 
     nxt = tmp;
     __syncthreads();
   }
-  // write back: the global word keeps the smaller value; a halo voxel that improved is pushed
-  // to its own block for the next round
+  // write back: the global word keeps the smaller value (fire-and-forget atomicMin); a halo
+  // voxel this block lowered is pushed to its own block for the next round (a push of a voxel
+  // that another block lowered even further is redundant work, never wrong)
   for (int c = threadIdx.x; c < G::T3; c += kThreads) {
     if (!(t.chg[c >> 5] & (1u << (c & 31)))) continue;
     uint32_t s;
     const uint32_t vid = cell_vid<B>(t, c, &s);
-    const unsigned long long nw = t.w[c];
-    const unsigned long long old = atomicMin(&m.esdf[vid], nw);
-    if (!cell_interior<B>(c) && fabsf(ew_d(old)) > fabsf(ew_d(nw))) {
+    atomicMin(&m.esdf[vid], t.w[c]);
+    if (!cell_interior<B>(c)) {
       set_bit(ra.nxt_bits, vid);
-      activate(ra.nxt_list, ra.nxt_cnt, m.bstamp_l, s, ra.ep_next, ra.mi);
+      atomicOr(&t.cnt[2], 1u << cell_block_dir<B>(c));
     }
+  }
+  __syncthreads();
+  if (threadIdx.x < 27) {
+    const uint32_t s = t.nslot[threadIdx.x];
+    if (s != kInvalid && (t.cnt[2] >> threadIdx.x & 1u)) activate(ra.nxt_list, ra.nxt_cnt, m.bstamp_l, s, ra.ep_next, ra.mi);
   }
   __syncthreads();
 }
@@ -407,13 +440,16 @@ __global__ void __launch_bounds__(kThreads) k_esdf(const DevMap* __restrict__ ma
       activate(ctl->ract0, &ctl->rcnt[0], m.bstamp_r, slot, e0, mi);
     } else if (!obs) {  // newly observed: its observed neighbours will lower it
       m.esdf[vid] = ew_pack(sdmax, kObserved, kNoParent);
+      uint32_t last = kInvalid;
       for (int k = 0; k < 27; ++k) {
         if (k == 13) continue;
         const uint32_t n = neighbor_vid(m, vid, k);
         if (n == kInvalid) continue;
         if (ew_flags(__ldcg(&m.esdf[n])) & kObserved) {
           set_bit(m.lbits0, n);
-          activate(ctl->lact0, &ctl->lcnt[0], m.bstamp_l, n >> m.b3log, e0, mi);
+          const uint32_t nb = n >> m.b3log;
+          if (nb != last) activate(ctl->lact0, &ctl->lcnt[0], m.bstamp_l, nb, e0, mi);
+          last = nb;
         }
       }
     } else if ((de < 0.0f) != neg) {  // sign flip of a propagated voxel
