@@ -265,7 +265,7 @@ def run_gpu(args):
     clocks = Clocks(local)
     clocks.start()
     launches0 = vbx.total_launches()
-    step_ms, tsdf_upd, esdf_upd, records, rounds = [], 0, 0, 0, 0
+    step_ms, tsdf_upd, esdf_upd, records, rounds, visits, liters = [], 0, 0, 0, 0, 0, 0
     for i in order[args.warmup:]:
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -280,6 +280,8 @@ def run_gpu(args):
         esdf_upd += st["raise_pops"] + st["lower_pops"]
         records += st["records"]
         rounds += st["raise_rounds"] + st["lower_rounds"]
+        visits += st["esdf_block_visits"]
+        liters += st["esdf_local_iters"]
     torch.cuda.synchronize()
     gpu_launches = vbx.total_launches() - launches0 - 0
     clk = clocks.stop()
@@ -408,6 +410,8 @@ def run_gpu(args):
             "ray_voxel_records": records * ws / secs / 1e6,
         },
         "esdf_rounds_per_scan": rounds / args.steps,
+        "esdf_block_visits_per_scan": visits / args.steps,
+        "esdf_local_iters_per_visit": liters / max(visits, 1),
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "scans/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

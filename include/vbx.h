@@ -129,6 +129,8 @@ typedef struct {
   int64_t raise_rounds;
   int64_t lower_rounds;
   int64_t launches;       /* kernels launched by this map since creation                    */
+  int64_t esdf_block_visits; /* blocks staged in shared memory by the last ESDF update       */
+  int64_t esdf_local_iters;  /* local relaxation iterations summed over those stagings       */
 } vbx_stats;
 
 /* Synchronises `stream`, then fills *out. Returns the sticky device error if one is set. */

@@ -442,6 +442,8 @@ vbx_status vbx_get_stats(vbx_map_t m, vbx_stats* out, void* stream) {
   out->raise_rounds = c.raise_rounds;
   out->lower_rounds = c.lower_rounds;
   out->launches = m->hook.launches;
+  out->esdf_block_visits = c.esdf_block_visits;
+  out->esdf_local_iters = c.esdf_local_iters;
   return read_error(m, (cudaStream_t)stream);
 }
 

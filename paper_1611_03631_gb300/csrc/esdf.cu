@@ -31,7 +31,7 @@ namespace vbx {
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
 constexpr unsigned kMaxRounds = 1u << 16;
 constexpr int kMaxLocalIters = 1 << 15;
 
@@ -40,19 +40,19 @@ struct Tile {
   unsigned long long* w;  // T^3 ESDF words, halo included
   uint16_t* a;            // active interior voxels (local index), current
   uint16_t* b;            // active interior voxels, next
-  uint32_t* in;           // B^3 bits: already queued for the next local iteration
+  uint32_t* in;           // 2 x B^3 bits: already queued for the next local iteration (by parity)
   uint32_t* chg;          // T^3 bits: word changed in this block-round
   uint32_t* nslot;        // 27 pool slots of the block and its neighbours
-  unsigned* cnt;          // [0] current count, [1] next count, [2] blocks to activate in the
-                          // next-round list, [3] blocks whose lower frontier was seeded (bit k =
-                          // neighbour direction k)
+  unsigned* cnt;          // [0..2] rotating list counts (read j%3, append (j+1)%3, clear
+                          // (j+2)%3), [3] blocks to activate in the next-round list, [4] blocks
+                          // whose lower frontier was seeded (bit k = neighbour direction k)
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 __host__ __device__ inline size_t tile_bytes(int B) {
   const size_t T = B + 2, T3 = T * T * T, B3 = (size_t)B * B * B;
-  return align16(T3 * 8) + align16(B3 * 2) * 2 + align16(B3 / 8) + align16((T3 + 31) / 32 * 4) + align16(27 * 4) + 16;
+  return align16(T3 * 8) + align16(B3 * 2) * 2 + align16(B3 / 4) + align16((T3 + 31) / 32 * 4) + align16(27 * 4) + 32;
 }
 
 // Appends v to a shared-memory list with one atomic per coalesced group of lanes.
@@ -75,7 +75,7 @@ __device__ inline Tile carve(unsigned char* base, int B) {
   t.b = reinterpret_cast<uint16_t*>(base + off);
   off += align16(B3 * 2);
   t.in = reinterpret_cast<uint32_t*>(base + off);
-  off += align16(B3 / 8);
+  off += align16(B3 / 4);
   t.chg = reinterpret_cast<uint32_t*>(base + off);
   off += align16((T3 + 31) / 32 * 4);
   t.nslot = reinterpret_cast<uint32_t*>(base + off);
@@ -157,9 +157,9 @@ template <int B>
 __device__ void stage_block(const DevMap& m, uint32_t slot, uint32_t* cur_bits, const Tile& t) {
   using G = Geo<B>;
   if (threadIdx.x < 27) t.nslot[threadIdx.x] = threadIdx.x == 13 ? slot : __ldcg(&m.nbr[(size_t)slot * 27 + threadIdx.x]);
-  if (threadIdx.x < 4) t.cnt[threadIdx.x] = 0u;
+  if (threadIdx.x < 8) t.cnt[threadIdx.x] = 0u;
   for (int i = threadIdx.x; i < (G::T3 + 31) / 32; i += blockDim.x) t.chg[i] = 0u;
-  for (int i = threadIdx.x; i < G::B3 / 32; i += blockDim.x) t.in[i] = 0u;
+  for (int i = threadIdx.x; i < G::B3 / 16; i += blockDim.x) t.in[i] = 0u;
   __syncthreads();
 #pragma unroll 4
   for (int c = threadIdx.x; c < G::T3; c += kThreads) {
@@ -199,17 +199,25 @@ __device__ void raise_block(const DevMap& m, uint32_t slot, uint32_t* cur_bits, 
   using G = Geo<B>;
   const Tile t = carve(smem, B);
   stage_block<B>(m, slot, cur_bits, t);
-  uint16_t* cur = t.a;
-  uint16_t* nxt = t.b;
   const float dmax = m.dmax;
+  unsigned iters = 0;
   for (int it = 0;; ++it) {
-    const unsigned na = t.cnt[0];
+    const unsigned na = t.cnt[it % 3];
     if (na == 0) break;
     if (it > kMaxLocalIters) {
       if (threadIdx.x == 0) atomicOr(&ctl->error, kErrTimeout);
       break;
     }
-    if (threadIdx.x == 0) *pops += na;
+    ++iters;
+    const uint16_t* cur = (it & 1) ? t.b : t.a;
+    uint16_t* nxt = (it & 1) ? t.a : t.b;
+    unsigned* ncnt = &t.cnt[(it + 1) % 3];
+    uint32_t* inb = t.in + (it & 1) * (G::B3 / 32);
+    if (threadIdx.x == 0) {
+      *pops += na;
+      t.cnt[(it + 2) % 3] = 0u;
+    }
+    for (int j = threadIdx.x; j < G::B3 / 32; j += kThreads) t.in[((it + 1) & 1) * (G::B3 / 32) + j] = 0u;
     // reset the raised voxels first, so that no child test below sees a stale parent
     for (unsigned i = threadIdx.x; i < na; i += kThreads) {
       const int c = G::cell_of_local(cur[i]);
@@ -221,44 +229,36 @@ __device__ void raise_block(const DevMap& m, uint32_t slot, uint32_t* cur_bits, 
       }
     }
     __syncthreads();
-    for (unsigned i = threadIdx.x; i < na; i += kThreads) {
+    for (unsigned p = threadIdx.x; p < na * 26u; p += kThreads) {
+      const unsigned i = p / 26u;
+      const int kk = (int)(p - i * 26u);
+      const int k = kk < 13 ? kk : kk + 1;
       const int c = G::cell_of_local(cur[i]);
-#pragma unroll
-      for (int kk = 0; kk < 26; ++kk) {
-        const int k = kk < 13 ? kk : kk + 1;
-        const int nc = c + G::off(k);
-        const unsigned long long nw = t.w[nc];
-        const unsigned nfl = ew_flags(nw);
-        if (!(nfl & kObserved)) continue;
-        if (!(nfl & kFixed) && ew_parent(nw) == (unsigned)(26 - k)) {  // a child: raise it
-          if (cell_interior<B>(nc)) {
-            const int nl = interior_local<B>(nc);
-            const uint32_t bit = 1u << (nl & 31);
-            if (!(atomicOr(&t.in[nl >> 5], bit) & bit)) smem_append(nxt, &t.cnt[1], (uint16_t)nl);
-          } else {
-            uint32_t s;
-            const uint32_t nvid = cell_vid<B>(t, nc, &s);
-            set_bit(ra.nxt_bits, nvid);
-            atomicOr(&t.cnt[2], 1u << cell_block_dir<B>(nc));
-          }
-        } else {  // any other observed neighbour re-seeds the lower wave
+      const int nc = c + G::off(k);
+      const unsigned long long nw = t.w[nc];
+      const unsigned nfl = ew_flags(nw);
+      if (!(nfl & kObserved)) continue;
+      if (!(nfl & kFixed) && ew_parent(nw) == (unsigned)(26 - k)) {  // a child: raise it
+        if (cell_interior<B>(nc)) {
+          const int nl = interior_local<B>(nc);
+          const uint32_t bit = 1u << (nl & 31);
+          if (!(atomicOr(&inb[nl >> 5], bit) & bit)) smem_append(nxt, ncnt, (uint16_t)nl);
+        } else {
           uint32_t s;
           const uint32_t nvid = cell_vid<B>(t, nc, &s);
-          set_bit(m.lbits0, nvid);
+          set_bit(ra.nxt_bits, nvid);
           atomicOr(&t.cnt[3], 1u << cell_block_dir<B>(nc));
         }
+      } else {  // any other observed neighbour re-seeds the lower wave
+        uint32_t s;
+        const uint32_t nvid = cell_vid<B>(t, nc, &s);
+        set_bit(m.lbits0, nvid);
+        atomicOr(&t.cnt[4], 1u << cell_block_dir<B>(nc));
       }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      t.cnt[0] = t.cnt[1];
-      t.cnt[1] = 0u;
-    }
-    uint16_t* tmp = cur;
-    cur = nxt;
-    nxt = tmp;
-    __syncthreads();
   }
+  if (threadIdx.x == 0) atomicAdd(&m.ctr->esdf_local_iters, iters);
   // write back the raised voxels (raise rounds never lower words, plain stores suffice)
   for (int c = threadIdx.x; c < G::T3; c += kThreads) {
     if (!(t.chg[c >> 5] & (1u << (c & 31)))) continue;
@@ -269,8 +269,8 @@ __device__ void raise_block(const DevMap& m, uint32_t slot, uint32_t* cur_bits, 
   // activate the blocks that received raise (next round) or lower (seed) frontier bits
   if (threadIdx.x < 27) {
     const uint32_t s = t.nslot[threadIdx.x];
-    if (s != kInvalid && (t.cnt[2] >> threadIdx.x & 1u)) activate(ra.nxt_list, ra.nxt_cnt, m.bstamp_r, s, ra.ep_next, ra.mi);
-    if (s != kInvalid && (t.cnt[3] >> threadIdx.x & 1u)) activate(ctl->lact0, &ctl->lcnt[0], m.bstamp_l, s, ra.e0, ra.mi);
+    if (s != kInvalid && (t.cnt[3] >> threadIdx.x & 1u)) activate(ra.nxt_list, ra.nxt_cnt, m.bstamp_r, s, ra.ep_next, ra.mi);
+    if (s != kInvalid && (t.cnt[4] >> threadIdx.x & 1u)) activate(ctl->lact0, &ctl->lcnt[0], m.bstamp_l, s, ra.e0, ra.mi);
   }
   __syncthreads();
 }
@@ -282,57 +282,55 @@ __device__ void lower_block(const DevMap& m, uint32_t slot, uint32_t* cur_bits, 
   using G = Geo<B>;
   const Tile t = carve(smem, B);
   stage_block<B>(m, slot, cur_bits, t);
-  uint16_t* cur = t.a;
-  uint16_t* nxt = t.b;
   const float L1 = m.L1, L2 = m.L2, L3 = m.L3;
+  unsigned iters = 0;
   for (int it = 0;; ++it) {
-    const unsigned na = t.cnt[0];
+    const unsigned na = t.cnt[it % 3];
     if (na == 0) break;
     if (it > kMaxLocalIters) {
       if (threadIdx.x == 0) atomicOr(&ctl->error, kErrTimeout);
       break;
     }
-    if (threadIdx.x == 0) *pops += na;
-    for (unsigned i = threadIdx.x; i < na; i += kThreads) {
+    ++iters;
+    const uint16_t* cur = (it & 1) ? t.b : t.a;
+    uint16_t* nxt = (it & 1) ? t.a : t.b;
+    unsigned* ncnt = &t.cnt[(it + 1) % 3];
+    uint32_t* inb = t.in + (it & 1) * (G::B3 / 32);
+    if (threadIdx.x == 0) {
+      *pops += na;
+      t.cnt[(it + 2) % 3] = 0u;
+    }
+    for (int j = threadIdx.x; j < G::B3 / 32; j += kThreads) t.in[((it + 1) & 1) * (G::B3 / 32) + j] = 0u;
+    for (unsigned p = threadIdx.x; p < na * 26u; p += kThreads) {
+      const unsigned i = p / 26u;
+      const int kk = (int)(p - i * 26u);
+      const int k = kk < 13 ? kk : kk + 1;
       const int c = G::cell_of_local(cur[i]);
       const unsigned long long w = t.w[c];
       if (!(ew_flags(w) & kObserved)) continue;
       const float dv = ew_d(w);
       const bool neg = dv < 0.0f;
-      const float av = fabsf(dv);
-#pragma unroll
-      for (int kk = 0; kk < 26; ++kk) {
-        const int k = kk < 13 ? kk : kk + 1;
-        const int n1 = (k / 9 != 1) + ((k / 3) % 3 != 1) + (k % 3 != 1);
-        const int nc = c + G::off(k);
-        const unsigned long long nw = t.w[nc];
-        const unsigned nfl = ew_flags(nw);
-        if ((nfl & (kObserved | kFixed)) != kObserved) continue;
-        const float dn = ew_d(nw);
-        if ((dn < 0.0f) != neg) continue;
-        const float cand = __fadd_rn(av, n1 == 1 ? L1 : (n1 == 2 ? L2 : L3));
-        if (!(cand < fabsf(dn))) continue;
-        const unsigned long long old = atomicMin(&t.w[nc], ew_pack(neg ? -cand : cand, nfl, (unsigned)(26 - k)));
-        if (!(fabsf(ew_d(old)) > cand)) continue;
-        atomicOr(&t.chg[nc >> 5], 1u << (nc & 31));
-        if (cell_interior<B>(nc)) {
-          const int nl = interior_local<B>(nc);
-          const uint32_t bit = 1u << (nl & 31);
-          if (!(atomicOr(&t.in[nl >> 5], bit) & bit)) smem_append(nxt, &t.cnt[1], (uint16_t)nl);
-        }
+      const int nc = c + G::off(k);
+      const unsigned long long nw = t.w[nc];
+      const unsigned nfl = ew_flags(nw);
+      if ((nfl & (kObserved | kFixed)) != kObserved) continue;
+      const float dn = ew_d(nw);
+      if ((dn < 0.0f) != neg) continue;
+      const int n1 = (k / 9 != 1) + ((k / 3) % 3 != 1) + (k % 3 != 1);
+      const float cand = __fadd_rn(fabsf(dv), n1 == 1 ? L1 : (n1 == 2 ? L2 : L3));
+      if (!(cand < fabsf(dn))) continue;
+      const unsigned long long old = atomicMin(&t.w[nc], ew_pack(neg ? -cand : cand, nfl, (unsigned)(26 - k)));
+      if (!(fabsf(ew_d(old)) > cand)) continue;
+      atomicOr(&t.chg[nc >> 5], 1u << (nc & 31));
+      if (cell_interior<B>(nc)) {
+        const int nl = interior_local<B>(nc);
+        const uint32_t bit = 1u << (nl & 31);
+        if (!(atomicOr(&inb[nl >> 5], bit) & bit)) smem_append(nxt, ncnt, (uint16_t)nl);
       }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      t.cnt[0] = t.cnt[1];
-      t.cnt[1] = 0u;
-    }
-    for (int j = threadIdx.x; j < G::B3 / 32; j += kThreads) t.in[j] = 0u;
-    uint16_t* tmp = cur;
-    cur = nxt;
-    nxt = tmp;
-    __syncthreads();
   }
+  if (threadIdx.x == 0) atomicAdd(&m.ctr->esdf_local_iters, iters);
   // write back: the global word keeps the smaller value (fire-and-forget atomicMin); a halo
   // voxel this block lowered is pushed to its own block for the next round (a push of a voxel
   // that another block lowered even further is redundant work, never wrong)
@@ -343,13 +341,13 @@ __device__ void lower_block(const DevMap& m, uint32_t slot, uint32_t* cur_bits, 
     atomicMin(&m.esdf[vid], t.w[c]);
     if (!cell_interior<B>(c)) {
       set_bit(ra.nxt_bits, vid);
-      atomicOr(&t.cnt[2], 1u << cell_block_dir<B>(c));
+      atomicOr(&t.cnt[3], 1u << cell_block_dir<B>(c));
     }
   }
   __syncthreads();
   if (threadIdx.x < 27) {
     const uint32_t s = t.nslot[threadIdx.x];
-    if (s != kInvalid && (t.cnt[2] >> threadIdx.x & 1u)) activate(ra.nxt_list, ra.nxt_cnt, m.bstamp_l, s, ra.ep_next, ra.mi);
+    if (s != kInvalid && (t.cnt[3] >> threadIdx.x & 1u)) activate(ra.nxt_list, ra.nxt_cnt, m.bstamp_l, s, ra.ep_next, ra.mi);
   }
   __syncthreads();
 }
@@ -395,14 +393,16 @@ __global__ void __launch_bounds__(kThreads) k_esdf(const DevMap* __restrict__ ma
   // ---------------------------------------------------------------- A6: classification
   // exclusive prefix of the maps' dirty counts (Hillis-Steele scan in shared memory)
   {
+    static_assert(kMaxBatch <= kThreads, "one prefix entry per thread");
+    const bool mine = threadIdx.x < kMaxBatch;
     const unsigned v = (int)threadIdx.x < nmaps ? __ldcg(&maps[threadIdx.x].ctr->ndirty) : 0u;
-    pfx[threadIdx.x + 1] = v;
+    if (mine) pfx[threadIdx.x + 1] = v;
     if (threadIdx.x == 0) pfx[0] = 0u;
     __syncthreads();
     for (int off = 1; off < kMaxBatch; off <<= 1) {
-      const unsigned add = (int)threadIdx.x >= off ? pfx[threadIdx.x + 1 - off] : 0u;
+      const unsigned add = (mine && (int)threadIdx.x >= off) ? pfx[threadIdx.x + 1 - off] : 0u;
       __syncthreads();
-      pfx[threadIdx.x + 1] += add;
+      if (mine) pfx[threadIdx.x + 1] += add;
       __syncthreads();
     }
   }
@@ -483,7 +483,10 @@ __global__ void __launch_bounds__(kThreads) k_esdf(const DevMap* __restrict__ ma
       ra.nxt_cnt = &ctl->rcnt[(r + 1) % 3];
       if (threadIdx.x == 0) cta_pops = 0;
       raise_dispatch(m, e.y, (r & 1) ? m.rbits1 : m.rbits0, ra, ctl, dsm, &cta_pops);
-      if (threadIdx.x == 0 && cta_pops) atomicAdd(&m.ctr->raise_pops, cta_pops);
+      if (threadIdx.x == 0) {
+        if (cta_pops) atomicAdd(&m.ctr->raise_pops, cta_pops);
+        atomicAdd(&m.ctr->esdf_block_visits, 1u);
+      }
     }
     if (!grid_barrier(&ctl->bar, gridDim.x, &ctl->error)) return;
   }
@@ -512,7 +515,10 @@ __global__ void __launch_bounds__(kThreads) k_esdf(const DevMap* __restrict__ ma
       ra.nxt_cnt = &ctl->lcnt[(l + 1) % 3];
       if (threadIdx.x == 0) cta_pops = 0;
       lower_dispatch(m, e.y, (l & 1) ? m.lbits1 : m.lbits0, ra, ctl, dsm, &cta_pops);
-      if (threadIdx.x == 0 && cta_pops) atomicAdd(&m.ctr->lower_pops, cta_pops);
+      if (threadIdx.x == 0) {
+        if (cta_pops) atomicAdd(&m.ctr->lower_pops, cta_pops);
+        atomicAdd(&m.ctr->esdf_block_visits, 1u);
+      }
     }
     if (!grid_barrier(&ctl->bar, gridDim.x, &ctl->error)) return;
   }

@@ -81,6 +81,8 @@ struct Counters {
   unsigned long long lower_pops;
   unsigned int seeds;
   unsigned int esdf_in;
+  unsigned int esdf_block_visits;  // staged block-rounds
+  unsigned int esdf_local_iters;   // local relaxation iterations summed over block-rounds
 };
 
 // Control block of one ESDF launch: one map, or a batch of maps updated by the same

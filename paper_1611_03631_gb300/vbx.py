@@ -65,6 +65,8 @@ class vbx_stats(ctypes.Structure):
             "raise_rounds",
             "lower_rounds",
             "launches",
+            "esdf_block_visits",
+            "esdf_local_iters",
         )
     ]
 
