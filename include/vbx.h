@@ -173,6 +173,57 @@ vbx_status vbx_get_kernel_times(vbx_map_t map, const char** names, double* ms, i
                                 int* n_out, void* stream);
 vbx_status vbx_reset_kernel_times(vbx_map_t map);
 
+/* ---- Batched form: many independent maps advanced by the same launches --------------------
+ * A batch has a fixed number of slots, each bound to one map (all on the current device, no map
+ * in two slots). One step integrates one scan per slot, updates every slot's ESDF in one
+ * cooperative launch and answers every slot's distance/gradient queries, with about seven
+ * kernel launches in total whatever the number of slots; with VBX_STEP_GRAPH the step is
+ * captured once into a CUDA graph per flag set and replayed. Each map's results are the same
+ * as when it is updated alone (the per-map arithmetic does not depend on the batch). The paper
+ * has no batched form; it is how many robots' maps share one GPU. */
+typedef struct vbx_batch_s* vbx_batch_t;
+
+typedef struct {
+  const float* points_dev;  /* n x 3 float32, sensor frame (device, caller-owned) */
+  int64_t n;                /* 0: no scan for this slot in this step */
+  float T_world_sensor[16]; /* row-major 4x4 pose */
+} vbx_scan_in;
+
+typedef struct {
+  const float* q_dev;   /* n x 3 float32 world points (device) */
+  int64_t n;            /* 0: no queries for this slot */
+  float* dist_dev;      /* n float32 (device) */
+  float* grad_dev;      /* n x 3 float32 (device) */
+  uint8_t* status_dev;  /* n uint8 (device), as vbx_query_distance_gradient */
+} vbx_query_io;
+
+enum { VBX_STEP_INTEGRATE = 1, VBX_STEP_ESDF = 2, VBX_STEP_QUERY = 4, VBX_STEP_GRAPH = 8 };
+
+/* Creates a batch of `count` slots (1..256) bound to maps[0..count). max_points and max_queries
+ * bound n per slot and step (the maps' scratch is grown to max_points here). */
+vbx_status vbx_batch_create(const vbx_map_t* maps, int count, int64_t max_points, int64_t max_queries,
+                            vbx_batch_t* out);
+
+/* Rebinds slot `slot` to `map` (same device, not bound to another slot); synchronises. */
+vbx_status vbx_batch_bind(vbx_batch_t batch, int slot, vbx_map_t map);
+
+/* One batched step on `stream`: scans[count] (VBX_STEP_INTEGRATE), ESDF update of every slot
+ * (VBX_STEP_ESDF), queries[count] (VBX_STEP_QUERY, may be NULL otherwise). Host arrays are copied
+ * before the call returns. Double-buffered: the call waits for the step issued two calls earlier. */
+vbx_status vbx_batch_step(vbx_batch_t batch, const vbx_scan_in* scans, const vbx_query_io* queries, int flags,
+                          void* stream);
+
+/* Chooses launch shapes (CTAs per SM of the traversal and ESDF kernels) by timing full steps on
+ * the given inputs, one step per candidate: the scans ARE integrated into the maps once per
+ * candidate, so call it on warm-up data. Writes a one-line description to report (may be NULL). */
+vbx_status vbx_batch_autotune(vbx_batch_t batch, const vbx_scan_in* scans, const vbx_query_io* queries, int flags,
+                              void* stream, char* report, int report_len);
+
+/* Waits for `stream`; returns the first sticky device error of the bound maps (and clears it). */
+vbx_status vbx_batch_sync(vbx_batch_t batch, void* stream);
+
+vbx_status vbx_batch_destroy(vbx_batch_t batch);
+
 /* Kernels launched by all maps of this process (a running counter). */
 int64_t vbx_total_launches(void);
 

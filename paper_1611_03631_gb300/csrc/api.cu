@@ -17,9 +17,9 @@
 #include "vbx_internal.cuh"
 
 namespace vbx {
-const char* const kKernelNames[kNumKernels] = {"bin_points",  "group_rays",   "link_blocks", "integrate_rays",
-                                               "apply",       "esdf",         "query",       "import_alloc",
-                                               "import_set",  "init_groups"};
+const char* const kKernelNames[kNumKernels] = {"reset_counters", "bin_points",  "group_rays", "link_blocks",
+                                               "integrate_rays", "apply",       "esdf",       "query",
+                                               "import_alloc",   "import_set",  "init_groups"};
 }  // namespace vbx
 
 namespace {
@@ -134,7 +134,7 @@ struct vbx_map_s {
   std::vector<void*> allocs;
   MapHook hook;
 
-  vbx::LaunchCfg cfg(void* stream) const { return vbx::LaunchCfg{num_sms, (cudaStream_t)stream}; }
+  vbx::LaunchCfg cfg(void* stream) const { return vbx::LaunchCfg{num_sms, (cudaStream_t)stream, vbx::kDefaultTuning}; }
 
   template <typename T>
   cudaError_t alloc(T** p, size_t count, int fill_byte) {
@@ -359,7 +359,7 @@ vbx_status vbx_integrate_scan(vbx_map_t m, const float* points_dev, int64_t n, c
   if (st != VBX_OK) return st;
   vbx::Pose pose;
   std::memcpy(pose.T, T, sizeof(pose.T));
-  e = vbx::launch_integrate(m->d, points_dev, (int)n, pose, m->cfg(stream), &m->hook);
+  e = vbx::launch_integrate(vbx::single_batch(m->d, points_dev, (int)n, pose), m->cfg(stream), &m->hook);
   if (e != cudaSuccess) return cuda_fail(e, "integrate launch");
   return VBX_OK;
 }
@@ -410,7 +410,13 @@ vbx_status vbx_query_distance_gradient(vbx_map_t m, const float* q_dev, int64_t 
   if (n < 0 || n > (int64_t(1) << 30)) return fail(VBX_ERR_INVALID_ARG, "n must lie in [0, 2^30]");
   if (n > 0 && (!q_dev || !dist_dev || !grad_dev || !status_dev))
     return fail(VBX_ERR_INVALID_ARG, "query buffers must not be NULL");
-  cudaError_t e = vbx::launch_query(m->d, q_dev, (int)n, dist_dev, grad_dev, status_dev, m->cfg(stream), &m->hook);
+  vbx::Batch b = vbx::single_batch(m->d, nullptr, 0, vbx::Pose{});
+  b.one_query.q = q_dev;
+  b.one_query.dist = dist_dev;
+  b.one_query.grad = grad_dev;
+  b.one_query.status = status_dev;
+  b.one_query.n = (unsigned)n;
+  cudaError_t e = vbx::launch_query(b, (unsigned)n, m->cfg(stream), &m->hook);
   if (e != cudaSuccess) return cuda_fail(e, "query launch");
   return VBX_OK;
 }
@@ -586,6 +592,374 @@ vbx_status vbx_reset_kernel_times(vbx_map_t m) {
     m->hook.ms[i] = 0.0;
     m->hook.count[i] = 0;
   }
+  return VBX_OK;
+}
+
+// ------------------------------------------------------------------------------- batches
+
+}  // extern "C"
+
+struct vbx_batch_s {
+  int count = 0;
+  int device = 0;
+  int num_sms = 0;
+  int max_B = 4;
+  int64_t max_points = 0, max_queries = 0;
+  std::vector<vbx_map_t> maps;
+  // device descriptor block: DevMap[count] | ScanDesc[count] | QueryDesc[count]
+  unsigned char* dev_block = nullptr;
+  size_t block_bytes = 0;
+  unsigned char* staging[2] = {nullptr, nullptr};  // pinned host copies, double-buffered
+  cudaEvent_t staged[2] = {nullptr, nullptr};
+  uint64_t steps = 0;
+  vbx::EsdfCtl* ctl_dev = nullptr;
+  std::vector<void*> dev_allocs;
+  vbx::Tuning tune = vbx::kDefaultTuning;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graphs[2][8] = {};
+  long long graph_kernels[2][8] = {};  // kernels captured into each graph
+  MapHook hook;
+
+  vbx::DevMap* maps_dev() const { return reinterpret_cast<vbx::DevMap*>(dev_block); }
+  vbx::ScanDesc* scans_dev() const { return reinterpret_cast<vbx::ScanDesc*>(dev_block + count * sizeof(vbx::DevMap)); }
+  vbx::QueryDesc* queries_dev() const {
+    return reinterpret_cast<vbx::QueryDesc*>(dev_block + count * (sizeof(vbx::DevMap) + sizeof(vbx::ScanDesc)));
+  }
+  vbx::Batch batch_arg() const {
+    vbx::Batch b;
+    std::memset(&b, 0, sizeof(b));
+    b.maps = maps_dev();
+    b.scans = scans_dev();
+    b.queries = queries_dev();
+    b.nmaps = count;
+    return b;
+  }
+  void drop_graphs() {
+    for (auto& row : graphs)
+      for (auto& g : row)
+        if (g) {
+          cudaGraphExecDestroy(g);
+          g = nullptr;
+        }
+  }
+  ~vbx_batch_s() {
+    cudaDeviceSynchronize();
+    drop_graphs();
+    for (int k = 0; k < 2; ++k) {
+      if (staging[k]) cudaFreeHost(staging[k]);
+      if (staged[k]) cudaEventDestroy(staged[k]);
+    }
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    for (void* p : dev_allocs) cudaFree(p);
+  }
+};
+
+namespace {
+
+vbx_status batch_enqueue(vbx_batch_t b, int k, int flags, cudaStream_t s) {
+  cudaError_t e = cudaMemcpyAsync(b->dev_block, b->staging[k], b->block_bytes, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(e, "batch descriptors");
+  const vbx::LaunchCfg cfg{b->num_sms, s, b->tune};
+  const vbx::Batch arg = b->batch_arg();
+  if (flags & (VBX_STEP_INTEGRATE | VBX_STEP_ESDF)) {
+    if ((e = vbx::launch_reset_counters(arg, cfg, &b->hook)) != cudaSuccess) return cuda_fail(e, "batch reset");
+  }
+  if (flags & VBX_STEP_INTEGRATE) {
+    if ((e = vbx::launch_integrate(arg, cfg, &b->hook)) != cudaSuccess) return cuda_fail(e, "batch integrate");
+  }
+  if (flags & VBX_STEP_ESDF) {
+    if ((e = cudaMemsetAsync(b->ctl_dev, 0, offsetof(vbx::EsdfCtl, cap), s)) != cudaSuccess)
+      return cuda_fail(e, "batch esdf reset");
+    if ((e = vbx::launch_esdf(b->maps_dev(), b->count, b->max_B, b->ctl_dev, cfg, &b->hook)) != cudaSuccess)
+      return cuda_fail(e, "batch esdf");
+  }
+  if (flags & VBX_STEP_QUERY) {
+    const unsigned maxq = (unsigned)std::min<int64_t>(b->max_queries * b->count, (int64_t)UINT32_MAX);
+    if ((e = vbx::launch_query(arg, maxq, cfg, &b->hook)) != cudaSuccess) return cuda_fail(e, "batch query");
+  }
+  return VBX_OK;
+}
+
+vbx_status batch_stage(vbx_batch_t b, const vbx_scan_in* scans, const vbx_query_io* queries, int flags, int* k_out) {
+  for (int i = 0; i < b->count; ++i) {
+    if (flags & VBX_STEP_INTEGRATE) {
+      if (!scans) return fail(VBX_ERR_INVALID_ARG, "scans is NULL");
+      if (scans[i].n < 0 || scans[i].n > b->max_points)
+        return fail(VBX_ERR_INVALID_ARG, "slot %d: n = %lld outside [0, max_points]", i, (long long)scans[i].n);
+      if (scans[i].n > 0 && !scans[i].points_dev) return fail(VBX_ERR_INVALID_ARG, "slot %d: points_dev is NULL", i);
+    }
+    if (flags & VBX_STEP_QUERY) {
+      if (!queries) return fail(VBX_ERR_INVALID_ARG, "queries is NULL");
+      if (queries[i].n < 0 || queries[i].n > b->max_queries)
+        return fail(VBX_ERR_INVALID_ARG, "slot %d: query n outside [0, max_queries]", i);
+      if (queries[i].n > 0 && (!queries[i].q_dev || !queries[i].dist_dev || !queries[i].grad_dev || !queries[i].status_dev))
+        return fail(VBX_ERR_INVALID_ARG, "slot %d: query buffers must not be NULL", i);
+    }
+  }
+  const int k = (int)(b->steps & 1);
+  cudaError_t e = cudaEventSynchronize(b->staged[k]);
+  if (e != cudaSuccess) return cuda_fail(e, "batch staging wait");
+  unsigned char* st = b->staging[k];
+  auto* dm = reinterpret_cast<vbx::DevMap*>(st);
+  auto* sd = reinterpret_cast<vbx::ScanDesc*>(st + b->count * sizeof(vbx::DevMap));
+  auto* qd = reinterpret_cast<vbx::QueryDesc*>(st + b->count * (sizeof(vbx::DevMap) + sizeof(vbx::ScanDesc)));
+  for (int i = 0; i < b->count; ++i) {
+    dm[i] = b->maps[i]->d;
+    vbx::ScanDesc d{};
+    if ((flags & VBX_STEP_INTEGRATE) && scans) {
+      d.pts = scans[i].points_dev;
+      d.n = (unsigned)scans[i].n;
+      std::memcpy(d.T, scans[i].T_world_sensor, sizeof(d.T));
+      b->maps[i]->last_points_in = scans[i].n;
+    }
+    sd[i] = d;
+    vbx::QueryDesc q{};
+    if ((flags & VBX_STEP_QUERY) && queries) {
+      q.q = queries[i].q_dev;
+      q.n = (unsigned)queries[i].n;
+      q.dist = queries[i].dist_dev;
+      q.grad = queries[i].grad_dev;
+      q.status = queries[i].status_dev;
+    }
+    qd[i] = q;
+  }
+  *k_out = k;
+  return VBX_OK;
+}
+
+vbx_status batch_run(vbx_batch_t b, const vbx_scan_in* scans, const vbx_query_io* queries, int flags, cudaStream_t s) {
+  int k = 0;
+  vbx_status st = batch_stage(b, scans, queries, flags, &k);
+  if (st != VBX_OK) return st;
+  const int f = flags & 7;
+  cudaError_t e;
+  if (flags & VBX_STEP_GRAPH) {
+    if (!b->graphs[k][f]) {
+      // capture on the batch's own stream (the legacy default stream cannot be captured)
+      if ((e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return cuda_fail(e, "begin capture");
+      const long long launches_before = b->hook.launches;
+      st = batch_enqueue(b, k, f, b->cap_stream);
+      b->graph_kernels[k][f] = b->hook.launches - launches_before;
+      g_total_launches.fetch_sub(b->graph_kernels[k][f]);  // captured, not launched
+      b->hook.launches = launches_before;
+      cudaGraph_t g = nullptr;
+      e = cudaStreamEndCapture(b->cap_stream, &g);
+      if (st != VBX_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+      }
+      if (e != cudaSuccess) return cuda_fail(e, "end capture");
+      e = cudaGraphInstantiate(&b->graphs[k][f], g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+    }
+    if ((e = cudaGraphLaunch(b->graphs[k][f], s)) != cudaSuccess) return cuda_fail(e, "graph launch");
+    // count the kernels the graph runs
+    b->hook.launches += b->graph_kernels[k][f];
+    g_total_launches.fetch_add(b->graph_kernels[k][f]);
+  } else {
+    st = batch_enqueue(b, k, f, s);
+    if (st != VBX_OK) return st;
+  }
+  if ((e = cudaEventRecord(b->staged[k], s)) != cudaSuccess) return cuda_fail(e, "batch event");
+  b->steps += 1;
+  return VBX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+vbx_status vbx_batch_create(const vbx_map_t* maps, int count, int64_t max_points, int64_t max_queries, vbx_batch_t* out) {
+  if (!out) return fail(VBX_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!maps || count < 1 || count > vbx::kMaxBatch) return fail(VBX_ERR_INVALID_ARG, "count must lie in [1, %d]", vbx::kMaxBatch);
+  if (max_points < 0 || max_points > (int64_t(1) << 28) || max_queries < 0 || max_queries > (int64_t(1) << 26))
+    return fail(VBX_ERR_INVALID_ARG, "max_points / max_queries out of range");
+  int device = 0;
+  cudaError_t e = cudaGetDevice(&device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  for (int i = 0; i < count; ++i) {
+    if (!maps[i]) return fail(VBX_ERR_INVALID_ARG, "slot %d: map is NULL", i);
+    if (maps[i]->device != device) return fail(VBX_ERR_INVALID_ARG, "slot %d: map lives on another device", i);
+    for (int j = 0; j < i; ++j)
+      if (maps[j] == maps[i]) return fail(VBX_ERR_INVALID_ARG, "a map is bound to two slots");
+  }
+  vbx_batch_s* b = new vbx_batch_s();
+  b->count = count;
+  b->device = device;
+  b->num_sms = maps[0]->num_sms;
+  b->max_points = max_points;
+  b->max_queries = max_queries;
+  b->maps.assign(maps, maps + count);
+  uint64_t cap_sum = 0;
+  for (int i = 0; i < count; ++i) {
+    vbx_status st = ensure_scratch(maps[i], std::max<int64_t>(max_points, 1), 0);
+    if (st != VBX_OK) {
+      delete b;
+      return st;
+    }
+    b->max_B = std::max(b->max_B, maps[i]->B);
+    cap_sum += maps[i]->d.cap_blocks;
+  }
+  b->block_bytes = (size_t)count * (sizeof(vbx::DevMap) + sizeof(vbx::ScanDesc) + sizeof(vbx::QueryDesc));
+  auto dalloc = [&](void** p, size_t bytes) -> cudaError_t {
+    cudaError_t r = cudaMalloc(p, std::max<size_t>(bytes, 16));
+    if (r == cudaSuccess) {
+      b->dev_allocs.push_back(*p);
+      r = cudaMemset(*p, 0, std::max<size_t>(bytes, 16));
+    }
+    return r;
+  };
+  vbx::EsdfCtl ctl{};
+  ctl.cap = (unsigned)std::min<uint64_t>(cap_sum, UINT32_MAX);
+  if ((e = dalloc((void**)&b->dev_block, b->block_bytes)) != cudaSuccess ||
+      (e = dalloc((void**)&b->ctl_dev, sizeof(vbx::EsdfCtl))) != cudaSuccess ||
+      (e = dalloc((void**)&ctl.ract0, cap_sum * sizeof(uint2))) != cudaSuccess ||
+      (e = dalloc((void**)&ctl.ract1, cap_sum * sizeof(uint2))) != cudaSuccess ||
+      (e = dalloc((void**)&ctl.lact0, cap_sum * sizeof(uint2))) != cudaSuccess ||
+      (e = dalloc((void**)&ctl.lact1, cap_sum * sizeof(uint2))) != cudaSuccess ||
+      (e = cudaMemcpy(b->ctl_dev, &ctl, sizeof(ctl), cudaMemcpyHostToDevice)) != cudaSuccess) {
+    delete b;
+    return cuda_fail(e, "batch buffers");
+  }
+  for (int k = 0; k < 2; ++k) {
+    if ((e = cudaMallocHost((void**)&b->staging[k], b->block_bytes)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&b->staged[k], cudaEventDisableTiming)) != cudaSuccess) {
+      delete b;
+      return cuda_fail(e, "batch staging");
+    }
+  }
+  if ((e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking)) != cudaSuccess) {
+    delete b;
+    return cuda_fail(e, "capture stream");
+  }
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) {
+    delete b;
+    return cuda_fail(e, "batch create sync");
+  }
+  *out = b;
+  return VBX_OK;
+}
+
+vbx_status vbx_batch_bind(vbx_batch_t b, int slot, vbx_map_t map) {
+  if (!b || !map) return fail(VBX_ERR_INVALID_ARG, "batch or map is NULL");
+  if (slot < 0 || slot >= b->count) return fail(VBX_ERR_INVALID_ARG, "slot out of range");
+  if (map->device != b->device) return fail(VBX_ERR_INVALID_ARG, "map lives on another device");
+  for (int j = 0; j < b->count; ++j)
+    if (j != slot && b->maps[j] == map) return fail(VBX_ERR_INVALID_ARG, "map already bound to slot %d", j);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "bind sync");
+  vbx_status st = ensure_scratch(map, std::max<int64_t>(b->max_points, 1), 0);
+  if (st != VBX_OK) return st;
+  if (map->B > b->max_B) {  // the ESDF launch's shared-memory tile must fit the largest block
+    b->max_B = map->B;
+    b->drop_graphs();
+  }
+  if ((uint64_t)map->d.cap_blocks > b->maps[slot]->d.cap_blocks) {
+    // the active lists were sized for the old maps' pools
+    uint64_t cap_sum = 0;
+    for (int j = 0; j < b->count; ++j) cap_sum += (j == slot ? map : b->maps[j])->d.cap_blocks;
+    vbx::EsdfCtl ctl{};
+    if ((e = cudaMemcpy(&ctl, b->ctl_dev, sizeof(ctl), cudaMemcpyDeviceToHost)) != cudaSuccess)
+      return cuda_fail(e, "esdf control");
+    if (cap_sum > ctl.cap) {
+      void* lists[4] = {nullptr, nullptr, nullptr, nullptr};
+      for (int i = 0; i < 4; ++i) {
+        if ((e = cudaMalloc(&lists[i], cap_sum * sizeof(uint2))) != cudaSuccess) {
+          for (int j = 0; j < i; ++j) cudaFree(lists[j]);
+          return cuda_fail(e, "esdf lists");
+        }
+        b->dev_allocs.push_back(lists[i]);
+      }
+      ctl.ract0 = (uint2*)lists[0];
+      ctl.ract1 = (uint2*)lists[1];
+      ctl.lact0 = (uint2*)lists[2];
+      ctl.lact1 = (uint2*)lists[3];
+      ctl.cap = (unsigned)std::min<uint64_t>(cap_sum, UINT32_MAX);
+      if ((e = cudaMemcpy(b->ctl_dev, &ctl, sizeof(ctl), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(e, "esdf control");
+    }
+  }
+  b->maps[slot] = map;
+  return VBX_OK;
+}
+
+vbx_status vbx_batch_step(vbx_batch_t b, const vbx_scan_in* scans, const vbx_query_io* queries, int flags, void* stream) {
+  if (!b) return fail(VBX_ERR_INVALID_ARG, "batch is NULL");
+  return batch_run(b, scans, queries, flags, (cudaStream_t)stream);
+}
+
+vbx_status vbx_batch_autotune(vbx_batch_t b, const vbx_scan_in* scans, const vbx_query_io* queries, int flags, void* stream,
+                              char* report, int report_len) {
+  if (!b) return fail(VBX_ERR_INVALID_ARG, "batch is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int f = flags & 7;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  auto time_step = [&](float* ms) -> vbx_status {
+    cudaEventRecord(e0, s);
+    vbx_status st = batch_run(b, scans, queries, f, s);
+    if (st != VBX_OK) return st;
+    cudaEventRecord(e1, s);
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune sync");
+    cudaEventElapsedTime(ms, e0, e1);
+    return VBX_OK;
+  };
+  vbx::Tuning best = b->tune;
+  float best_ms = 1e30f;
+  vbx_status st = VBX_OK;
+  // coordinate search: traversal grid first, then the cooperative ESDF grid
+  const int rays_opts[3] = {8, 16, 32};
+  for (int r : rays_opts) {
+    b->tune = best;
+    b->tune.rays_ctas_per_sm = r;
+    float ms = 0.0f;
+    if ((st = time_step(&ms)) != VBX_OK) break;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = b->tune;
+    }
+  }
+  if (st == VBX_OK && (f & VBX_STEP_ESDF)) {
+    best_ms = 1e30f;
+    const int esdf_opts[3] = {1, 2, 3};
+    for (int c : esdf_opts) {
+      b->tune = best;
+      b->tune.esdf_ctas_per_sm = c;
+      float ms = 0.0f;
+      if ((st = time_step(&ms)) != VBX_OK) break;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = b->tune;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->tune = best;
+  b->drop_graphs();  // launch shapes changed
+  if (report && report_len > 0)
+    snprintf(report, (size_t)report_len, "rays_ctas_per_sm=%d esdf_ctas_per_sm=%d bin_ctas_per_sm=%d apply_ctas_per_sm=%d best_step_ms=%.4f",
+             best.rays_ctas_per_sm, best.esdf_ctas_per_sm, best.bin_ctas_per_sm, best.apply_ctas_per_sm, best_ms);
+  return st;
+}
+
+vbx_status vbx_batch_sync(vbx_batch_t b, void* stream) {
+  if (!b) return fail(VBX_ERR_INVALID_ARG, "batch is NULL");
+  vbx_status first = VBX_OK;
+  for (int i = 0; i < b->count; ++i) {
+    vbx_status st = read_error(b->maps[i], (cudaStream_t)stream);
+    if (st != VBX_OK && first == VBX_OK) first = st;
+  }
+  return first;
+}
+
+vbx_status vbx_batch_destroy(vbx_batch_t b) {
+  delete b;
   return VBX_OK;
 }
 

@@ -19,7 +19,6 @@
 // phase the lower wave computes the greatest fixpoint below the current values of a monotone
 // relaxation), so the block-staged rounds give the batch-recompute result.
 #include <cooperative_groups.h>
-#include <cstdlib>
 #include <cuda_runtime.h>
 
 #include "launch.h"
@@ -537,22 +536,19 @@ __global__ void __launch_bounds__(kThreads) k_esdf(const DevMap* __restrict__ ma
 
 size_t esdf_smem_bytes(int max_B) { return tile_bytes(max_B); }
 
-int esdf_grid(int num_sms, int max_B) {
+int esdf_grid(int num_sms, int max_B, int ctas_per_sm) {
   const size_t smem = tile_bytes(max_B);
   if (cudaFuncSetAttribute(k_esdf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_esdf, kThreads, smem) != cudaSuccess) return 0;
-  // resident CTAs per SM of the cooperative grid: 2 by default, VBX_ESDF_CTAS_PER_SM to tune
-  int want = 2;
-  if (const char* e = getenv("VBX_ESDF_CTAS_PER_SM")) want = atoi(e) > 0 ? atoi(e) : want;
-  if (nb > want) nb = want;
+  if (ctas_per_sm > 0 && nb > ctas_per_sm) nb = ctas_per_sm;
   return nb * num_sms;
 }
 
 cudaError_t launch_esdf(const DevMap* maps_dev, int nmaps, int max_B, EsdfCtl* ctl, const LaunchCfg& cfg,
                         LaunchHook* hook) {
   if (nmaps <= 0 || nmaps > kMaxBatch) return cudaErrorInvalidValue;
-  const int grid = esdf_grid(cfg.num_sms, max_B);
+  const int grid = esdf_grid(cfg.num_sms, max_B, cfg.tune.esdf_ctas_per_sm);
   if (grid <= 0) return cudaErrorCooperativeLaunchTooLarge;
   const size_t smem = tile_bytes(max_B);
   void* args[] = {(void*)&maps_dev, (void*)&nmaps, (void*)&ctl};

@@ -14,6 +14,7 @@
 // explicitly rounded intrinsics, so the compiler cannot contract or reorder it.
 #include <cuda_runtime.h>
 
+#include <cstring>
 #include <mutex>
 
 #include <cooperative_groups.h>
@@ -66,6 +67,50 @@ __device__ __forceinline__ unsigned div128_small(unsigned long long lo, unsigned
   return q;
 }
 
+// ---- batch addressing: work items of all maps are concatenated; each CTA builds the exclusive
+// prefix of the per-map counts in shared memory and finds an item's map by binary search.
+
+__device__ __forceinline__ const DevMap& map_of(const Batch& b, unsigned mi) { return b.maps ? b.maps[mi] : b.one; }
+__device__ __forceinline__ const ScanDesc& scan_of(const Batch& b, unsigned mi) { return b.scans ? b.scans[mi] : b.one_scan; }
+
+template <typename F>
+__device__ __forceinline__ unsigned cta_prefix(unsigned* pfx, const Batch& b, F count) {
+  const int nm = b.maps ? b.nmaps : 1;
+  const int t = threadIdx.x;
+  if (nm == 1) {
+    if (t == 0) {
+      pfx[0] = 0u;
+      pfx[1] = count(0u);
+    }
+    __syncthreads();
+    return pfx[1];
+  }
+  pfx[t + 1] = t < nm ? count((unsigned)t) : 0u;
+  if (t == 0) pfx[0] = 0u;
+  __syncthreads();
+  for (int off = 1; off < kMaxBatch; off <<= 1) {
+    const unsigned add = t >= off ? pfx[t + 1 - off] : 0u;
+    __syncthreads();
+    pfx[t + 1] += add;
+    __syncthreads();
+  }
+  return pfx[nm];
+}
+
+__device__ __forceinline__ unsigned map_index(const unsigned* pfx, int nm, unsigned i) {
+  int lo = 0, hi = nm - 1;  // largest mi with pfx[mi] <= i
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pfx[mid] <= i)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return (unsigned)lo;
+}
+
+__device__ __forceinline__ int nmaps_of(const Batch& b) { return b.maps ? b.nmaps : 1; }
+
 __global__ void __launch_bounds__(kThreads) k_init_groups(GroupEntry* tab, uint32_t entries) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < entries; i += gridDim.x * blockDim.x) {
     GroupEntry e;
@@ -78,30 +123,57 @@ __global__ void __launch_bounds__(kThreads) k_init_groups(GroupEntry* tab, uint3
   }
 }
 
+__global__ void __launch_bounds__(kThreads) k_reset_counters(Batch b) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nmaps_of(b); i += gridDim.x * blockDim.x) {
+    Counters* c = map_of(b, i).ctr;
+    c->ngroups = 0;
+    c->nnew = 0;
+    c->nupdated = 0;
+    c->npoints_valid = 0;
+    c->nrecords = 0;
+    c->raise_rounds = 0;
+    c->lower_rounds = 0;
+    c->raise_pops = 0;
+    c->lower_pops = 0;
+    c->seeds = 0;
+    c->esdf_in = 0;
+    c->esdf_block_visits = 0;
+    c->esdf_local_iters = 0;
+  }
+}
+
 // ------------------------------------------------------------------------------- A1 + A2
-__global__ void __launch_bounds__(kThreads) k_bin_points(DevMap m, const float* __restrict__ pts, int n, Pose T) {
+__global__ void __launch_bounds__(kThreads) k_bin_points(Batch b) {
+  __shared__ unsigned pfx[kMaxBatch + 1];
   __shared__ unsigned long long sh_w[kWarps][32];
   __shared__ unsigned long long sh_o[3][kWarps][32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int stride = gridDim.x * blockDim.x;
-  for (int base = blockIdx.x * blockDim.x; base < n; base += stride) {
-    const int i = base + threadIdx.x;
+  const int nm = nmaps_of(b);
+  const unsigned total = cta_prefix(pfx, b, [&](unsigned mi) { return scan_of(b, mi).n; });
+  const unsigned stride = gridDim.x * blockDim.x;
+  for (unsigned base = blockIdx.x * blockDim.x; base < total; base += stride) {
+    const unsigned i = base + threadIdx.x;
     bool valid = false;
+    unsigned mi = 0;
     unsigned long long key = kEmptyKey;
     unsigned long long wq = 0, o[3] = {0, 0, 0};
     float pw[3] = {0.f, 0.f, 0.f};
     float w = 0.0f;
-    if (i < n) {
-      const float x = __ldg(&pts[3 * (size_t)i + 0]);
-      const float y = __ldg(&pts[3 * (size_t)i + 1]);
-      const float z = __ldg(&pts[3 * (size_t)i + 2]);
+    if (i < total) {
+      mi = map_index(pfx, nm, i);
+      const DevMap& m = map_of(b, mi);
+      const ScanDesc& sd = scan_of(b, mi);
+      const unsigned j = i - pfx[mi];
+      const float x = __ldg(&sd.pts[3 * (size_t)j + 0]);
+      const float y = __ldg(&sd.pts[3 * (size_t)j + 1]);
+      const float z = __ldg(&sd.pts[3 * (size_t)j + 2]);
       if (accept_point(m, x, y, z, &w)) {
         bool in_range = true;
         float q[3];
         for (int r = 0; r < 3; ++r) {
-          pw[r] = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(T.T[4 * r], x), __fmul_rn(T.T[4 * r + 1], y)),
-                                      __fmul_rn(T.T[4 * r + 2], z)),
-                            T.T[4 * r + 3]);
+          pw[r] = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(sd.T[4 * r], x), __fmul_rn(sd.T[4 * r + 1], y)),
+                                      __fmul_rn(sd.T[4 * r + 2], z)),
+                            sd.T[4 * r + 3]);
           q[r] = __fdiv_rn(pw[r], m.v);
           if (!(fabsf(q[r]) < 1048576.0f)) in_range = false;
         }
@@ -118,29 +190,31 @@ __global__ void __launch_bounds__(kThreads) k_bin_points(DevMap m, const float* 
           wq = m.weighting == 0 ? 1ull : (unsigned long long)__float2ll_rn(__fmul_rn(w, 1048576.0f));
         }
       }
-    }
-    const unsigned vmask = __ballot_sync(kFull, valid);
-    if (lane == 0 && vmask) atomicAdd(&m.ctr->npoints_valid, (unsigned)__popc(vmask));
-    if (!m.grouped) {  // one ray per point
       if (valid) {
-        const unsigned r = atomicAdd(&m.ctr->ngroups, 1u);
-        m.rays[r] = make_float4(pw[0], pw[1], pw[2], w);
+        if (!m.grouped) {  // one ray per point
+          const unsigned r = atomicAdd(&m.ctr->ngroups, 1u);
+          m.rays[r] = make_float4(pw[0], pw[1], pw[2], w);
+          valid = false;
+          atomicAdd(&m.ctr->npoints_valid, 1u);
+          key = kEmptyKey;
+        }
       }
-      continue;
     }
-    // warp pre-aggregation of points that share a voxel (neighbouring pixels usually do)
-    const unsigned peers = __match_any_sync(kFull, key);
+    // warp pre-aggregation of points of one map that share a voxel (neighbouring pixels usually do)
+    const unsigned peers = __match_any_sync(kFull, key) & __match_any_sync(kFull, mi);
     const int leader = __ffs(peers) - 1;
     sh_w[wid][lane] = wq;
     for (int r = 0; r < 3; ++r) sh_o[r][wid][lane] = wq * o[r];
     __syncwarp();
     if (valid && lane == leader) {
+      const DevMap& m = map_of(b, mi);
       unsigned long long sw = 0, so[3] = {0, 0, 0};
       for (unsigned pm = peers; pm; pm &= pm - 1) {
         const int src = __ffs(pm) - 1;
         sw += sh_w[wid][src];
         for (int r = 0; r < 3; ++r) so[r] += sh_o[r][wid][src];
       }
+      atomicAdd(&m.ctr->npoints_valid, (unsigned)__popc(peers));
       uint32_t h = hash64(key) & m.gmask;
       bool placed = false;
       for (uint32_t probe = 0; probe <= m.gmask; ++probe) {
@@ -177,12 +251,17 @@ __global__ void __launch_bounds__(kThreads) k_bin_points(DevMap m, const float* 
 }
 
 // ------------------------------------------------------------------------------- A2 + A3
-__global__ void __launch_bounds__(kThreads) k_group_rays(DevMap m, Pose T) {
-  const unsigned ng = __ldcg(&m.ctr->ngroups);
-  const float s[3] = {T.T[3], T.T[7], T.T[11]};
-  for (unsigned gi = blockIdx.x * blockDim.x + threadIdx.x; gi < ng; gi += gridDim.x * blockDim.x) {
+__global__ void __launch_bounds__(kThreads) k_group_rays(Batch b) {
+  __shared__ unsigned pfx[kMaxBatch + 1];
+  const int nm = nmaps_of(b);
+  const unsigned total = cta_prefix(pfx, b, [&](unsigned mi) { return __ldcg(&map_of(b, mi).ctr->ngroups); });
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const unsigned mi = map_index(pfx, nm, i);
+    const unsigned gi = i - pfx[mi];
+    const DevMap& m = map_of(b, mi);
+    const ScanDesc& sd = scan_of(b, mi);
+    const float s[3] = {sd.T[3], sd.T[7], sd.T[11]};
     float pbar[3];
-    float Wg;
     if (m.grouped) {
       const uint32_t h = m.glist[gi];
       GroupEntry e = m.gtab[h];
@@ -202,7 +281,7 @@ __global__ void __launch_bounds__(kThreads) k_group_rays(DevMap m, Pose T) {
         const unsigned mo = div128_small(lo, hi, e.sw);
         pbar[a] = __fmul_rn(__fadd_rn((float)kk[a], __fmul_rn((float)mo, 1.0f / 65536.0f)), m.v);
       }
-      Wg = m.weighting == 0 ? __uint2float_rn(e.n) : __fmul_rn(__ull2float_rn(e.sw), 1.0f / 1048576.0f);
+      const float Wg = m.weighting == 0 ? __uint2float_rn(e.n) : __fmul_rn(__ull2float_rn(e.sw), 1.0f / 1048576.0f);
       m.rays[gi] = make_float4(pbar[0], pbar[1], pbar[2], Wg);
     } else {
       const float4 r = m.rays[gi];
@@ -225,19 +304,24 @@ __global__ void __launch_bounds__(kThreads) k_group_rays(DevMap m, Pose T) {
 }
 
 // ------------------------------------------------------------------------------------ A3
-__global__ void __launch_bounds__(kThreads) k_link_blocks(DevMap m) {
-  const unsigned nn = __ldcg(&m.ctr->nnew);
+__global__ void __launch_bounds__(kThreads) k_link_blocks(Batch b) {
+  __shared__ unsigned pfx[kMaxBatch + 1];
+  const int nm = nmaps_of(b);
   // one thread per (new block, direction)
-  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < nn * 27u; t += gridDim.x * blockDim.x) {
-    const uint32_t p = m.newblk[t / 27u];
+  const unsigned total = cta_prefix(pfx, b, [&](unsigned mi) { return __ldcg(&map_of(b, mi).ctr->nnew) * 27u; });
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    const unsigned mi = map_index(pfx, nm, t);
+    const DevMap& m = map_of(b, mi);
+    const unsigned u = t - pfx[mi];
+    const uint32_t p = m.newblk[u / 27u];
     if (p >= m.cap_blocks) continue;
-    const int k = (int)(t % 27u);
+    const int k = (int)(u % 27u);
     if (k == 13) {
       m.nbr[(size_t)p * 27 + 13] = p;
       continue;
     }
-    const int3 b = m.bcoord[p];
-    const uint32_t q = block_lookup(m, b.x + k / 9 - 1, b.y + (k / 3) % 3 - 1, b.z + k % 3 - 1);
+    const int3 bc = m.bcoord[p];
+    const uint32_t q = block_lookup(m, bc.x + k / 9 - 1, bc.y + (k / 3) % 3 - 1, bc.z + k % 3 - 1);
     m.nbr[(size_t)p * 27 + k] = q;
     if (q != kInvalid) m.nbr[(size_t)q * 27 + (26 - k)] = p;
   }
@@ -261,17 +345,29 @@ __device__ __forceinline__ void accumulate(const DevMap& m, uint32_t vid, const 
   atomicOr(&m.touch[vid], 1u);
 }
 
-__global__ void __launch_bounds__(kThreads) k_integrate_rays(DevMap m, Pose T) {
+__global__ void __launch_bounds__(kThreads) k_integrate_rays(Batch b) {
+  __shared__ unsigned pfx[kMaxBatch + 1];
   __shared__ long long sh_v[4][kWarps][32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const unsigned nr = __ldcg(&m.ctr->ngroups);
-  const float s[3] = {T.T[3], T.T[7], T.T[11]};
-  const int B = m.B, blog = m.blog;
+  const int nm = nmaps_of(b);
+  // each map's rays are padded to whole warps, so a warp never mixes maps
+  const unsigned total = cta_prefix(pfx, b, [&](unsigned mi) { return (__ldcg(&map_of(b, mi).ctr->ngroups) + 31u) & ~31u; });
   const unsigned warps_total = gridDim.x * kWarps;
   unsigned long long nrec = 0;
-  for (unsigned base = (blockIdx.x * kWarps + wid) * 32u; base < nr; base += warps_total * 32u) {
-    const unsigned gi = base + lane;
-    bool active = gi < nr;
+  unsigned rec_map = 0;
+  for (unsigned base = (blockIdx.x * kWarps + wid) * 32u; base < total; base += warps_total * 32u) {
+    const unsigned mi = map_index(pfx, nm, base);
+    const DevMap& m = map_of(b, mi);
+    const ScanDesc& sd = scan_of(b, mi);
+    if (nrec && mi != rec_map) {
+      atomicAdd(&map_of(b, rec_map).ctr->nrecords, nrec);
+      nrec = 0;
+    }
+    rec_map = mi;
+    const float s[3] = {sd.T[3], sd.T[7], sd.T[11]};
+    const int B = m.B, blog = m.blog;
+    const unsigned gi = base - pfx[mi] + lane;
+    bool active = gi < __ldcg(&m.ctr->ngroups);
     RayGeom g;
     float Wg = 0.0f;
     Dda dda;
@@ -376,7 +472,7 @@ __global__ void __launch_bounds__(kThreads) k_integrate_rays(DevMap m, Pose T) {
       }
     }
   }
-  if (nrec) atomicAdd(&m.ctr->nrecords, nrec);
+  if (nrec) atomicAdd(&map_of(b, rec_map).ctr->nrecords, nrec);
 }
 
 // ------------------------------------------------------------------------------------ A5
@@ -392,13 +488,21 @@ __device__ __forceinline__ void append(uint32_t* list, unsigned* count, uint32_t
 // One CTA per touched block: every voxel that received records this scan gets the Eq. (3)
 // merge, its sums and flag are cleared, and it joins the scan's updated list and (once) the
 // queue of the next ESDF update.
-__global__ void __launch_bounds__(kThreads) k_apply(DevMap m) {
-  const unsigned nb = min(__ldcg(&m.ctr->blocks), m.cap_blocks);
-  const unsigned B3 = 1u << m.b3log;
-  for (unsigned b = blockIdx.x; b < nb; b += gridDim.x) {
-    if (__ldcg(&m.btouch[b]) == 0u) continue;  // uniform across the CTA
+__global__ void __launch_bounds__(kThreads) k_apply(Batch b) {
+  __shared__ unsigned pfx[kMaxBatch + 1];
+  const int nm = nmaps_of(b);
+  const unsigned total = cta_prefix(pfx, b, [&](unsigned mi) {
+    const DevMap& m = map_of(b, mi);
+    return min(__ldcg(&m.ctr->blocks), m.cap_blocks);
+  });
+  for (unsigned item = blockIdx.x; item < total; item += gridDim.x) {
+    const unsigned mi = map_index(pfx, nm, item);
+    const DevMap& m = map_of(b, mi);
+    const unsigned blk = item - pfx[mi];
+    if (__ldcg(&m.btouch[blk]) == 0u) continue;  // uniform across the CTA
+    const unsigned B3 = 1u << m.b3log;
     for (unsigned l = threadIdx.x; l < B3; l += blockDim.x) {
-      const uint32_t vid = (b << m.b3log) | l;
+      const uint32_t vid = (blk << m.b3log) | l;
       if (m.touch[vid] == 0u) continue;
       m.touch[vid] = 0u;
       ulonglong2* a = reinterpret_cast<ulonglong2*>(&m.acc[4 * (size_t)vid]);
@@ -421,7 +525,7 @@ __global__ void __launch_bounds__(kThreads) k_apply(DevMap m) {
       }
     }
     __syncthreads();
-    if (threadIdx.x == 0) m.btouch[b] = 0u;
+    if (threadIdx.x == 0) m.btouch[blk] = 0u;
   }
 }
 
@@ -460,6 +564,20 @@ int grid_for(long long items, int num_sms, int per_sm) {
 
 }  // namespace
 
+Batch single_batch(const DevMap& m, const float* pts, int n, const Pose& T) {
+  Batch b;
+  std::memset(&b, 0, sizeof(b));
+  b.maps = nullptr;
+  b.scans = nullptr;
+  b.queries = nullptr;
+  b.nmaps = 1;
+  b.one = m;
+  b.one_scan.pts = pts;
+  b.one_scan.n = (unsigned)n;
+  std::memcpy(b.one_scan.T, T.T, sizeof(T.T));
+  return b;
+}
+
 cudaError_t launch_init_groups(GroupEntry* tab, uint32_t entries, cudaStream_t s, LaunchHook* hook) {
   hook->begin(kKInitGroups, s);
   k_init_groups<<<(entries + kThreads - 1) / kThreads > 65535 ? 65535 : (entries + kThreads - 1) / kThreads, kThreads, 0, s>>>(tab, entries);
@@ -467,24 +585,33 @@ cudaError_t launch_init_groups(GroupEntry* tab, uint32_t entries, cudaStream_t s
   return cudaGetLastError();
 }
 
-cudaError_t launch_integrate(const DevMap& m, const float* pts, int n, const Pose& T, const LaunchCfg& cfg,
-                             LaunchHook* hook) {
+cudaError_t launch_reset_counters(const Batch& b, const LaunchCfg& cfg, LaunchHook* hook) {
+  hook->begin(kKReset, cfg.stream);
+  k_reset_counters<<<1, kThreads, 0, cfg.stream>>>(b);
+  hook->end(kKReset, cfg.stream);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_integrate(const Batch& b, const LaunchCfg& cfg, LaunchHook* hook) {
   const cudaStream_t s = cfg.stream;
-  const int gpts = grid_for(n, cfg.num_sms, 16);
+  // single-map launches size the point grid by the scan; batched launches use the tuned grid
+  // (all kernels stride over their device-side work counts)
+  const int gpts = b.maps ? cfg.num_sms * cfg.tune.bin_ctas_per_sm : grid_for(b.one_scan.n, cfg.num_sms, cfg.tune.bin_ctas_per_sm);
+  const int grays = b.maps ? cfg.num_sms * cfg.tune.rays_ctas_per_sm : grid_for(b.one_scan.n, cfg.num_sms, cfg.tune.rays_ctas_per_sm);
   hook->begin(kKBin, s);
-  k_bin_points<<<gpts, kThreads, 0, s>>>(m, pts, n, T);
+  k_bin_points<<<gpts, kThreads, 0, s>>>(b);
   hook->end(kKBin, s);
   hook->begin(kKGroupRays, s);
-  k_group_rays<<<gpts, kThreads, 0, s>>>(m, T);
+  k_group_rays<<<gpts, kThreads, 0, s>>>(b);
   hook->end(kKGroupRays, s);
   hook->begin(kKLink, s);
-  k_link_blocks<<<cfg.num_sms * 4, kThreads, 0, s>>>(m);
+  k_link_blocks<<<cfg.num_sms * 4, kThreads, 0, s>>>(b);
   hook->end(kKLink, s);
   hook->begin(kKIntegrateRays, s);
-  k_integrate_rays<<<gpts, kThreads, 0, s>>>(m, T);
+  k_integrate_rays<<<grays, kThreads, 0, s>>>(b);
   hook->end(kKIntegrateRays, s);
   hook->begin(kKApply, s);
-  k_apply<<<cfg.num_sms * 8, kThreads, 0, s>>>(m);
+  k_apply<<<cfg.num_sms * cfg.tune.apply_ctas_per_sm, kThreads, 0, s>>>(b);
   hook->end(kKApply, s);
   return cudaGetLastError();
 }
@@ -497,7 +624,7 @@ cudaError_t launch_import(const DevMap& m, const int* vox, const float* D, const
   k_import_alloc<<<g, kThreads, 0, s>>>(m, vox, n);
   hook->end(kKImportAlloc, s);
   hook->begin(kKLink, s);
-  k_link_blocks<<<cfg.num_sms * 4, kThreads, 0, s>>>(m);
+  k_link_blocks<<<cfg.num_sms * 4, kThreads, 0, s>>>(single_batch(m, nullptr, 0, Pose{}));
   hook->end(kKLink, s);
   hook->begin(kKImportSet, s);
   k_import_set<<<g, kThreads, 0, s>>>(m, vox, D, W, n);
@@ -561,7 +688,7 @@ cudaError_t launch_integrate_noalloc(const DevMap& m, void* scratch, const float
   ms.rays = reinterpret_cast<float4*>(base + kNoAllocGroupBytes + kNoAllocListBytes);
   cudaError_t e = launch_init_groups(ms.gtab, kNoAllocGroupEntries, cfg.stream, hook);
   if (e != cudaSuccess) return e;
-  return launch_integrate(ms, pts, n, T, cfg, hook);
+  return launch_integrate(single_batch(ms, pts, n, T), cfg, hook);
 }
 
 }  // namespace vbx

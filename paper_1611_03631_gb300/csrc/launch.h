@@ -11,9 +11,51 @@ struct Pose {
   float T[16];  // row-major T_world_sensor
 };
 
+constexpr int kMaxBatch = 256;  // maps per batched launch (one prefix entry per thread of a CTA)
+
+// One map's scan and query batch inside a batched launch.
+struct ScanDesc {
+  const float* pts;  // n x 3 float32, sensor frame (device)
+  unsigned n;
+  unsigned pad;
+  float T[16];  // row-major T_world_sensor
+};
+
+struct QueryDesc {
+  const float* q;  // n x 3 (device)
+  float* dist;
+  float* grad;
+  unsigned char* status;
+  unsigned n;
+  unsigned pad;
+};
+
+// Kernel parameter of every map-update kernel: either a device array of nmaps maps with their
+// scan / query descriptors, or (maps == nullptr) the single map `one` with `one_scan` and
+// `one_query` passed by value.
+struct Batch {
+  const DevMap* maps;
+  const ScanDesc* scans;
+  const QueryDesc* queries;
+  int nmaps;
+  DevMap one;
+  ScanDesc one_scan;
+  QueryDesc one_query;
+};
+
+// Launch shape knobs (chosen by the batch autotuner).
+struct Tuning {
+  int rays_ctas_per_sm;  // CTAs per SM of the voxel-traversal kernel
+  int bin_ctas_per_sm;   // CTAs per SM of the point and group kernels
+  int apply_ctas_per_sm;
+  int esdf_ctas_per_sm;  // resident CTAs per SM of the cooperative ESDF grid
+};
+constexpr Tuning kDefaultTuning = {16, 16, 8, 2};
+
 struct LaunchCfg {
   int num_sms;
   cudaStream_t stream;
+  Tuning tune;
 };
 
 // Records one launch (for profiling and launch counting). Implemented by the API layer.
@@ -24,7 +66,8 @@ struct LaunchHook {
 };
 
 enum KernelId {
-  kKBin = 0,
+  kKReset = 0,
+  kKBin,
   kKGroupRays,
   kKLink,
   kKIntegrateRays,
@@ -41,25 +84,25 @@ extern const char* const kKernelNames[kNumKernels];
 
 // integrate.cu
 cudaError_t launch_init_groups(GroupEntry* tab, uint32_t entries, cudaStream_t s, LaunchHook* hook);
-cudaError_t launch_integrate(const DevMap& m, const float* pts, int n, const Pose& T, const LaunchCfg& cfg,
-                             LaunchHook* hook);
+cudaError_t launch_integrate(const Batch& b, const LaunchCfg& cfg, LaunchHook* hook);
+// zeroes the per-scan and per-ESDF counters of every map of a device array of maps
+cudaError_t launch_reset_counters(const Batch& b, const LaunchCfg& cfg, LaunchHook* hook);
 // Largest scan accepted by the allocation-free integration entry point.
 constexpr int kNoAllocMaxPoints = 1 << 16;
 cudaError_t noalloc_scratch_setup(int device, void** ptr);
 cudaError_t launch_integrate_noalloc(const DevMap& m, void* scratch, const float* pts, int n, const Pose& T,
                                      const LaunchCfg& cfg, LaunchHook* hook);
+Batch single_batch(const DevMap& m, const float* pts, int n, const Pose& T);
 cudaError_t launch_import(const DevMap& m, const int* vox, const float* D, const float* W, int n,
                           const LaunchCfg& cfg, LaunchHook* hook);
 
 // esdf.cu: one cooperative launch updates the ESDF of nmaps maps (device array of DevMap)
-constexpr int kMaxBatch = 256;  // maps per ESDF launch (one prefix entry per thread)
 size_t esdf_smem_bytes(int max_B);
-int esdf_grid(int num_sms, int max_B);
+int esdf_grid(int num_sms, int max_B, int ctas_per_sm);
 cudaError_t launch_esdf(const DevMap* maps_dev, int nmaps, int max_B, EsdfCtl* ctl, const LaunchCfg& cfg,
                         LaunchHook* hook);
 
-// query.cu
-cudaError_t launch_query(const DevMap& m, const float* q, int n, float* dist, float* grad, unsigned char* status,
-                         const LaunchCfg& cfg, LaunchHook* hook);
+// query.cu: b.queries (or b.one_query) give each map's query points and outputs
+cudaError_t launch_query(const Batch& b, unsigned max_total, const LaunchCfg& cfg, LaunchHook* hook);
 
 }  // namespace vbx

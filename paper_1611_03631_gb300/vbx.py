@@ -71,6 +71,22 @@ class vbx_stats(ctypes.Structure):
     ]
 
 
+class vbx_scan_in(ctypes.Structure):
+    _fields_ = [("points_dev", ctypes.c_void_p), ("n", ctypes.c_int64), ("T_world_sensor", ctypes.c_float * 16)]
+
+
+class vbx_query_io(ctypes.Structure):
+    _fields_ = [
+        ("q_dev", ctypes.c_void_p),
+        ("n", ctypes.c_int64),
+        ("dist_dev", ctypes.c_void_p),
+        ("grad_dev", ctypes.c_void_p),
+        ("status_dev", ctypes.c_void_p),
+    ]
+
+
+STEP_INTEGRATE, STEP_ESDF, STEP_QUERY, STEP_GRAPH = 1, 2, 4, 8
+
 _lib = None
 
 # exported symbols and their (restype, argtypes)
@@ -100,6 +116,12 @@ _SIGS = {
     ),
     "vbx_reset_kernel_times": (ctypes.c_int, [_vp]),
     "vbx_total_launches": (_i64, []),
+    "vbx_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, _i64, _i64, ctypes.POINTER(_vp)]),
+    "vbx_batch_bind": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
+    "vbx_batch_step": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
+    "vbx_batch_autotune": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_char_p, ctypes.c_int]),
+    "vbx_batch_sync": (ctypes.c_int, [_vp, _vp]),
+    "vbx_batch_destroy": (ctypes.c_int, [_vp]),
     "vbx_last_error": (ctypes.c_char_p, []),
 }
 
@@ -314,3 +336,73 @@ class Map:
 
     def reset_kernel_times(self) -> None:
         _check(self._lib.vbx_reset_kernel_times(self._h))
+
+
+class MapBatch:
+    """A fixed-slot batch of maps advanced by the same launches (vbx_batch_* in vbx.h)."""
+
+    def __init__(self, maps, max_points: int, max_queries: int = 0):
+        self._lib = load_library()
+        self.maps = list(maps)
+        arr = (ctypes.c_void_p * len(self.maps))(*[m.handle for m in self.maps])
+        h = ctypes.c_void_p()
+        _check(self._lib.vbx_batch_create(arr, len(self.maps), int(max_points), int(max_queries), ctypes.byref(h)))
+        self._h = h
+        self.count = len(self.maps)
+        self._scans = (vbx_scan_in * self.count)()
+        self._queries = (vbx_query_io * self.count)()
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.vbx_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def bind(self, slot: int, m: "Map") -> None:
+        _check(self._lib.vbx_batch_bind(self._h, int(slot), m.handle))
+        self.maps[slot] = m
+
+    def _fill(self, points, poses, queries):
+        for i in range(self.count):
+            s = self._scans[i]
+            p = points[i] if points is not None else None
+            if p is None or p.shape[0] == 0:
+                s.points_dev, s.n = None, 0
+            else:
+                _dev_f32(p, 3)
+                s.points_dev, s.n = p.data_ptr(), p.shape[0]
+            if poses is not None and poses[i] is not None:
+                T = np.asarray(poses[i], dtype=np.float32).reshape(16)
+                for j in range(16):
+                    s.T_world_sensor[j] = float(T[j])
+            q = self._queries[i]
+            if queries is None or queries[i] is None:
+                q.q_dev, q.n, q.dist_dev, q.grad_dev, q.status_dev = None, 0, None, None, None
+            else:
+                qq, dist, grad, status = queries[i]
+                _dev_f32(qq, 3)
+                q.q_dev, q.n = qq.data_ptr(), qq.shape[0]
+                q.dist_dev, q.grad_dev, q.status_dev = dist.data_ptr(), grad.data_ptr(), status.data_ptr()
+
+    def step(self, points=None, poses=None, queries=None, flags: int = STEP_INTEGRATE | STEP_ESDF, stream=None) -> None:
+        """points[i]: (N,3) device tensor or None; poses[i]: 4x4; queries[i]: (q, dist, grad, status) or None."""
+        self._fill(points, poses, queries)
+        _check(self._lib.vbx_batch_step(self._h, ctypes.byref(self._scans), ctypes.byref(self._queries), int(flags), _stream_ptr(stream)))
+
+    def autotune(self, points=None, poses=None, queries=None, flags: int = STEP_INTEGRATE | STEP_ESDF, stream=None) -> str:
+        self._fill(points, poses, queries)
+        buf = ctypes.create_string_buffer(256)
+        _check(
+            self._lib.vbx_batch_autotune(
+                self._h, ctypes.byref(self._scans), ctypes.byref(self._queries), int(flags), _stream_ptr(stream), buf, 256
+            )
+        )
+        return buf.value.decode()
+
+    def sync(self, stream=None) -> None:
+        _check(self._lib.vbx_batch_sync(self._h, _stream_ptr(stream)))
