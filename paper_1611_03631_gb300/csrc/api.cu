@@ -272,6 +272,7 @@ vbx_status vbx_create_map(float voxel_size, int voxels_per_block, float truncati
   d.B = B;
   d.blog = ilog2(B);
   d.b3log = 3 * d.blog;
+  d.tile_shift = B == 16 ? 3 : 0;
   d.weighting = opt.weighting;
   d.grouped = opt.grouped ? 1 : 0;
   d.cap_blocks = (uint32_t)cap;
@@ -299,8 +300,9 @@ vbx_status vbx_create_map(float voxel_size, int voxels_per_block, float truncati
   VBX_ALLOC(d.rbits1, V / 32, 0);
   VBX_ALLOC(d.lbits0, V / 32, 0);
   VBX_ALLOC(d.lbits1, V / 32, 0);
-  VBX_ALLOC(d.bstamp_r, (size_t)cap, 0);
-  VBX_ALLOC(d.bstamp_l, (size_t)cap, 0);
+  const size_t items = (size_t)cap << d.tile_shift;  // ESDF tiles
+  VBX_ALLOC(d.bstamp_r, items, 0);
+  VBX_ALLOC(d.bstamp_l, items, 0);
   VBX_ALLOC(d.updated, V, 0);
   VBX_ALLOC(d.dirty, V, 0);
   VBX_ALLOC(d.newblk, (size_t)cap, 0);
@@ -309,11 +311,11 @@ vbx_status vbx_create_map(float voxel_size, int voxels_per_block, float truncati
   VBX_ALLOC(m->ctl_dev, 1, 0);
   {
     vbx::EsdfCtl ctl{};
-    ctl.cap = (unsigned)cap;
-    VBX_ALLOC(ctl.ract0, (size_t)cap, 0);
-    VBX_ALLOC(ctl.ract1, (size_t)cap, 0);
-    VBX_ALLOC(ctl.lact0, (size_t)cap, 0);
-    VBX_ALLOC(ctl.lact1, (size_t)cap, 0);
+    ctl.cap = (unsigned)items;
+    VBX_ALLOC(ctl.ract0, items, 0);
+    VBX_ALLOC(ctl.ract1, items, 0);
+    VBX_ALLOC(ctl.lact0, items, 0);
+    VBX_ALLOC(ctl.lact1, items, 0);
     if ((e = cudaMemcpy(m->ctl_dev, &ctl, sizeof(ctl), cudaMemcpyHostToDevice)) != cudaSuccess) {
       delete m;
       return cuda_fail(e, "esdf control block");
@@ -801,7 +803,7 @@ vbx_status vbx_batch_create(const vbx_map_t* maps, int count, int64_t max_points
       return st;
     }
     b->max_B = std::max(b->max_B, maps[i]->B);
-    cap_sum += maps[i]->d.cap_blocks;
+    cap_sum += (uint64_t)maps[i]->d.cap_blocks << maps[i]->d.tile_shift;
   }
   b->block_bytes = (size_t)count * (sizeof(vbx::DevMap) + sizeof(vbx::ScanDesc) + sizeof(vbx::QueryDesc));
   auto dalloc = [&](void** p, size_t bytes) -> cudaError_t {
@@ -857,10 +859,13 @@ vbx_status vbx_batch_bind(vbx_batch_t b, int slot, vbx_map_t map) {
     b->max_B = map->B;
     b->drop_graphs();
   }
-  if ((uint64_t)map->d.cap_blocks > b->maps[slot]->d.cap_blocks) {
+  if (((uint64_t)map->d.cap_blocks << map->d.tile_shift) > ((uint64_t)b->maps[slot]->d.cap_blocks << b->maps[slot]->d.tile_shift)) {
     // the active lists were sized for the old maps' pools
     uint64_t cap_sum = 0;
-    for (int j = 0; j < b->count; ++j) cap_sum += (j == slot ? map : b->maps[j])->d.cap_blocks;
+    for (int j = 0; j < b->count; ++j) {
+      const vbx_map_t mj = j == slot ? map : b->maps[j];
+      cap_sum += (uint64_t)mj->d.cap_blocks << mj->d.tile_shift;
+    }
     vbx::EsdfCtl ctl{};
     if ((e = cudaMemcpy(&ctl, b->ctl_dev, sizeof(ctl), cudaMemcpyDeviceToHost)) != cudaSuccess)
       return cuda_fail(e, "esdf control");
@@ -926,7 +931,7 @@ vbx_status vbx_batch_autotune(vbx_batch_t b, const vbx_scan_in* scans, const vbx
   }
   if (st == VBX_OK && (f & VBX_STEP_ESDF)) {
     best_ms = 1e30f;
-    const int esdf_opts[3] = {1, 2, 3};
+    const int esdf_opts[3] = {2, 3, 4};
     for (int c : esdf_opts) {
       b->tune = best;
       b->tune.esdf_ctas_per_sm = c;

@@ -3,17 +3,17 @@
 //   A6 classify : every TSDF voxel updated since the last call takes one branch of the first
 //                 loop of Algorithm 1 (fixed band |D| < gamma, leaving the band, new voxel,
 //                 sign flip) and seeds the raise and lower frontiers
-//   A7 raise    : global rounds over active blocks; a CTA stages one block and its one-voxel
-//                 halo in shared memory and raises within the block until no child is left
-//                 there: a raised non-fixed voxel is reset to +-d_max, neighbours whose parent
+//   A7 raise    : global rounds over active tiles (a block, or an 8^3 octant of a 16^3 block);
+//                 a CTA stages one tile and its one-voxel halo in shared memory and raises
+//                 within the tile until no child is left there: a raised non-fixed voxel is reset to +-d_max, neighbours whose parent
 //                 direction points back at it are raised next, all other observed neighbours
 //                 join the lower frontier; children in the halo are raised in the next round
-//   A8 lower    : global rounds over active blocks; the CTA relaxes the staged block to local
+//   A8 lower    : global rounds over active tiles; the CTA relaxes the staged tile to local
 //                 convergence (observed, non-fixed, same-sign 26-neighbours, quasi-Euclidean
 //                 steps, 64-bit atomicMin on {distance bits, flags, parent} in shared memory),
 //                 then writes every changed voxel back with a global 64-bit atomicMin; halo
-//                 voxels that improved are pushed to their own block for the next round
-// Frontiers are per-voxel bitmasks (current / next) plus lists of active (map, block) pairs
+//                 voxels that improved are pushed to their own tile for the next round
+// Frontiers are per-voxel bitmasks (current / next) plus lists of active (map, tile) pairs
 // de-duplicated per round with monotone epoch stamps. The paper processes the open set with a
 // priority queue or a FIFO; any processing order reaches the same fixpoint (after the raise
 // phase the lower wave computes the greatest fixpoint below the current values of a monotone
@@ -30,28 +30,54 @@ namespace vbx {
 
 namespace {
 
-constexpr int kThreads = 512;
+constexpr int kThreads = 256;
 constexpr unsigned kMaxRounds = 1u << 16;
 constexpr int kMaxLocalIters = 1 << 15;
 
-// Shared-memory layout of one staged block of edge B (tile edge T = B + 2).
+// Shared-memory layout of one staged tile: an S^3 sub-block (S = min(B, 8); a 16^3 block is
+// staged as eight 8^3 octants, so a round has more independent work items) with its one-voxel
+// halo (tile edge T = S + 2).
 struct Tile {
   unsigned long long* w;  // T^3 ESDF words, halo included
-  uint16_t* a;            // active interior voxels (local index), current
+  uint16_t* a;            // active interior voxels (tile-local index), current
   uint16_t* b;            // active interior voxels, next
-  uint32_t* in;           // 2 x B^3 bits: already queued for the next local iteration (by parity)
-  uint32_t* chg;          // T^3 bits: word changed in this block-round
+  uint32_t* in;           // 2 x S^3 bits: already queued for the next local iteration (by parity)
+  uint32_t* chg;          // T^3 bits: word changed in this tile-round
   uint32_t* nslot;        // 27 pool slots of the block and its neighbours
   unsigned* cnt;          // [0..2] rotating list counts (read j%3, append (j+1)%3, clear
-                          // (j+2)%3), [3] blocks to activate in the next-round list, [4] blocks
-                          // whose lower frontier was seeded (bit k = neighbour direction k)
+                          // (j+2)%3), [3] neighbour tiles to activate in the next-round list,
+                          // [4] neighbour tiles whose lower frontier was seeded (bit k = direction
+                          // k of the neighbour tile relative to this one)
 };
+
+constexpr int kTileEdge = 8;  // sub-block edge S for B >= 8
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
-__host__ __device__ inline size_t tile_bytes(int B) {
-  const size_t T = B + 2, T3 = T * T * T, B3 = (size_t)B * B * B;
-  return align16(T3 * 8) + align16(B3 * 2) * 2 + align16(B3 / 4) + align16((T3 + 31) / 32 * 4) + align16(27 * 4) + 32;
+__host__ __device__ inline size_t tile_bytes(int S) {
+  const size_t T = S + 2, T3 = T * T * T, S3 = (size_t)S * S * S;
+  return align16(T3 * 8) + align16(S3 * 2) * 2 + align16(S3 / 4 < 16 ? 16 : S3 / 4) + align16((T3 + 31) / 32 * 4) +
+         align16(27 * 4) + 32;
+}
+
+__device__ inline Tile carve(unsigned char* base, int S) {
+  const size_t T = S + 2, T3 = T * T * T, S3 = (size_t)S * S * S;
+  Tile t;
+  size_t off = 0;
+  t.w = reinterpret_cast<unsigned long long*>(base + off);
+  off += align16(T3 * 8);
+  t.a = reinterpret_cast<uint16_t*>(base + off);
+  off += align16(S3 * 2);
+  t.b = reinterpret_cast<uint16_t*>(base + off);
+  off += align16(S3 * 2);
+  t.in = reinterpret_cast<uint32_t*>(base + off);
+  off += align16(S3 / 4 < 16 ? 16 : S3 / 4);
+  t.chg = reinterpret_cast<uint32_t*>(base + off);
+  off += align16((T3 + 31) / 32 * 4);
+  t.nslot = reinterpret_cast<uint32_t*>(base + off);
+  off += align16(27 * 4);
+  t.cnt = reinterpret_cast<unsigned*>(base + off);
+  return t;
 }
 
 // Appends v to a shared-memory list with one atomic per coalesced group of lanes.
@@ -63,120 +89,168 @@ __device__ __forceinline__ void smem_append(uint16_t* list, unsigned* count, uin
   list[base + g.thread_rank()] = v;
 }
 
-__device__ inline Tile carve(unsigned char* base, int B) {
-  const size_t T = B + 2, T3 = T * T * T, B3 = (size_t)B * B * B;
-  Tile t;
-  size_t off = 0;
-  t.w = reinterpret_cast<unsigned long long*>(base + off);
-  off += align16(T3 * 8);
-  t.a = reinterpret_cast<uint16_t*>(base + off);
-  off += align16(B3 * 2);
-  t.b = reinterpret_cast<uint16_t*>(base + off);
-  off += align16(B3 * 2);
-  t.in = reinterpret_cast<uint32_t*>(base + off);
-  off += align16(B3 / 4);
-  t.chg = reinterpret_cast<uint32_t*>(base + off);
-  off += align16((T3 + 31) / 32 * 4);
-  t.nslot = reinterpret_cast<uint32_t*>(base + off);
-  off += align16(27 * 4);
-  t.cnt = reinterpret_cast<unsigned*>(base + off);
-  return t;
-}
-
 __device__ __forceinline__ void set_bit(uint32_t* bits, uint32_t i) { atomicOr(&bits[i >> 5], 1u << (i & 31)); }
 
-// Puts (map, block) on an active list unless it is already there for this epoch.
-__device__ __forceinline__ void activate(uint2* list, unsigned* count, uint32_t* stamps, uint32_t slot, unsigned epoch,
+// Puts (map, tile) on an active list unless it is already there for this epoch.
+__device__ __forceinline__ void activate(uint2* list, unsigned* count, uint32_t* stamps, uint32_t item, unsigned epoch,
                                          unsigned mi) {
-  if (__ldcg(&stamps[slot]) >= epoch) return;
-  if (atomicMax(&stamps[slot], epoch) >= epoch) return;
+  if (__ldcg(&stamps[item]) >= epoch) return;
+  if (atomicMax(&stamps[item], epoch) >= epoch) return;
   const unsigned i = atomicAdd(count, 1u);
-  list[i] = make_uint2(mi, slot);
+  list[i] = make_uint2(mi, item);
 }
 
-// ---- block-local helpers, templated on the block edge B (tile edge T = B + 2) so that all
-// index arithmetic is by compile-time constants
+// Tile item (slot * tiles per block + tile index) of a voxel id.
+__device__ __forceinline__ uint32_t tile_item_of(const DevMap& m, uint32_t vid) {
+  const uint32_t slot = vid >> m.b3log;
+  if (m.tile_shift == 0) return slot;
+  const uint32_t l = vid & ((1u << m.b3log) - 1u);
+  const int B = m.B, blog = m.blog;
+  const uint32_t x = l & (B - 1), y = (l >> blog) & (B - 1), z = l >> (2 * blog);
+  return (slot << 3) | ((z >> 3) << 2) | ((y >> 3) << 1) | (x >> 3);
+}
 
-template <int B>
+// ---- tile geometry, templated on the block edge B and the tile edge S so that all index
+// arithmetic is by compile-time constants
+
+template <int B, int S>
 struct Geo {
-  static constexpr int T = B + 2;
+  static constexpr int T = S + 2;
   static constexpr int T3 = T * T * T;
-  static constexpr int B3 = B * B * B;
-  static constexpr int LOG = B == 4 ? 2 : (B == 8 ? 3 : 4);
+  static constexpr int S3 = S * S * S;
+  static constexpr int O = B / S;  // tiles per block and axis (1 or 2)
+  static constexpr int LOGB = B == 4 ? 2 : (B == 8 ? 3 : 4);
+  static constexpr int LOGS = S == 4 ? 2 : 3;
   __device__ static __forceinline__ int cell_of_local(int l) {
-    return (((l >> (2 * LOG)) + 1) * T + (((l >> LOG) & (B - 1)) + 1)) * T + ((l & (B - 1)) + 1);
+    return (((l >> (2 * LOGS)) + 1) * T + (((l >> LOGS) & (S - 1)) + 1)) * T + ((l & (S - 1)) + 1);
   }
   __device__ static __forceinline__ int off(int k) { return (k % 3 - 1) * T * T + ((k / 3) % 3 - 1) * T + (k / 9 - 1); }
+  __device__ static __forceinline__ void xyz(int c, int* x, int* y, int* z) {
+    *x = c % T - 1;
+    *y = (c / T) % T - 1;
+    *z = c / (T * T) - 1;
+  }
 };
 
-// Voxel id of tile cell c (coordinates -1..B per axis); kInvalid if its block does not exist.
-template <int B>
-__device__ __forceinline__ uint32_t cell_vid(const Tile& t, int c, uint32_t* slot_out) {
-  using G = Geo<B>;
-  int x = c % G::T - 1, y = (c / G::T) % G::T - 1, z = c / (G::T * G::T) - 1;
+struct TileRef {
+  uint32_t slot;  // pool slot of the block
+  int ox, oy, oz;  // tile origin inside the block
+  int tx, ty, tz;  // tile coordinates inside the block (0..O-1)
+};
+
+template <int B, int S>
+__device__ __forceinline__ TileRef tile_ref(uint32_t item) {
+  using G = Geo<B, S>;
+  TileRef r;
+  if (G::O == 1) {
+    r.slot = item;
+    r.tx = r.ty = r.tz = 0;
+  } else {
+    r.slot = item >> 3;
+    r.tx = item & 1;
+    r.ty = (item >> 1) & 1;
+    r.tz = (item >> 2) & 1;
+  }
+  r.ox = r.tx * S;
+  r.oy = r.ty * S;
+  r.oz = r.tz * S;
+  return r;
+}
+
+// Voxel id of tile cell c (tile coordinates -1..S per axis); kInvalid if its block is absent.
+template <int B, int S>
+__device__ __forceinline__ uint32_t cell_vid(const Tile& t, const TileRef& r, int c) {
+  using G = Geo<B, S>;
+  int x, y, z;
+  G::xyz(c, &x, &y, &z);
+  x += r.ox;
+  y += r.oy;
+  z += r.oz;
   const int bx = x < 0 ? -1 : (x >= B ? 1 : 0);
   const int by = y < 0 ? -1 : (y >= B ? 1 : 0);
   const int bz = z < 0 ? -1 : (z >= B ? 1 : 0);
   const uint32_t s = t.nslot[(bx + 1) * 9 + (by + 1) * 3 + (bz + 1)];
-  *slot_out = s;
   if (s == kInvalid) return kInvalid;
   x -= bx * B;
   y -= by * B;
   z -= bz * B;
-  return (s << (3 * G::LOG)) | (uint32_t)((((z << G::LOG) | y) << G::LOG) | x);
+  return (s << (3 * G::LOGB)) | (uint32_t)((((z << G::LOGB) | y) << G::LOGB) | x);
 }
 
-template <int B>
-__device__ __forceinline__ int cell_block_dir(int c) {
-  using G = Geo<B>;
-  const int x = c % G::T - 1, y = (c / G::T) % G::T - 1, z = c / (G::T * G::T) - 1;
-  const int bx = x < 0 ? -1 : (x >= B ? 1 : 0);
-  const int by = y < 0 ? -1 : (y >= B ? 1 : 0);
-  const int bz = z < 0 ? -1 : (z >= B ? 1 : 0);
-  return (bx + 1) * 9 + (by + 1) * 3 + (bz + 1);
+// Direction (0..26) of the neighbour tile that holds tile cell c, relative to this tile.
+template <int B, int S>
+__device__ __forceinline__ int cell_tile_dir(int c) {
+  using G = Geo<B, S>;
+  int x, y, z;
+  G::xyz(c, &x, &y, &z);
+  const int dx = x < 0 ? -1 : (x >= S ? 1 : 0);
+  const int dy = y < 0 ? -1 : (y >= S ? 1 : 0);
+  const int dz = z < 0 ? -1 : (z >= S ? 1 : 0);
+  return (dx + 1) * 9 + (dy + 1) * 3 + (dz + 1);
 }
 
-template <int B>
+template <int B, int S>
 __device__ __forceinline__ bool cell_interior(int c) {
-  using G = Geo<B>;
-  const int x = c % G::T - 1, y = (c / G::T) % G::T - 1, z = c / (G::T * G::T) - 1;
-  return (unsigned)x < (unsigned)B && (unsigned)y < (unsigned)B && (unsigned)z < (unsigned)B;
+  using G = Geo<B, S>;
+  int x, y, z;
+  G::xyz(c, &x, &y, &z);
+  return (unsigned)x < (unsigned)S && (unsigned)y < (unsigned)S && (unsigned)z < (unsigned)S;
 }
 
-template <int B>
+template <int B, int S>
 __device__ __forceinline__ int interior_local(int c) {
-  using G = Geo<B>;
-  const int x = c % G::T - 1, y = (c / G::T) % G::T - 1, z = c / (G::T * G::T) - 1;
-  return (((z << G::LOG) | y) << G::LOG) | x;
+  using G = Geo<B, S>;
+  int x, y, z;
+  G::xyz(c, &x, &y, &z);
+  return (((z << G::LOGS) | y) << G::LOGS) | x;
 }
 
-// Stages block `slot` of map m: its words with the one-voxel halo, and the current frontier
-// bits of its interior (cleared in global memory, appended to the active list).
-template <int B>
-__device__ void stage_block(const DevMap& m, uint32_t slot, uint32_t* cur_bits, const Tile& t) {
-  using G = Geo<B>;
-  if (threadIdx.x < 27) t.nslot[threadIdx.x] = threadIdx.x == 13 ? slot : __ldcg(&m.nbr[(size_t)slot * 27 + threadIdx.x]);
+// Item of the neighbour tile in direction k of this tile (kInvalid if its block is absent).
+template <int B, int S>
+__device__ __forceinline__ uint32_t neighbor_tile_item(const Tile& t, const TileRef& r, int k) {
+  using G = Geo<B, S>;
+  int tx = r.tx + (k / 9 - 1), ty = r.ty + ((k / 3) % 3 - 1), tz = r.tz + (k % 3 - 1);
+  const int bx = tx < 0 ? -1 : (tx >= G::O ? 1 : 0);
+  const int by = ty < 0 ? -1 : (ty >= G::O ? 1 : 0);
+  const int bz = tz < 0 ? -1 : (tz >= G::O ? 1 : 0);
+  const uint32_t s = t.nslot[(bx + 1) * 9 + (by + 1) * 3 + (bz + 1)];
+  if (s == kInvalid) return kInvalid;
+  if (G::O == 1) return s;
+  tx -= bx * G::O;
+  ty -= by * G::O;
+  tz -= bz * G::O;
+  return (s << 3) | (uint32_t)((tz << 2) | (ty << 1) | tx);
+}
+
+// Stages tile `item` of map m: its words with the one-voxel halo, and the current frontier bits
+// of its interior (cleared in global memory, appended to the active list).
+template <int B, int S>
+__device__ void stage_tile(const DevMap& m, const TileRef& r, uint32_t* cur_bits, const Tile& t) {
+  using G = Geo<B, S>;
+  if (threadIdx.x < 27) t.nslot[threadIdx.x] = threadIdx.x == 13 ? r.slot : __ldcg(&m.nbr[(size_t)r.slot * 27 + threadIdx.x]);
   if (threadIdx.x < 8) t.cnt[threadIdx.x] = 0u;
-  for (int i = threadIdx.x; i < (G::T3 + 31) / 32; i += blockDim.x) t.chg[i] = 0u;
-  for (int i = threadIdx.x; i < G::B3 / 16; i += blockDim.x) t.in[i] = 0u;
+  for (int i = threadIdx.x; i < (G::T3 + 31) / 32; i += kThreads) t.chg[i] = 0u;
+  for (int i = threadIdx.x; i < (2 * G::S3 + 31) / 32; i += kThreads) t.in[i] = 0u;
   __syncthreads();
-#pragma unroll 4
+#pragma unroll 2
   for (int c = threadIdx.x; c < G::T3; c += kThreads) {
-    uint32_t s;
-    const uint32_t vid = cell_vid<B>(t, c, &s);
+    const uint32_t vid = cell_vid<B, S>(t, r, c);
     t.w[c] = vid == kInvalid ? 0ull : __ldcg(&m.esdf[vid]);
   }
-  uint32_t* bits = cur_bits + ((size_t)slot << (3 * G::LOG)) / 32;
-  for (int j = threadIdx.x; j < G::B3 / 32; j += blockDim.x) {
-    uint32_t w = __ldcg(&bits[j]);
-    if (!w) continue;
-    bits[j] = 0u;
-    const unsigned base = atomicAdd(&t.cnt[0], (unsigned)__popc(w));
-    unsigned i = base;
-    while (w) {
-      const int bit = __ffs(w) - 1;
-      w &= w - 1;
-      t.a[i++] = (uint16_t)(j * 32 + bit);
+  // frontier bits: tile row (z, y) = S consecutive bits of the block bitmap, inside one word
+  for (int row = threadIdx.x; row < S * S; row += kThreads) {
+    const int z = row / S, y = row % S;
+    const uint32_t base = (r.slot << (3 * G::LOGB)) + (uint32_t)((((r.oz + z) << G::LOGB) | (r.oy + y)) << G::LOGB) + r.ox;
+    uint32_t* wp = &cur_bits[base >> 5];
+    const uint32_t mask = ((1u << S) - 1u) << (base & 31);
+    if (!(__ldcg(wp) & mask)) continue;
+    uint32_t chunk = (atomicAnd(wp, ~mask) & mask) >> (base & 31);
+    const unsigned at = atomicAdd(&t.cnt[0], (unsigned)__popc(chunk));
+    unsigned i = at;
+    while (chunk) {
+      const int x = __ffs(chunk) - 1;
+      chunk &= chunk - 1;
+      t.a[i++] = (uint16_t)((((z << G::LOGS) | y) << G::LOGS) | x);
     }
   }
   __syncthreads();
@@ -191,13 +265,14 @@ struct RoundArgs {
   unsigned* nxt_cnt;
 };
 
-// A7 for one staged block (all threads of the CTA; one thread per active voxel).
-template <int B>
-__device__ void raise_block(const DevMap& m, uint32_t slot, uint32_t* cur_bits, const RoundArgs& ra, EsdfCtl* ctl,
-                            unsigned char* smem, unsigned long long* pops) {
-  using G = Geo<B>;
-  const Tile t = carve(smem, B);
-  stage_block<B>(m, slot, cur_bits, t);
+// A7 for one staged tile (all threads of the CTA).
+template <int B, int S>
+__device__ void raise_tile(const DevMap& m, uint32_t item, uint32_t* cur_bits, const RoundArgs& ra, EsdfCtl* ctl,
+                           unsigned char* smem, unsigned long long* pops) {
+  using G = Geo<B, S>;
+  const Tile t = carve(smem, S);
+  const TileRef r = tile_ref<B, S>(item);
+  stage_tile<B, S>(m, r, cur_bits, t);
   const float dmax = m.dmax;
   unsigned iters = 0;
   for (int it = 0;; ++it) {
@@ -211,12 +286,13 @@ __device__ void raise_block(const DevMap& m, uint32_t slot, uint32_t* cur_bits, 
     const uint16_t* cur = (it & 1) ? t.b : t.a;
     uint16_t* nxt = (it & 1) ? t.a : t.b;
     unsigned* ncnt = &t.cnt[(it + 1) % 3];
-    uint32_t* inb = t.in + (it & 1) * (G::B3 / 32);
+    uint32_t* inb = t.in + (it & 1) * (G::S3 / 32 > 0 ? G::S3 / 32 : 1);
     if (threadIdx.x == 0) {
       *pops += na;
       t.cnt[(it + 2) % 3] = 0u;
     }
-    for (int j = threadIdx.x; j < G::B3 / 32; j += kThreads) t.in[((it + 1) & 1) * (G::B3 / 32) + j] = 0u;
+    for (int j = threadIdx.x; j < (G::S3 + 31) / 32; j += kThreads)
+      t.in[((it + 1) & 1) * (G::S3 / 32 > 0 ? G::S3 / 32 : 1) + j] = 0u;
     // reset the raised voxels first, so that no child test below sees a stale parent
     for (unsigned i = threadIdx.x; i < na; i += kThreads) {
       const int c = G::cell_of_local(cur[i]);
@@ -238,21 +314,17 @@ __device__ void raise_block(const DevMap& m, uint32_t slot, uint32_t* cur_bits, 
       const unsigned nfl = ew_flags(nw);
       if (!(nfl & kObserved)) continue;
       if (!(nfl & kFixed) && ew_parent(nw) == (unsigned)(26 - k)) {  // a child: raise it
-        if (cell_interior<B>(nc)) {
-          const int nl = interior_local<B>(nc);
+        if (cell_interior<B, S>(nc)) {
+          const int nl = interior_local<B, S>(nc);
           const uint32_t bit = 1u << (nl & 31);
           if (!(atomicOr(&inb[nl >> 5], bit) & bit)) smem_append(nxt, ncnt, (uint16_t)nl);
         } else {
-          uint32_t s;
-          const uint32_t nvid = cell_vid<B>(t, nc, &s);
-          set_bit(ra.nxt_bits, nvid);
-          atomicOr(&t.cnt[3], 1u << cell_block_dir<B>(nc));
+          set_bit(ra.nxt_bits, cell_vid<B, S>(t, r, nc));
+          atomicOr(&t.cnt[3], 1u << cell_tile_dir<B, S>(nc));
         }
       } else {  // any other observed neighbour re-seeds the lower wave
-        uint32_t s;
-        const uint32_t nvid = cell_vid<B>(t, nc, &s);
-        set_bit(m.lbits0, nvid);
-        atomicOr(&t.cnt[4], 1u << cell_block_dir<B>(nc));
+        set_bit(m.lbits0, cell_vid<B, S>(t, r, nc));
+        atomicOr(&t.cnt[4], 1u << cell_tile_dir<B, S>(nc));
       }
     }
     __syncthreads();
@@ -261,26 +333,31 @@ __device__ void raise_block(const DevMap& m, uint32_t slot, uint32_t* cur_bits, 
   // write back the raised voxels (raise rounds never lower words, plain stores suffice)
   for (int c = threadIdx.x; c < G::T3; c += kThreads) {
     if (!(t.chg[c >> 5] & (1u << (c & 31)))) continue;
-    uint32_t s;
-    const uint32_t vid = cell_vid<B>(t, c, &s);
-    m.esdf[vid] = t.w[c];
+    m.esdf[cell_vid<B, S>(t, r, c)] = t.w[c];
   }
-  // activate the blocks that received raise (next round) or lower (seed) frontier bits
+  // activate the tiles that received raise (next round) or lower (seed) frontier bits
   if (threadIdx.x < 27) {
-    const uint32_t s = t.nslot[threadIdx.x];
-    if (s != kInvalid && (t.cnt[3] >> threadIdx.x & 1u)) activate(ra.nxt_list, ra.nxt_cnt, m.bstamp_r, s, ra.ep_next, ra.mi);
-    if (s != kInvalid && (t.cnt[4] >> threadIdx.x & 1u)) activate(ctl->lact0, &ctl->lcnt[0], m.bstamp_l, s, ra.e0, ra.mi);
+    const int k = threadIdx.x;
+    const bool rz = t.cnt[3] >> k & 1u, lz = t.cnt[4] >> k & 1u;
+    if (rz || lz) {
+      const uint32_t nit = neighbor_tile_item<B, S>(t, r, k);
+      if (nit != kInvalid) {
+        if (rz) activate(ra.nxt_list, ra.nxt_cnt, m.bstamp_r, nit, ra.ep_next, ra.mi);
+        if (lz) activate(ctl->lact0, &ctl->lcnt[0], m.bstamp_l, nit, ra.e0, ra.mi);
+      }
+    }
   }
   __syncthreads();
 }
 
-// A8 for one staged block (all threads of the CTA; one thread per active voxel).
-template <int B>
-__device__ void lower_block(const DevMap& m, uint32_t slot, uint32_t* cur_bits, const RoundArgs& ra, EsdfCtl* ctl,
-                            unsigned char* smem, unsigned long long* pops) {
-  using G = Geo<B>;
-  const Tile t = carve(smem, B);
-  stage_block<B>(m, slot, cur_bits, t);
+// A8 for one staged tile (all threads of the CTA).
+template <int B, int S>
+__device__ void lower_tile(const DevMap& m, uint32_t item, uint32_t* cur_bits, const RoundArgs& ra, EsdfCtl* ctl,
+                           unsigned char* smem, unsigned long long* pops) {
+  using G = Geo<B, S>;
+  const Tile t = carve(smem, S);
+  const TileRef r = tile_ref<B, S>(item);
+  stage_tile<B, S>(m, r, cur_bits, t);
   const float L1 = m.L1, L2 = m.L2, L3 = m.L3;
   unsigned iters = 0;
   for (int it = 0;; ++it) {
@@ -294,12 +371,13 @@ __device__ void lower_block(const DevMap& m, uint32_t slot, uint32_t* cur_bits, 
     const uint16_t* cur = (it & 1) ? t.b : t.a;
     uint16_t* nxt = (it & 1) ? t.a : t.b;
     unsigned* ncnt = &t.cnt[(it + 1) % 3];
-    uint32_t* inb = t.in + (it & 1) * (G::B3 / 32);
+    uint32_t* inb = t.in + (it & 1) * (G::S3 / 32 > 0 ? G::S3 / 32 : 1);
     if (threadIdx.x == 0) {
       *pops += na;
       t.cnt[(it + 2) % 3] = 0u;
     }
-    for (int j = threadIdx.x; j < G::B3 / 32; j += kThreads) t.in[((it + 1) & 1) * (G::B3 / 32) + j] = 0u;
+    for (int j = threadIdx.x; j < (G::S3 + 31) / 32; j += kThreads)
+      t.in[((it + 1) & 1) * (G::S3 / 32 > 0 ? G::S3 / 32 : 1) + j] = 0u;
     for (unsigned p = threadIdx.x; p < na * 26u; p += kThreads) {
       const unsigned i = p / 26u;
       const int kk = (int)(p - i * 26u);
@@ -321,8 +399,8 @@ __device__ void lower_block(const DevMap& m, uint32_t slot, uint32_t* cur_bits, 
       const unsigned long long old = atomicMin(&t.w[nc], ew_pack(neg ? -cand : cand, nfl, (unsigned)(26 - k)));
       if (!(fabsf(ew_d(old)) > cand)) continue;
       atomicOr(&t.chg[nc >> 5], 1u << (nc & 31));
-      if (cell_interior<B>(nc)) {
-        const int nl = interior_local<B>(nc);
+      if (cell_interior<B, S>(nc)) {
+        const int nl = interior_local<B, S>(nc);
         const uint32_t bit = 1u << (nl & 31);
         if (!(atomicOr(&inb[nl >> 5], bit) & bit)) smem_append(nxt, ncnt, (uint16_t)nl);
       }
@@ -331,41 +409,40 @@ __device__ void lower_block(const DevMap& m, uint32_t slot, uint32_t* cur_bits, 
   }
   if (threadIdx.x == 0) atomicAdd(&m.ctr->esdf_local_iters, iters);
   // write back: the global word keeps the smaller value (fire-and-forget atomicMin); a halo
-  // voxel this block lowered is pushed to its own block for the next round (a push of a voxel
-  // that another block lowered even further is redundant work, never wrong)
+  // voxel this tile lowered is pushed to its own tile for the next round (a push of a voxel
+  // that another tile lowered even further is redundant work, never wrong)
   for (int c = threadIdx.x; c < G::T3; c += kThreads) {
     if (!(t.chg[c >> 5] & (1u << (c & 31)))) continue;
-    uint32_t s;
-    const uint32_t vid = cell_vid<B>(t, c, &s);
+    const uint32_t vid = cell_vid<B, S>(t, r, c);
     atomicMin(&m.esdf[vid], t.w[c]);
-    if (!cell_interior<B>(c)) {
+    if (!cell_interior<B, S>(c)) {
       set_bit(ra.nxt_bits, vid);
-      atomicOr(&t.cnt[3], 1u << cell_block_dir<B>(c));
+      atomicOr(&t.cnt[3], 1u << cell_tile_dir<B, S>(c));
     }
   }
   __syncthreads();
-  if (threadIdx.x < 27) {
-    const uint32_t s = t.nslot[threadIdx.x];
-    if (s != kInvalid && (t.cnt[3] >> threadIdx.x & 1u)) activate(ra.nxt_list, ra.nxt_cnt, m.bstamp_l, s, ra.ep_next, ra.mi);
+  if (threadIdx.x < 27 && (t.cnt[3] >> threadIdx.x & 1u)) {
+    const uint32_t nit = neighbor_tile_item<B, S>(t, r, threadIdx.x);
+    if (nit != kInvalid) activate(ra.nxt_list, ra.nxt_cnt, m.bstamp_l, nit, ra.ep_next, ra.mi);
   }
   __syncthreads();
 }
 
-__device__ __forceinline__ void raise_dispatch(const DevMap& m, uint32_t slot, uint32_t* cur_bits, const RoundArgs& ra,
+__device__ __forceinline__ void raise_dispatch(const DevMap& m, uint32_t item, uint32_t* cur_bits, const RoundArgs& ra,
                                                EsdfCtl* ctl, unsigned char* smem, unsigned long long* pops) {
   switch (m.B) {
-    case 4: raise_block<4>(m, slot, cur_bits, ra, ctl, smem, pops); break;
-    case 8: raise_block<8>(m, slot, cur_bits, ra, ctl, smem, pops); break;
-    default: raise_block<16>(m, slot, cur_bits, ra, ctl, smem, pops); break;
+    case 4: raise_tile<4, 4>(m, item, cur_bits, ra, ctl, smem, pops); break;
+    case 8: raise_tile<8, 8>(m, item, cur_bits, ra, ctl, smem, pops); break;
+    default: raise_tile<16, kTileEdge>(m, item, cur_bits, ra, ctl, smem, pops); break;
   }
 }
 
-__device__ __forceinline__ void lower_dispatch(const DevMap& m, uint32_t slot, uint32_t* cur_bits, const RoundArgs& ra,
+__device__ __forceinline__ void lower_dispatch(const DevMap& m, uint32_t item, uint32_t* cur_bits, const RoundArgs& ra,
                                                EsdfCtl* ctl, unsigned char* smem, unsigned long long* pops) {
   switch (m.B) {
-    case 4: lower_block<4>(m, slot, cur_bits, ra, ctl, smem, pops); break;
-    case 8: lower_block<8>(m, slot, cur_bits, ra, ctl, smem, pops); break;
-    default: lower_block<16>(m, slot, cur_bits, ra, ctl, smem, pops); break;
+    case 4: lower_tile<4, 4>(m, item, cur_bits, ra, ctl, smem, pops); break;
+    case 8: lower_tile<8, 8>(m, item, cur_bits, ra, ctl, smem, pops); break;
+    default: lower_tile<16, kTileEdge>(m, item, cur_bits, ra, ctl, smem, pops); break;
   }
 }
 
@@ -422,7 +499,7 @@ __global__ void __launch_bounds__(kThreads) k_esdf(const DevMap* __restrict__ ma
     const unsigned fl = ew_flags(w);
     const bool obs = (fl & kObserved) != 0;
     const float de = ew_d(w);
-    const uint32_t slot = vid >> m.b3log;
+    const uint32_t slot = tile_item_of(m, vid);
     if (fabsf(Df) < m.gamma) {  // isFixed, evaluated on the TSDF voxel
       atomicAdd(&m.ctr->seeds, 1u);
       const bool lower_only = !obs || (((de < 0.0f) == neg) && fabsf(Df) <= fabsf(de));
@@ -446,7 +523,7 @@ __global__ void __launch_bounds__(kThreads) k_esdf(const DevMap* __restrict__ ma
         if (n == kInvalid) continue;
         if (ew_flags(__ldcg(&m.esdf[n])) & kObserved) {
           set_bit(m.lbits0, n);
-          const uint32_t nb = n >> m.b3log;
+          const uint32_t nb = tile_item_of(m, n);
           if (nb != last) activate(ctl->lact0, &ctl->lcnt[0], m.bstamp_l, nb, e0, mi);
           last = nb;
         }
@@ -534,10 +611,10 @@ __global__ void __launch_bounds__(kThreads) k_esdf(const DevMap* __restrict__ ma
 
 }  // namespace
 
-size_t esdf_smem_bytes(int max_B) { return tile_bytes(max_B); }
+size_t esdf_smem_bytes(int max_B) { return tile_bytes(max_B < kTileEdge ? max_B : kTileEdge); }
 
 int esdf_grid(int num_sms, int max_B, int ctas_per_sm) {
-  const size_t smem = tile_bytes(max_B);
+  const size_t smem = esdf_smem_bytes(max_B);
   if (cudaFuncSetAttribute(k_esdf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_esdf, kThreads, smem) != cudaSuccess) return 0;
@@ -550,7 +627,7 @@ cudaError_t launch_esdf(const DevMap* maps_dev, int nmaps, int max_B, EsdfCtl* c
   if (nmaps <= 0 || nmaps > kMaxBatch) return cudaErrorInvalidValue;
   const int grid = esdf_grid(cfg.num_sms, max_B, cfg.tune.esdf_ctas_per_sm);
   if (grid <= 0) return cudaErrorCooperativeLaunchTooLarge;
-  const size_t smem = tile_bytes(max_B);
+  const size_t smem = esdf_smem_bytes(max_B);
   void* args[] = {(void*)&maps_dev, (void*)&nmaps, (void*)&ctl};
   hook->begin(kKEsdf, cfg.stream);
   cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_esdf, dim3(grid), dim3(kThreads), args, smem, cfg.stream);

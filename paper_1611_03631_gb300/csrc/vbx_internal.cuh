@@ -13,7 +13,8 @@
 //                    esdf[vid]   u64 packed {d f32 | flags u8 | parent u8} 8 B
 //                    vflags[vid] u8 (bit0 queued for the ESDF)
 //                    rbits/lbits[2][vid/32] u32 raise / lower frontier bitmasks (current, next)
-//   per block      : bstamp_r/bstamp_l[slot] u32 epochs de-duplicating block activations
+//   per ESDF tile  : bstamp_r/bstamp_l[item] u32 epochs de-duplicating tile activations, item =
+//                    slot << tile_shift | tile (a tile is the block, or an 8^3 octant of a 16^3 one)
 //   lists          : updated (last scan), dirty (since last ESDF); the ESDF's active
 //                    (map, block) lists live in the launch group's EsdfCtl
 //   per-scan scratch: group hash table (64 B entries), group list, rays (float4)
@@ -108,6 +109,7 @@ struct DevMap {
   float range_lim2;  // (16384 v)^2: points farther than 2^14 voxels are dropped
   float L1, L2, L3;  // quasi-Euclidean step lengths v, v*sqrt(2), v*sqrt(3)
   int B, blog, b3log;
+  int tile_shift;  // log2 of the ESDF tiles per block: 3 for B = 16 (8^3 octants), else 0
   int weighting, grouped;
   // block hash
   unsigned long long* hkeys;
