@@ -266,6 +266,7 @@ def run_gpu(args):
     clocks.start()
     launches0 = vbx.total_launches()
     step_ms, tsdf_upd, esdf_upd, records, rounds, visits, liters = [], 0, 0, 0, 0, 0, 0
+    phase_ns = [0, 0, 0]
     for i in order[args.warmup:]:
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -282,6 +283,9 @@ def run_gpu(args):
         rounds += st["raise_rounds"] + st["lower_rounds"]
         visits += st["esdf_block_visits"]
         liters += st["esdf_local_iters"]
+        phase_ns[0] += st["esdf_classify_ns"]
+        phase_ns[1] += st["esdf_raise_ns"]
+        phase_ns[2] += st["esdf_lower_ns"]
     torch.cuda.synchronize()
     gpu_launches = vbx.total_launches() - launches0 - 0
     clk = clocks.stop()
@@ -412,6 +416,7 @@ def run_gpu(args):
         "esdf_rounds_per_scan": rounds / args.steps,
         "esdf_block_visits_per_scan": visits / args.steps,
         "esdf_local_iters_per_visit": liters / max(visits, 1),
+        "esdf_phase_ms_per_scan": {k: v / 1e6 / args.steps for k, v in zip(("classify", "raise", "lower"), phase_ns)},
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "scans/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -129,8 +129,11 @@ typedef struct {
   int64_t raise_rounds;
   int64_t lower_rounds;
   int64_t launches;       /* kernels launched by this map since creation                    */
-  int64_t esdf_block_visits; /* blocks staged in shared memory by the last ESDF update       */
+  int64_t esdf_block_visits; /* tiles staged in shared memory by the last ESDF update        */
   int64_t esdf_local_iters;  /* local relaxation iterations summed over those stagings       */
+  int64_t esdf_classify_ns;  /* device time of the classification phase of the last update  */
+  int64_t esdf_raise_ns;     /* ... of the raise rounds                                       */
+  int64_t esdf_lower_ns;     /* ... of the lower rounds                                       */
 } vbx_stats;
 
 /* Synchronises `stream`, then fills *out. Returns the sticky device error if one is set. */

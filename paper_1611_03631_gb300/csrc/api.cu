@@ -452,6 +452,9 @@ vbx_status vbx_get_stats(vbx_map_t m, vbx_stats* out, void* stream) {
   out->launches = m->hook.launches;
   out->esdf_block_visits = c.esdf_block_visits;
   out->esdf_local_iters = c.esdf_local_iters;
+  out->esdf_classify_ns = c.esdf_phase_ns[0];
+  out->esdf_raise_ns = c.esdf_phase_ns[1];
+  out->esdf_lower_ns = c.esdf_phase_ns[2];
   return read_error(m, (cudaStream_t)stream);
 }
 

@@ -465,6 +465,7 @@ __global__ void __launch_bounds__(kThreads) k_esdf(const DevMap* __restrict__ ma
   __shared__ unsigned long long cta_pops;
   const unsigned tid = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned nthreads = gridDim.x * blockDim.x;
+  const unsigned long long t_start = global_ns();
 
   // ---------------------------------------------------------------- A6: classification
   // exclusive prefix of the maps' dirty counts (Hillis-Steele scan in shared memory)
@@ -535,6 +536,7 @@ __global__ void __launch_bounds__(kThreads) k_esdf(const DevMap* __restrict__ ma
     }
   }
   if (!grid_barrier(&ctl->bar, gridDim.x, &ctl->error)) return;
+  const unsigned long long t_classified = global_ns();
 
   // ------------------------------------------------------------------------ A7: raise
   unsigned r = 0;
@@ -567,6 +569,7 @@ __global__ void __launch_bounds__(kThreads) k_esdf(const DevMap* __restrict__ ma
     if (!grid_barrier(&ctl->bar, gridDim.x, &ctl->error)) return;
   }
   const unsigned raise_rounds = r;
+  const unsigned long long t_raised = global_ns();
 
   // ------------------------------------------------------------------------ A8: lower
   unsigned l = 0;
@@ -598,8 +601,12 @@ __global__ void __launch_bounds__(kThreads) k_esdf(const DevMap* __restrict__ ma
     }
     if (!grid_barrier(&ctl->bar, gridDim.x, &ctl->error)) return;
   }
+  const unsigned long long t_end = global_ns();
   for (unsigned i = tid; i < (unsigned)nmaps; i += nthreads) {
     Counters* c = maps[i].ctr;
+    c->esdf_phase_ns[0] = (unsigned)(t_classified - t_start);
+    c->esdf_phase_ns[1] = (unsigned)(t_raised - t_classified);
+    c->esdf_phase_ns[2] = (unsigned)(t_end - t_raised);
     c->esdf_in = pfx[i + 1] - pfx[i];
     c->raise_rounds = raise_rounds;
     c->lower_rounds = l;

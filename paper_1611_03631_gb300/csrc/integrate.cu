@@ -139,6 +139,7 @@ __global__ void __launch_bounds__(kThreads) k_reset_counters(Batch b) {
     c->esdf_in = 0;
     c->esdf_block_visits = 0;
     c->esdf_local_iters = 0;
+    c->esdf_phase_ns[0] = c->esdf_phase_ns[1] = c->esdf_phase_ns[2] = 0;
   }
 }
 
@@ -190,18 +191,21 @@ __global__ void __launch_bounds__(kThreads) k_bin_points(Batch b) {
           wq = m.weighting == 0 ? 1ull : (unsigned long long)__float2ll_rn(__fmul_rn(w, 1048576.0f));
         }
       }
-      if (valid) {
-        if (!m.grouped) {  // one ray per point
-          const unsigned r = atomicAdd(&m.ctr->ngroups, 1u);
-          m.rays[r] = make_float4(pw[0], pw[1], pw[2], w);
-          valid = false;
-          atomicAdd(&m.ctr->npoints_valid, 1u);
-          key = kEmptyKey;
-        }
+      if (valid && !m.grouped) {  // one ray per point
+        const unsigned r = atomicAdd(&m.ctr->ngroups, 1u);
+        m.rays[r] = make_float4(pw[0], pw[1], pw[2], w);
       }
     }
+    // accepted points, counted once per warp and map
+    const unsigned mpeers = __match_any_sync(kFull, mi);
+    const unsigned vmask = __ballot_sync(kFull, valid);
+    if (lane == __ffs(mpeers) - 1 && (vmask & mpeers)) atomicAdd(&map_of(b, mi).ctr->npoints_valid, (unsigned)__popc(vmask & mpeers));
+    if (valid && !map_of(b, mi).grouped) {
+      valid = false;
+      key = kEmptyKey;
+    }
     // warp pre-aggregation of points of one map that share a voxel (neighbouring pixels usually do)
-    const unsigned peers = __match_any_sync(kFull, key) & __match_any_sync(kFull, mi);
+    const unsigned peers = __match_any_sync(kFull, key) & mpeers;
     const int leader = __ffs(peers) - 1;
     sh_w[wid][lane] = wq;
     for (int r = 0; r < 3; ++r) sh_o[r][wid][lane] = wq * o[r];
@@ -214,7 +218,6 @@ __global__ void __launch_bounds__(kThreads) k_bin_points(Batch b) {
         sw += sh_w[wid][src];
         for (int r = 0; r < 3; ++r) so[r] += sh_o[r][wid][src];
       }
-      atomicAdd(&m.ctr->npoints_valid, (unsigned)__popc(peers));
       uint32_t h = hash64(key) & m.gmask;
       bool placed = false;
       for (uint32_t probe = 0; probe <= m.gmask; ++probe) {

@@ -82,8 +82,9 @@ struct Counters {
   unsigned long long lower_pops;
   unsigned int seeds;
   unsigned int esdf_in;
-  unsigned int esdf_block_visits;  // staged block-rounds
-  unsigned int esdf_local_iters;   // local relaxation iterations summed over block-rounds
+  unsigned int esdf_block_visits;  // staged tile-rounds
+  unsigned int esdf_local_iters;   // local relaxation iterations summed over tile-rounds
+  unsigned int esdf_phase_ns[3];   // device time of classification, raise and lower phases
 };
 
 // Control block of one ESDF launch: one map, or a batch of maps updated by the same
@@ -328,6 +329,12 @@ struct Dda {
     return 2;
   }
 };
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 // ---------------------------------------------------------------------------------------
 // grid-wide barrier for cooperative launches, with a bounded wait

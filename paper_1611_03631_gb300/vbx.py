@@ -67,6 +67,9 @@ class vbx_stats(ctypes.Structure):
             "launches",
             "esdf_block_visits",
             "esdf_local_iters",
+            "esdf_classify_ns",
+            "esdf_raise_ns",
+            "esdf_lower_ns",
         )
     ]
 
