@@ -202,10 +202,11 @@ typedef struct {
 
 enum { VBX_STEP_INTEGRATE = 1, VBX_STEP_ESDF = 2, VBX_STEP_QUERY = 4, VBX_STEP_GRAPH = 8 };
 
-/* Creates a batch of `count` slots (1..256) bound to maps[0..count). max_points and max_queries
- * bound n per slot and step (the maps' scratch is grown to max_points here). */
-vbx_status vbx_batch_create(const vbx_map_t* maps, int count, int64_t max_points, int64_t max_queries,
-                            vbx_batch_t* out);
+/* Creates a batch of `count` slots (1..256) bound to maps[0..count). max_queries bounds the
+ * query count per slot and step. A slot's scan may hold at most as many points as its map's
+ * per-scan capacity (vbx_map_options.max_points rounded up to a power of two, or the largest
+ * scan the map has integrated alone); batches never grow a map's scratch. */
+vbx_status vbx_batch_create(const vbx_map_t* maps, int count, int64_t max_queries, vbx_batch_t* out);
 
 /* Rebinds slot `slot` to `map` (same device, not bound to another slot); synchronises. */
 vbx_status vbx_batch_bind(vbx_batch_t batch, int slot, vbx_map_t map);
@@ -226,6 +227,17 @@ vbx_status vbx_batch_autotune(vbx_batch_t batch, const vbx_scan_in* scans, const
 vbx_status vbx_batch_sync(vbx_batch_t batch, void* stream);
 
 vbx_status vbx_batch_destroy(vbx_batch_t batch);
+
+/* Device bytes a map created with these parameters allocates (pool, hash, lists, per-scan
+ * scratch for opt->max_points points), for admission control against a memory budget. */
+vbx_status vbx_map_bytes(int voxels_per_block, const vbx_map_options* opt, int64_t* bytes_out);
+
+/* Device bytes the map holds now. */
+vbx_status vbx_map_device_bytes(vbx_map_t map, int64_t* bytes_out);
+
+/* Empties the map (no blocks, no observed voxels, nothing queued) without freeing its memory,
+ * so that it can serve a new session. Synchronises `stream`. */
+vbx_status vbx_reset_map(vbx_map_t map, void* stream);
 
 /* Kernels launched by all maps of this process (a running counter). */
 int64_t vbx_total_launches(void);

@@ -136,12 +136,15 @@ struct vbx_map_s {
 
   vbx::LaunchCfg cfg(void* stream) const { return vbx::LaunchCfg{num_sms, (cudaStream_t)stream, vbx::kDefaultTuning}; }
 
+  std::vector<size_t> alloc_bytes;
+
   template <typename T>
   cudaError_t alloc(T** p, size_t count, int fill_byte) {
     void* q = nullptr;
     cudaError_t e = cudaMalloc(&q, std::max<size_t>(count * sizeof(T), 16));
     if (e != cudaSuccess) return e;
     allocs.push_back(q);
+    alloc_bytes.push_back(std::max<size_t>(count * sizeof(T), 16));
     e = cudaMemset(q, fill_byte, std::max<size_t>(count * sizeof(T), 16));
     *p = (T*)q;
     return e;
@@ -149,7 +152,10 @@ struct vbx_map_s {
   void release(void* p) {
     if (!p) return;
     auto it = std::find(allocs.begin(), allocs.end(), p);
-    if (it != allocs.end()) allocs.erase(it);
+    if (it != allocs.end()) {
+      alloc_bytes.erase(alloc_bytes.begin() + (it - allocs.begin()));
+      allocs.erase(it);
+    }
     cudaFree(p);
   }
   ~vbx_map_s() {
@@ -609,7 +615,7 @@ struct vbx_batch_s {
   int device = 0;
   int num_sms = 0;
   int max_B = 4;
-  int64_t max_points = 0, max_queries = 0;
+  int64_t max_queries = 0;
   std::vector<vbx_map_t> maps;
   // device descriptor block: DevMap[count] | ScanDesc[count] | QueryDesc[count]
   unsigned char* dev_block = nullptr;
@@ -689,8 +695,9 @@ vbx_status batch_stage(vbx_batch_t b, const vbx_scan_in* scans, const vbx_query_
   for (int i = 0; i < b->count; ++i) {
     if (flags & VBX_STEP_INTEGRATE) {
       if (!scans) return fail(VBX_ERR_INVALID_ARG, "scans is NULL");
-      if (scans[i].n < 0 || scans[i].n > b->max_points)
-        return fail(VBX_ERR_INVALID_ARG, "slot %d: n = %lld outside [0, max_points]", i, (long long)scans[i].n);
+      if (scans[i].n < 0 || scans[i].n > b->maps[i]->pts_cap)
+        return fail(VBX_ERR_INVALID_ARG, "slot %d: n = %lld outside [0, %lld], the map's per-scan capacity", i,
+                    (long long)scans[i].n, (long long)b->maps[i]->pts_cap);
       if (scans[i].n > 0 && !scans[i].points_dev) return fail(VBX_ERR_INVALID_ARG, "slot %d: points_dev is NULL", i);
     }
     if (flags & VBX_STEP_QUERY) {
@@ -776,12 +783,11 @@ vbx_status batch_run(vbx_batch_t b, const vbx_scan_in* scans, const vbx_query_io
 
 extern "C" {
 
-vbx_status vbx_batch_create(const vbx_map_t* maps, int count, int64_t max_points, int64_t max_queries, vbx_batch_t* out) {
+vbx_status vbx_batch_create(const vbx_map_t* maps, int count, int64_t max_queries, vbx_batch_t* out) {
   if (!out) return fail(VBX_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (!maps || count < 1 || count > vbx::kMaxBatch) return fail(VBX_ERR_INVALID_ARG, "count must lie in [1, %d]", vbx::kMaxBatch);
-  if (max_points < 0 || max_points > (int64_t(1) << 28) || max_queries < 0 || max_queries > (int64_t(1) << 26))
-    return fail(VBX_ERR_INVALID_ARG, "max_points / max_queries out of range");
+  if (max_queries < 0 || max_queries > (int64_t(1) << 26)) return fail(VBX_ERR_INVALID_ARG, "max_queries out of range");
   int device = 0;
   cudaError_t e = cudaGetDevice(&device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
@@ -795,16 +801,10 @@ vbx_status vbx_batch_create(const vbx_map_t* maps, int count, int64_t max_points
   b->count = count;
   b->device = device;
   b->num_sms = maps[0]->num_sms;
-  b->max_points = max_points;
   b->max_queries = max_queries;
   b->maps.assign(maps, maps + count);
   uint64_t cap_sum = 0;
   for (int i = 0; i < count; ++i) {
-    vbx_status st = ensure_scratch(maps[i], std::max<int64_t>(max_points, 1), 0);
-    if (st != VBX_OK) {
-      delete b;
-      return st;
-    }
     b->max_B = std::max(b->max_B, maps[i]->B);
     cap_sum += (uint64_t)maps[i]->d.cap_blocks << maps[i]->d.tile_shift;
   }
@@ -856,8 +856,6 @@ vbx_status vbx_batch_bind(vbx_batch_t b, int slot, vbx_map_t map) {
     if (j != slot && b->maps[j] == map) return fail(VBX_ERR_INVALID_ARG, "map already bound to slot %d", j);
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(e, "bind sync");
-  vbx_status st = ensure_scratch(map, std::max<int64_t>(b->max_points, 1), 0);
-  if (st != VBX_OK) return st;
   if (map->B > b->max_B) {  // the ESDF launch's shared-memory tile must fit the largest block
     b->max_B = map->B;
     b->drop_graphs();
@@ -968,6 +966,80 @@ vbx_status vbx_batch_sync(vbx_batch_t b, void* stream) {
 
 vbx_status vbx_batch_destroy(vbx_batch_t b) {
   delete b;
+  return VBX_OK;
+}
+
+vbx_status vbx_map_bytes(int B, const vbx_map_options* opt_in, int64_t* out) {
+  if (!out) return fail(VBX_ERR_INVALID_ARG, "bytes_out is NULL");
+  if (B != 4 && B != 8 && B != 16) return fail(VBX_ERR_INVALID_ARG, "voxels_per_block must be 4, 8 or 16");
+  vbx_map_options opt;
+  vbx_default_options(&opt);
+  if (opt_in) opt = *opt_in;
+  const uint64_t B3 = (uint64_t)B * B * B;
+  const uint64_t cap = opt.block_capacity > 0 ? (uint64_t)opt.block_capacity : (uint64_t(1) << 25) / B3;
+  const uint64_t V = cap * B3;
+  const uint64_t tiles = cap << (B == 16 ? 3 : 0);
+  const uint64_t H = next_pow2(cap * 2);
+  const uint64_t pts = next_pow2((uint64_t)std::max<int64_t>(opt.max_points > 0 ? opt.max_points : (int64_t(1) << 20), 1024));
+  const uint64_t entries = next_pow2(pts * 2);
+  uint64_t bytes = 0;
+  bytes += H * (8 + 4);                                   // block hash
+  bytes += cap * (12 + 27 * 4 + 4 + 4);                   // block coords, links, touch flag, new list
+  bytes += V * (8 + 32 + 4 + 8 + 1 + 4 + 4);              // tsdf, sums, touch, esdf, flags, lists
+  bytes += 4 * (V / 32) * 4;                              // frontier bitmasks
+  bytes += tiles * (2 * 4 + 4 * 8);                       // tile stamps, active lists
+  bytes += entries * sizeof(vbx::GroupEntry) + pts * (4 + 16);  // per-scan scratch
+  *out = (int64_t)bytes;
+  return VBX_OK;
+}
+
+vbx_status vbx_map_device_bytes(vbx_map_t m, int64_t* out) {
+  if (!m || !out) return fail(VBX_ERR_INVALID_ARG, "map or bytes_out is NULL");
+  size_t total = 0;
+  for (size_t b : m->alloc_bytes) total += b;
+  *out = (int64_t)total;
+  return VBX_OK;
+}
+
+vbx_status vbx_reset_map(vbx_map_t m, void* stream) {
+  if (!m) return fail(VBX_ERR_INVALID_ARG, "map is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "reset sync");
+  vbx::Counters c;
+  if ((e = cudaMemcpy(&c, m->d.ctr, sizeof(c), cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_fail(e, "reset counters");
+  const size_t nb = std::min<size_t>(c.blocks, m->d.cap_blocks);
+  const size_t B3 = (size_t)m->B * m->B * m->B;
+  const size_t V = nb * B3;
+  vbx::DevMap& d = m->d;
+  const size_t tiles = nb << d.tile_shift;
+  struct Clear {
+    void* p;
+    size_t bytes;
+    int fill;
+  } clears[] = {
+      {d.hkeys, ((size_t)d.hmask + 1) * 8, 0xff},
+      {d.hvals, ((size_t)d.hmask + 1) * 4, 0xff},
+      {d.nbr, nb * 27 * 4, 0xff},
+      {d.bcoord, nb * 12, 0},
+      {d.btouch, nb * 4, 0},
+      {d.tsdf, V * 8, 0},
+      {d.acc, V * 32, 0},
+      {d.touch, V * 4, 0},
+      {d.esdf, V * 8, 0},
+      {d.vflags, V, 0},
+      {d.rbits0, V / 8, 0},
+      {d.rbits1, V / 8, 0},
+      {d.lbits0, V / 8, 0},
+      {d.lbits1, V / 8, 0},
+      {d.bstamp_r, tiles * 4, 0},
+      {d.bstamp_l, tiles * 4, 0},
+      {d.ctr, sizeof(vbx::Counters), 0},
+  };
+  for (const Clear& x : clears)
+    if (x.bytes && (e = cudaMemsetAsync(x.p, x.fill, x.bytes, s)) != cudaSuccess) return cuda_fail(e, "reset clear");
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "reset sync");
+  m->last_points_in = 0;
   return VBX_OK;
 }
 

@@ -276,6 +276,7 @@ def room(
     seed: int = 2,
     size: float = 10.0,
     voxel_size: float = 0.05,
+    block: int = 16,
 ) -> ScanSet:
     """10 x 10 x 3 m room with seeded objects and an RGB-D camera random walk."""
     if cx is None:
@@ -322,7 +323,7 @@ def room(
         poses.append(_pose(R, pos))
     params = dict(
         voxel_size=voxel_size,
-        voxels_per_block=16,
+        voxels_per_block=block,
         truncation=2.0 * voxel_size,
         max_esdf_dist=2.0,
         weighting=1,
@@ -514,6 +515,63 @@ def random_queries(scans: ScanSet, n: int, radius: float = 2.0, seed: int = 5, s
     d /= np.linalg.norm(d, axis=1, keepdims=True)
     r = radius * rng.uniform(0.0, 1.0, n) ** (1.0 / 3.0)
     return (centers[k] + d * r[:, None]).astype(np.float32)
+
+
+def _mix_one(args):
+    kind, kw = args
+    return make_scene(kind, **kw)
+
+
+def batch_mix_specs(n_maps: int = 64, frames: int = 4, seed: int = 4, kinds=("room", "lidar_terrain")):
+    """Seeded specifications of independent map workloads of uneven sizes: rooms of 5-40 m with
+    v in {0.05, 0.1} m and 160x120 .. 640x480 RGB-D frames, and LiDAR terrains of 40-80 m with
+    v = 0.2 m and 16x1024 .. 64x2048 beams."""
+    rng = np.random.default_rng(seed)
+    specs = []
+    for i in range(n_maps):
+        kind = kinds[int(rng.integers(0, len(kinds)))] if len(kinds) > 1 else kinds[0]
+        if kind == "room":
+            w, h = [(160, 120), (320, 240), (640, 480)][int(rng.integers(0, 3))]
+            v = [0.05, 0.1][int(rng.integers(0, 2))]
+            size = float(rng.uniform(5.0, 40.0))
+            kw = dict(
+                frames=frames,
+                width=w,
+                height=h,
+                fx=525.0 * w / 640.0,
+                fy=525.0 * w / 640.0,
+                n_objects=int(max(5, min(60, size * size / 5.0))),
+                seed=1000 + i,
+                size=size,
+                voxel_size=v,
+                block=16 if v < 0.075 else 8,
+            )
+        else:
+            beams, cols = [(16, 1024), (32, 1024), (64, 2048)][int(rng.integers(0, 3))]
+            ext = float(rng.uniform(40.0, 80.0))
+            kw = dict(
+                scans=frames,
+                beams=beams,
+                columns=cols,
+                path_length=ext,
+                n_buildings=int(ext * ext / 130.0),
+                n_trees=int(ext * ext / 80.0),
+                extent=ext,
+                seed=2000 + i,
+            )
+        specs.append((kind, kw))
+    return specs
+
+
+def batch_mix(n_maps: int = 64, frames: int = 4, seed: int = 4, kinds=("room", "lidar_terrain"), workers: int = 0):
+    """The scan sets of batch_mix_specs, generated in parallel worker processes when workers > 1."""
+    specs = batch_mix_specs(n_maps, frames, seed, kinds)
+    if workers and workers > 1:
+        import multiprocessing as mp
+
+        with mp.get_context("spawn").Pool(workers) as pool:
+            return pool.map(_mix_one, specs)
+    return [_mix_one(x) for x in specs]
 
 
 def make_scene(name: str, **kw) -> ScanSet:

@@ -1,0 +1,277 @@
+"""Continuous-batching server of robot mapping sessions on one GPU.
+
+Each session is a robot that streams posed scans at its own rate and, after every scan, asks
+for distances and gradients at a batch of points near its trajectory (the planner's query of
+the paper's Sec. VII). The server keeps every admitted session's TSDF/ESDF map resident on the
+device and advances all sessions that have a scan waiting with one batched step
+(``vbx_batch_step``): a request that arrives while the GPU works joins the next step, so the
+batch changes from step to step (continuous batching). Sessions are admitted in arrival order
+when a slot is free and their map fits the device-memory budget; a finished session's map is
+reset and reused by the next session of the same kind, or freed to make room for another kind.
+
+The per-map arithmetic does not depend on which other maps share a step, so a session's map
+and query results are the same alone and in the mix.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import time
+from typing import Callable, Dict, List, Optional
+
+import numpy as np
+
+from . import vbx
+
+
+@dataclasses.dataclass
+class SessionSpec:
+    sid: int
+    kind: str  # key of the scan pool
+    seq: int  # sequence index inside the pool kind
+    offset: int  # first frame of the sequence
+    n_scans: int
+    rate_hz: float
+    start: float  # arrival time of the session (s since the run started)
+
+
+def poisson_sessions(
+    n: int,
+    kinds: List[str],
+    seqs_per_kind: Dict[str, int],
+    frames_per_seq: Dict[str, int],
+    sessions_per_s: float,
+    scans_per_session: int,
+    rate_range=(10.0, 30.0),
+    seed: int = 5,
+) -> List[SessionSpec]:
+    """Sessions arriving as a Poisson process, each streaming scans at U(rate_range) Hz."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for i in range(n):
+        t += float(rng.exponential(1.0 / sessions_per_s))
+        kind = kinds[int(rng.integers(0, len(kinds)))]
+        out.append(
+            SessionSpec(
+                sid=i,
+                kind=kind,
+                seq=int(rng.integers(0, seqs_per_kind[kind])),
+                offset=int(rng.integers(0, frames_per_seq[kind])),
+                n_scans=scans_per_session,
+                rate_hz=float(rng.uniform(*rate_range)),
+                start=t,
+            )
+        )
+    return out
+
+
+class ScanPool:
+    """Pre-generated scan sequences per kind, resident in device memory, with a query batch of
+    points within `radius` of the sensor for every frame."""
+
+    def __init__(self, sets_by_kind: Dict[str, list], n_queries: int, radius: float = 2.0, seed: int = 9):
+        import torch
+
+        from . import scenes
+
+        self.kinds = list(sets_by_kind)
+        self.params = {k: dict(v[0].params) for k, v in sets_by_kind.items()}
+        self.points, self.poses, self.queries = {}, {}, {}
+        self.n_queries = n_queries
+        for k, sets in sets_by_kind.items():
+            self.points[k] = [[torch.from_numpy(p).cuda() for p in s.points] for s in sets]
+            self.poses[k] = [[np.asarray(T, np.float32) for T in s.poses] for s in sets]
+            self.queries[k] = [
+                [
+                    torch.from_numpy(scenes.random_queries(s, n_queries, radius=radius, seed=seed + 31 * j + f, scan_index=f)).cuda()
+                    for f in range(len(s.points))
+                ]
+                for j, s in enumerate(sets)
+            ]
+
+    def frames(self, kind: str) -> int:
+        return len(self.poses[kind][0])
+
+    def frame(self, spec: SessionSpec, k: int):
+        f = (spec.offset + k) % len(self.poses[spec.kind][spec.seq])
+        return self.points[spec.kind][spec.seq][f], self.poses[spec.kind][spec.seq][f], self.queries[spec.kind][spec.seq][f]
+
+
+@dataclasses.dataclass
+class _Active:
+    spec: SessionSpec
+    m: vbx.Map
+    arrivals: np.ndarray
+    next: int = 0
+
+
+class MapServer:
+    def __init__(
+        self,
+        pool: ScanPool,
+        slots: int = 128,
+        hbm_budget: float = 120e9,
+        capacity: Optional[Dict[str, int]] = None,
+        use_graph: bool = True,
+    ):
+        import torch
+
+        self.pool = pool
+        self.slots = slots
+        self.budget = float(hbm_budget)
+        self.capacity = capacity or {}
+        self.use_graph = use_graph
+        self.used = 0
+        self.peak = 0
+        self.free: Dict[str, List[vbx.Map]] = collections.defaultdict(list)
+        # idle placeholder maps keep unbound slots valid (a slot always holds a map)
+        self.idle = [vbx.Map(0.5, 4, 0.5, 1.0, block_capacity=8, max_points=1024) for _ in range(slots)]
+        self.batch = vbx.MapBatch(self.idle, max_queries=pool.n_queries)
+        q = pool.n_queries
+        self.out = [
+            (
+                torch.empty(q, dtype=torch.float32, device="cuda"),
+                torch.empty((q, 3), dtype=torch.float32, device="cuda"),
+                torch.empty(q, dtype=torch.uint8, device="cuda"),
+            )
+            for _ in range(slots)
+        ]
+
+    # ----------------------------------------------------------------------- memory
+    def _new_map(self, kind: str) -> vbx.Map:
+        p = self.pool.params[kind]
+        pts = max(int(t.shape[0]) for seq in self.pool.points[kind] for t in seq)
+        return vbx.Map.from_scene_params(p, block_capacity=self.capacity.get(kind, 0), max_points=pts)
+
+    def _map_bytes(self, kind: str) -> int:
+        p = self.pool.params[kind]
+        pts = max(int(t.shape[0]) for seq in self.pool.points[kind] for t in seq)
+        return vbx.map_bytes(int(p["voxels_per_block"]), self.capacity.get(kind, 0), pts)
+
+    def _acquire(self, kind: str) -> Optional[vbx.Map]:
+        if self.free[kind]:
+            m = self.free[kind].pop()
+            m.reset()
+            return m
+        need = self._map_bytes(kind)
+        for other in list(self.free):
+            while other != kind and self.free[other] and self.used + need > self.budget:
+                m = self.free[other].pop()
+                self.used -= m.device_bytes()
+                m.close()
+        if self.used + need > self.budget:
+            return None
+        m = self._new_map(kind)
+        self.used += m.device_bytes()
+        self.peak = max(self.peak, self.used)
+        return m
+
+    def close(self) -> None:
+        self.batch.close()
+        for ms in self.free.values():
+            for m in ms:
+                m.close()
+        self.free.clear()
+
+    # -------------------------------------------------------------------------- run
+    def run(
+        self,
+        sessions: List[SessionSpec],
+        seed: int = 7,
+        on_finish: Optional[Callable[[SessionSpec, vbx.Map, tuple], None]] = None,
+        time_limit: float = 600.0,
+    ) -> Dict[str, object]:
+        import torch
+
+        rng = np.random.default_rng(seed)
+        waiting = collections.deque(sorted(sessions, key=lambda s: s.start))
+        active: Dict[int, _Active] = {}
+        free_slots = list(range(self.slots))[::-1]
+        flags_map = vbx.STEP_INTEGRATE | vbx.STEP_ESDF | (vbx.STEP_GRAPH if self.use_graph else 0)
+        flags_q = vbx.STEP_QUERY | (vbx.STEP_GRAPH if self.use_graph else 0)
+        lat_scan, lat_query, batch_sizes = [], [], []
+        admitted = 0
+        max_active = 0
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e2 = torch.cuda.Event(enable_timing=True)
+        gpu_ms = 0.0
+        t0 = time.perf_counter()
+        while waiting or active:
+            now = time.perf_counter() - t0
+            if now > time_limit:
+                raise RuntimeError("serving run exceeded its time limit")
+            # admission: arrival order, a free slot and room in the memory budget
+            while waiting and waiting[0].start <= now and free_slots:
+                spec = waiting[0]
+                m = self._acquire(spec.kind)
+                if m is None:
+                    break
+                waiting.popleft()
+                slot = free_slots.pop()
+                self.batch.bind(slot, m)
+                gaps = rng.exponential(1.0 / spec.rate_hz, size=spec.n_scans)
+                arrivals = max(spec.start, now) + np.cumsum(gaps) - gaps[0]
+                active[slot] = _Active(spec, m, arrivals)
+                admitted += 1
+            max_active = max(max_active, len(active))
+            ready = [s for s, a in active.items() if a.arrivals[a.next] <= now]
+            if not ready:
+                nxt = [a.arrivals[a.next] for a in active.values()]
+                if waiting and free_slots:
+                    nxt.append(waiting[0].start)
+                wait = (min(nxt) - now) if nxt else 0.001
+                time.sleep(min(max(wait, 0.0), 0.002))
+                continue
+            points = [None] * self.slots
+            poses = [None] * self.slots
+            queries = [None] * self.slots
+            for s in ready:
+                a = active[s]
+                p, T, q = self.pool.frame(a.spec, a.next)
+                points[s], poses[s] = p, T
+                queries[s] = (q,) + self.out[s]
+            e0.record()
+            self.batch.step(points, poses, flags=flags_map)
+            e1.record()
+            self.batch.step(queries=queries, flags=flags_q)
+            e2.record()
+            e2.synchronize()
+            t_done = time.perf_counter() - t0
+            q_ms = e1.elapsed_time(e2)
+            gpu_ms += e0.elapsed_time(e2)
+            batch_sizes.append(len(ready))
+            for s in ready:
+                a = active[s]
+                arrival = float(a.arrivals[a.next])
+                lat_query.append(t_done - arrival)
+                lat_scan.append(t_done - q_ms * 1e-3 - arrival)
+                a.next += 1
+                if a.next == a.spec.n_scans:
+                    if on_finish is not None:
+                        on_finish(a.spec, a.m, tuple(t.clone() for t in self.out[s]))
+                    self.batch.bind(s, self.idle[s])
+                    self.free[a.spec.kind].append(a.m)
+                    del active[s]
+                    free_slots.append(s)
+        self.batch.sync()
+        wall = time.perf_counter() - t0
+        n = len(lat_scan)
+        ls = np.asarray(lat_scan) * 1e3
+        lq = np.asarray(lat_query) * 1e3
+        return dict(
+            sessions=admitted,
+            scans=n,
+            wall_s=wall,
+            scans_per_s=n / wall,
+            gpu_busy_frac=gpu_ms / 1e3 / wall,
+            scans_per_gpu_s=n / (gpu_ms / 1e3),
+            steps=len(batch_sizes),
+            mean_batch=float(np.mean(batch_sizes)) if batch_sizes else 0.0,
+            max_concurrent_sessions=max_active,
+            scan_latency_ms=dict(p50=float(np.percentile(ls, 50)), p99=float(np.percentile(ls, 99))),
+            query_latency_ms=dict(p50=float(np.percentile(lq, 50)), p99=float(np.percentile(lq, 99))),
+            peak_map_bytes=self.peak,
+            budget_bytes=self.budget,
+        )

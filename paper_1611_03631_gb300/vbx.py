@@ -119,7 +119,10 @@ _SIGS = {
     ),
     "vbx_reset_kernel_times": (ctypes.c_int, [_vp]),
     "vbx_total_launches": (_i64, []),
-    "vbx_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, _i64, _i64, ctypes.POINTER(_vp)]),
+    "vbx_map_bytes": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(vbx_map_options), ctypes.POINTER(_i64)]),
+    "vbx_map_device_bytes": (ctypes.c_int, [_vp, ctypes.POINTER(_i64)]),
+    "vbx_reset_map": (ctypes.c_int, [_vp, _vp]),
+    "vbx_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, _i64, ctypes.POINTER(_vp)]),
     "vbx_batch_bind": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
     "vbx_batch_step": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
     "vbx_batch_autotune": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_char_p, ctypes.c_int]),
@@ -340,16 +343,36 @@ class Map:
     def reset_kernel_times(self) -> None:
         _check(self._lib.vbx_reset_kernel_times(self._h))
 
+    def device_bytes(self) -> int:
+        n = ctypes.c_int64()
+        _check(self._lib.vbx_map_device_bytes(self._h, ctypes.byref(n)))
+        return int(n.value)
+
+    def reset(self, stream=None) -> None:
+        _check(self._lib.vbx_reset_map(self._h, _stream_ptr(stream)))
+
+
+def map_bytes(voxels_per_block: int, block_capacity: int = 0, max_points: int = 0) -> int:
+    """Device bytes of a map with these sizes (vbx_map_bytes)."""
+    lib = load_library()
+    o = vbx_map_options()
+    _check(lib.vbx_default_options(ctypes.byref(o)))
+    o.block_capacity = int(block_capacity)
+    o.max_points = int(max_points)
+    n = ctypes.c_int64()
+    _check(lib.vbx_map_bytes(int(voxels_per_block), ctypes.byref(o), ctypes.byref(n)))
+    return int(n.value)
+
 
 class MapBatch:
     """A fixed-slot batch of maps advanced by the same launches (vbx_batch_* in vbx.h)."""
 
-    def __init__(self, maps, max_points: int, max_queries: int = 0):
+    def __init__(self, maps, max_queries: int = 0):
         self._lib = load_library()
         self.maps = list(maps)
         arr = (ctypes.c_void_p * len(self.maps))(*[m.handle for m in self.maps])
         h = ctypes.c_void_p()
-        _check(self._lib.vbx_batch_create(arr, len(self.maps), int(max_points), int(max_queries), ctypes.byref(h)))
+        _check(self._lib.vbx_batch_create(arr, len(self.maps), int(max_queries), ctypes.byref(h)))
         self._h = h
         self.count = len(self.maps)
         self._scans = (vbx_scan_in * self.count)()

@@ -54,7 +54,7 @@ def test_batch_matches_maps_updated_alone(vbx, graph):
     ss = _scenes()
     alone = _maps(vbx, ss)
     mixed = _maps(vbx, ss)
-    batch = vbx.MapBatch(mixed, max_points=max(s.points[0].shape[0] for s in ss), max_queries=2048)
+    batch = vbx.MapBatch(mixed, max_queries=2048)
     flags = vbx.STEP_INTEGRATE | vbx.STEP_ESDF | (vbx.STEP_GRAPH if graph else 0)
     for f in range(3):
         pts = [torch.from_numpy(s.points[f]).cuda() for s in ss]
@@ -82,7 +82,7 @@ def test_batch_slots_without_scans_and_autotune(vbx):
     ss = _scenes()[:3]
     maps = _maps(vbx, ss)
     ref = _maps(vbx, ss)
-    batch = vbx.MapBatch(maps, max_points=max(s.points[0].shape[0] for s in ss))
+    batch = vbx.MapBatch(maps)
     pts = [torch.from_numpy(s.points[0]).cuda() for s in ss]
     report = batch.autotune(pts, [s.poses[0] for s in ss])
     assert "esdf_ctas_per_sm" in report
