@@ -176,6 +176,13 @@ def run_batched(args, vbx, torch, dev):
         step_ms.append(e0.elapsed_time(e1))
     launches = vbx.total_launches() - l0
     batch.sync()
+    # per-kernel device time of the batched step: a few direct (non-graph) steps with events
+    batch.set_profiling(True)
+    prof_steps = 3
+    for f in order[:prof_steps]:
+        batch.step([p[f] for p in pts], [s.poses[f] for s in sets], flags=flags)
+    kt = batch.kernel_times()
+    batch.set_profiling(False)
     blocks = [m.num_blocks() for m in maps]
     batch.close()
     for m in maps:
@@ -198,6 +205,7 @@ def run_batched(args, vbx, torch, dev):
         "graph": True,
         "autotune": report,
         "max_blocks_per_map": int(max(blocks)),
+        "kernels_ms_per_step": {k: v["ms"] / prof_steps for k, v in kt.items() if v["launches"]},
     }
 
 

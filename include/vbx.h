@@ -223,6 +223,12 @@ vbx_status vbx_batch_step(vbx_batch_t batch, const vbx_scan_in* scans, const vbx
 vbx_status vbx_batch_autotune(vbx_batch_t batch, const vbx_scan_in* scans, const vbx_query_io* queries, int flags,
                               void* stream, char* report, int report_len);
 
+/* Per-kernel CUDA-event timing of this batch's direct (non-graph) steps, as vbx_set_profiling and
+ * vbx_get_kernel_times do for a map. */
+vbx_status vbx_batch_set_profiling(vbx_batch_t batch, int enable);
+vbx_status vbx_batch_kernel_times(vbx_batch_t batch, const char** names, double* ms, int64_t* launches, int cap,
+                                  int* n_out, void* stream);
+
 /* Waits for `stream`; returns the first sticky device error of the bound maps (and clears it). */
 vbx_status vbx_batch_sync(vbx_batch_t batch, void* stream);
 

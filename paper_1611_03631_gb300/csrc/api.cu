@@ -954,6 +954,27 @@ vbx_status vbx_batch_autotune(vbx_batch_t b, const vbx_scan_in* scans, const vbx
   return st;
 }
 
+vbx_status vbx_batch_set_profiling(vbx_batch_t b, int enable) {
+  if (!b) return fail(VBX_ERR_INVALID_ARG, "batch is NULL");
+  b->hook.profile = enable != 0;
+  return VBX_OK;
+}
+
+vbx_status vbx_batch_kernel_times(vbx_batch_t b, const char** names, double* ms, int64_t* launches, int cap, int* n_out,
+                                  void* stream) {
+  if (!b || !n_out) return fail(VBX_ERR_INVALID_ARG, "batch or n_out is NULL");
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "sync");
+  b->hook.collect();
+  *n_out = vbx::kNumKernels;
+  for (int i = 0; i < vbx::kNumKernels && i < cap; ++i) {
+    if (names) names[i] = vbx::kKernelNames[i];
+    if (ms) ms[i] = b->hook.ms[i];
+    if (launches) launches[i] = b->hook.count[i];
+  }
+  return VBX_OK;
+}
+
 vbx_status vbx_batch_sync(vbx_batch_t b, void* stream) {
   if (!b) return fail(VBX_ERR_INVALID_ARG, "batch is NULL");
   vbx_status first = VBX_OK;

@@ -127,6 +127,11 @@ _SIGS = {
     "vbx_batch_step": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
     "vbx_batch_autotune": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_char_p, ctypes.c_int]),
     "vbx_batch_sync": (ctypes.c_int, [_vp, _vp]),
+    "vbx_batch_set_profiling": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "vbx_batch_kernel_times": (
+        ctypes.c_int,
+        [_vp, ctypes.POINTER(ctypes.c_char_p), _vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _vp],
+    ),
     "vbx_batch_destroy": (ctypes.c_int, [_vp]),
     "vbx_last_error": (ctypes.c_char_p, []),
 }
@@ -432,3 +437,15 @@ class MapBatch:
 
     def sync(self, stream=None) -> None:
         _check(self._lib.vbx_batch_sync(self._h, _stream_ptr(stream)))
+
+    def set_profiling(self, enable: bool) -> None:
+        _check(self._lib.vbx_batch_set_profiling(self._h, 1 if enable else 0))
+
+    def kernel_times(self, stream=None):
+        cap = 32
+        names = (ctypes.c_char_p * cap)()
+        ms = np.zeros(cap, np.float64)
+        cnt = np.zeros(cap, np.int64)
+        n = ctypes.c_int()
+        _check(self._lib.vbx_batch_kernel_times(self._h, names, ms.ctypes.data, cnt.ctypes.data, cap, ctypes.byref(n), _stream_ptr(stream)))
+        return {names[i].decode(): dict(ms=float(ms[i]), launches=int(cnt[i])) for i in range(min(n.value, cap))}
