@@ -88,6 +88,7 @@ SERVE_SESSIONS = 256
 SERVE_SLOTS = 128
 SERVE_BUDGET = 120e9
 SERVE_CAPACITY = {"room": 2048, "lidar_terrain": 1 << 16}
+SERVE_ARRIVALS = 32.0  # sessions per second
 
 
 def _batch_sets():
@@ -176,6 +177,13 @@ def run_batched(args, vbx, torch, dev):
         step_ms.append(e0.elapsed_time(e1))
     launches = vbx.total_launches() - l0
     batch.sync()
+    last = [m.stats() for m in maps]
+    esdf_last = {
+        k: int(sum(st[k] for st in last))
+        for k in ("esdf_in", "raise_pops", "lower_pops", "esdf_block_visits", "esdf_local_iters", "updated", "records")
+    }
+    esdf_last["rounds"] = int(max(st["raise_rounds"] + st["lower_rounds"] for st in last))
+    esdf_last["phase_ms"] = {k: last[0]["esdf_" + k + "_ns"] / 1e6 for k in ("classify", "raise", "lower")}
     # per-kernel device time of the batched step: a few direct (non-graph) steps with events
     batch.set_profiling(True)
     prof_steps = 3
@@ -206,6 +214,7 @@ def run_batched(args, vbx, torch, dev):
         "autotune": report,
         "max_blocks_per_map": int(max(blocks)),
         "kernels_ms_per_step": {k: v["ms"] / prof_steps for k, v in kt.items() if v["launches"]},
+        "last_step_totals": esdf_last,
     }
 
 
@@ -220,13 +229,13 @@ def run_served(args, vbx, torch):
         list(sets),
         {k: len(v) for k, v in sets.items()},
         {k: pool.frames(k) for k in sets},
-        sessions_per_s=64.0,
+        sessions_per_s=SERVE_ARRIVALS,
         scans_per_session=16,
     )
     res = srv.run(specs)
     srv.close()
     res["workload"] = (
-        f"{SERVE_SESSIONS} robot sessions arriving as a Poisson process (64/s), half room RGB-D 640x480 (v=0.05 m), "
+        f"{SERVE_SESSIONS} robot sessions arriving as a Poisson process ({SERVE_ARRIVALS:.0f}/s), half room RGB-D 640x480 (v=0.05 m), "
         "half LiDAR 64x2048 terrain (v=0.2 m), 16 scans each at U(10,30) Hz, each scan followed by 10k "
         f"distance+gradient queries within 2 m of the sensor; {SERVE_SLOTS} batch slots, {SERVE_BUDGET/1e9:.0f} GB map budget"
     )

@@ -18,8 +18,8 @@
 
 namespace vbx {
 const char* const kKernelNames[kNumKernels] = {"reset_counters", "bin_points",  "group_rays", "link_blocks",
-                                               "integrate_rays", "apply",       "esdf",       "query",
-                                               "import_alloc",   "import_set",  "init_groups"};
+                                               "integrate_rays", "touched",     "apply",      "esdf",
+                                               "query",          "import_alloc", "import_set", "init_groups"};
 }  // namespace vbx
 
 namespace {
@@ -300,6 +300,7 @@ vbx_status vbx_create_map(float voxel_size, int voxels_per_block, float truncati
   VBX_ALLOC(d.acc, 4 * V, 0);
   VBX_ALLOC(d.touch, V, 0);
   VBX_ALLOC(d.btouch, (size_t)cap, 0);
+  VBX_ALLOC(d.tlist, (size_t)cap, 0);
   VBX_ALLOC(d.esdf, V, 0);
   VBX_ALLOC(d.vflags, V, 0);
   VBX_ALLOC(d.rbits0, V / 32, 0);
@@ -1005,7 +1006,7 @@ vbx_status vbx_map_bytes(int B, const vbx_map_options* opt_in, int64_t* out) {
   const uint64_t entries = next_pow2(pts * 2);
   uint64_t bytes = 0;
   bytes += H * (8 + 4);                                   // block hash
-  bytes += cap * (12 + 27 * 4 + 4 + 4);                   // block coords, links, touch flag, new list
+  bytes += cap * (12 + 27 * 4 + 4 + 4 + 4);               // block coords, links, touch flag, lists
   bytes += V * (8 + 32 + 4 + 8 + 1 + 4 + 4);              // tsdf, sums, touch, esdf, flags, lists
   bytes += 4 * (V / 32) * 4;                              // frontier bitmasks
   bytes += tiles * (2 * 4 + 4 * 8);                       // tile stamps, active lists

@@ -8,8 +8,9 @@
 //                           per-voxel sums of w and w*d in 2^-28 fixed point with integer
 //                           atomics, pre-aggregated across the warp (order-independent, so
 //                           the result does not depend on scheduling)
-//   k_apply          A5     Eq. (3) merge of each voxel that received records (found through the
-//                           per-block and per-voxel touch flags); queues it for the ESDF
+//   k_touched        A5     compacts the blocks the rays entered into a per-map list
+//   k_apply          A5     Eq. (3) merge of each voxel that received records (one thread per
+//                           voxel of a touched block); queues it for the ESDF
 // All float32 arithmetic that decides a set (keys, endpoints, visited voxels, w > 0) uses
 // explicitly rounded intrinsics, so the compiler cannot contract or reorder it.
 #include <cuda_runtime.h>
@@ -130,6 +131,7 @@ __global__ void __launch_bounds__(kThreads) k_reset_counters(Batch b) {
     c->nnew = 0;
     c->nupdated = 0;
     c->npoints_valid = 0;
+    c->ntouched = 0;
     c->nrecords = 0;
     c->raise_rounds = 0;
     c->lower_rounds = 0;
@@ -488,47 +490,59 @@ __device__ __forceinline__ void append(uint32_t* list, unsigned* count, uint32_t
   list[base + g.thread_rank()] = vid;
 }
 
-// One CTA per touched block: every voxel that received records this scan gets the Eq. (3)
-// merge, its sums and flag are cleared, and it joins the scan's updated list and (once) the
-// queue of the next ESDF update.
-__global__ void __launch_bounds__(kThreads) k_apply(Batch b) {
+// Compacts the blocks whose touch flag the rays set into the map's touched-block list.
+__global__ void __launch_bounds__(kThreads) k_touched(Batch b) {
   __shared__ unsigned pfx[kMaxBatch + 1];
   const int nm = nmaps_of(b);
   const unsigned total = cta_prefix(pfx, b, [&](unsigned mi) {
     const DevMap& m = map_of(b, mi);
     return min(__ldcg(&m.ctr->blocks), m.cap_blocks);
   });
-  for (unsigned item = blockIdx.x; item < total; item += gridDim.x) {
-    const unsigned mi = map_index(pfx, nm, item);
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const unsigned mi = map_index(pfx, nm, i);
     const DevMap& m = map_of(b, mi);
-    const unsigned blk = item - pfx[mi];
-    if (__ldcg(&m.btouch[blk]) == 0u) continue;  // uniform across the CTA
-    const unsigned B3 = 1u << m.b3log;
-    for (unsigned l = threadIdx.x; l < B3; l += blockDim.x) {
-      const uint32_t vid = (blk << m.b3log) | l;
-      if (m.touch[vid] == 0u) continue;
-      m.touch[vid] = 0u;
-      ulonglong2* a = reinterpret_cast<ulonglong2*>(&m.acc[4 * (size_t)vid]);
-      const ulonglong2 hi = a[0], lo = a[1];
-      a[0] = make_ulonglong2(0ull, 0ull);
-      a[1] = make_ulonglong2(0ull, 0ull);
-      const float Sw = __fadd_rn(__fmul_rn(__ll2float_rn((long long)hi.x), kAccInvScale),
-                                 __fmul_rn(__ll2float_rn((long long)lo.x), kAccLoInvScale));
-      const float Swd = __fadd_rn(__fmul_rn(__ll2float_rn((long long)hi.y), kAccInvScale),
-                                  __fmul_rn(__ll2float_rn((long long)lo.y), kAccLoInvScale));
-      const float2 t = m.tsdf[vid];
-      // Eq. (3): D <- (W D + sum w d) / (W + sum w), W <- min(W + sum w, W_max)
-      const float Wn = __fadd_rn(t.y, Sw);
-      const float D = __fdiv_rn(__fadd_rn(__fmul_rn(t.y, t.x), Swd), Wn);
-      m.tsdf[vid] = make_float2(D, fminf(Wn, m.wmax));
-      append(m.updated, &m.ctr->nupdated, vid);
-      if (!(m.vflags[vid] & kQueuedForEsdf)) {
-        m.vflags[vid] |= kQueuedForEsdf;
-        append(m.dirty, &m.ctr->ndirty, vid);
-      }
+    const unsigned blk = i - pfx[mi];
+    if (m.btouch[blk] == 0u) continue;
+    m.btouch[blk] = 0u;
+    append(m.tlist, &m.ctr->ntouched, blk);
+  }
+}
+
+// One thread per voxel of a touched block: every voxel that received records this scan gets
+// the Eq. (3) merge, its sums and flag are cleared, and it joins the scan's updated list and
+// (once) the queue of the next ESDF update.
+__global__ void __launch_bounds__(kThreads) k_apply(Batch b) {
+  __shared__ unsigned pfx[kMaxBatch + 1];
+  const int nm = nmaps_of(b);
+  const unsigned total = cta_prefix(pfx, b, [&](unsigned mi) {
+    const DevMap& m = map_of(b, mi);
+    return __ldcg(&m.ctr->ntouched) << m.b3log;
+  });
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const unsigned mi = map_index(pfx, nm, i);
+    const DevMap& m = map_of(b, mi);
+    const unsigned u = i - pfx[mi];
+    const uint32_t vid = (m.tlist[u >> m.b3log] << m.b3log) | (u & ((1u << m.b3log) - 1u));
+    if (m.touch[vid] == 0u) continue;
+    m.touch[vid] = 0u;
+    ulonglong2* a = reinterpret_cast<ulonglong2*>(&m.acc[4 * (size_t)vid]);
+    const ulonglong2 hi = a[0], lo = a[1];
+    a[0] = make_ulonglong2(0ull, 0ull);
+    a[1] = make_ulonglong2(0ull, 0ull);
+    const float Sw = __fadd_rn(__fmul_rn(__ll2float_rn((long long)hi.x), kAccInvScale),
+                               __fmul_rn(__ll2float_rn((long long)lo.x), kAccLoInvScale));
+    const float Swd = __fadd_rn(__fmul_rn(__ll2float_rn((long long)hi.y), kAccInvScale),
+                                __fmul_rn(__ll2float_rn((long long)lo.y), kAccLoInvScale));
+    const float2 t = m.tsdf[vid];
+    // Eq. (3): D <- (W D + sum w d) / (W + sum w), W <- min(W + sum w, W_max)
+    const float Wn = __fadd_rn(t.y, Sw);
+    const float D = __fdiv_rn(__fadd_rn(__fmul_rn(t.y, t.x), Swd), Wn);
+    m.tsdf[vid] = make_float2(D, fminf(Wn, m.wmax));
+    append(m.updated, &m.ctr->nupdated, vid);
+    if (!(m.vflags[vid] & kQueuedForEsdf)) {
+      m.vflags[vid] |= kQueuedForEsdf;
+      append(m.dirty, &m.ctr->ndirty, vid);
     }
-    __syncthreads();
-    if (threadIdx.x == 0) m.btouch[blk] = 0u;
   }
 }
 
@@ -613,6 +627,9 @@ cudaError_t launch_integrate(const Batch& b, const LaunchCfg& cfg, LaunchHook* h
   hook->begin(kKIntegrateRays, s);
   k_integrate_rays<<<grays, kThreads, 0, s>>>(b);
   hook->end(kKIntegrateRays, s);
+  hook->begin(kKTouched, s);
+  k_touched<<<cfg.num_sms * 4, kThreads, 0, s>>>(b);
+  hook->end(kKTouched, s);
   hook->begin(kKApply, s);
   k_apply<<<cfg.num_sms * cfg.tune.apply_ctas_per_sm, kThreads, 0, s>>>(b);
   hook->end(kKApply, s);

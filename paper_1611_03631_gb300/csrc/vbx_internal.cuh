@@ -69,6 +69,8 @@ struct Counters {
   unsigned int nnew;
   unsigned int nupdated;
   unsigned int npoints_valid;
+  unsigned int ntouched;  // blocks entered by the scan's rays (compacted list length)
+  unsigned int pad0;
   unsigned long long nrecords;
   // ---- persistent
   unsigned int blocks;
@@ -124,6 +126,7 @@ struct DevMap {
   unsigned long long* acc;
   uint32_t* touch;
   uint32_t* btouch;
+  uint32_t* tlist;  // compacted list of the blocks touched by the current scan
   unsigned long long* esdf;
   uint8_t* vflags;
   uint32_t* rbits0;
