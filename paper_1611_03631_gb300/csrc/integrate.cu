@@ -481,13 +481,17 @@ __global__ void __launch_bounds__(kThreads) k_integrate_rays(Batch b) {
 }
 
 // ------------------------------------------------------------------------------------ A5
-// Appends vid to a list with one atomic per coalesced group of lanes.
+// Appends vid to a list with one atomic per group of active lanes that append to the same list
+// (lanes of one warp may belong to different maps of a batch).
 __device__ __forceinline__ void append(uint32_t* list, unsigned* count, uint32_t vid) {
-  cg::coalesced_group g = cg::coalesced_threads();
+  const unsigned active = __activemask();
+  const unsigned peers = __match_any_sync(active, (unsigned long long)(uintptr_t)count);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(peers) - 1;
   unsigned base = 0;
-  if (g.thread_rank() == 0) base = atomicAdd(count, g.size());
-  base = g.shfl(base, 0);
-  list[base + g.thread_rank()] = vid;
+  if (lane == leader) base = atomicAdd(count, (unsigned)__popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  list[base + __popc(peers & ((1u << lane) - 1u))] = vid;
 }
 
 // Compacts the blocks whose touch flag the rays set into the map's touched-block list.
