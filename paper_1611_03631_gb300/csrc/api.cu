@@ -933,7 +933,7 @@ vbx_status vbx_batch_autotune(vbx_batch_t b, const vbx_scan_in* scans, const vbx
   }
   if (st == VBX_OK && (f & VBX_STEP_ESDF)) {
     best_ms = 1e30f;
-    const int esdf_opts[3] = {2, 3, 4};
+    const int esdf_opts[3] = {4, 6, 8};
     for (int c : esdf_opts) {
       b->tune = best;
       b->tune.esdf_ctas_per_sm = c;

@@ -30,7 +30,7 @@ namespace vbx {
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 128;
 constexpr unsigned kMaxRounds = 1u << 16;
 constexpr int kMaxLocalIters = 1 << 15;
 
@@ -468,21 +468,32 @@ __global__ void __launch_bounds__(kThreads) k_esdf(const DevMap* __restrict__ ma
   const unsigned long long t_start = global_ns();
 
   // ---------------------------------------------------------------- A6: classification
-  // exclusive prefix of the maps' dirty counts (Hillis-Steele scan in shared memory)
-  {
-    static_assert(kMaxBatch <= kThreads, "one prefix entry per thread");
-    const bool mine = threadIdx.x < kMaxBatch;
-    const unsigned v = (int)threadIdx.x < nmaps ? __ldcg(&maps[threadIdx.x].ctr->ndirty) : 0u;
-    if (mine) pfx[threadIdx.x + 1] = v;
+  // exclusive prefix of the maps' dirty counts: warp 0 scans kMaxBatch / 32 counts per lane
+  if (threadIdx.x < 32) {
+    constexpr int per = kMaxBatch / 32;
+    unsigned v[per];
+    unsigned sum = 0;
+#pragma unroll
+    for (int j = 0; j < per; ++j) {
+      const int mi = (int)threadIdx.x * per + j;
+      v[j] = mi < nmaps ? __ldcg(&maps[mi].ctr->ndirty) : 0u;
+      sum += v[j];
+    }
+    unsigned incl = sum;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const unsigned up = __shfl_up_sync(0xffffffffu, incl, off);
+      if ((int)threadIdx.x >= off) incl += up;
+    }
+    unsigned run = incl - sum;
     if (threadIdx.x == 0) pfx[0] = 0u;
-    __syncthreads();
-    for (int off = 1; off < kMaxBatch; off <<= 1) {
-      const unsigned add = (mine && (int)threadIdx.x >= off) ? pfx[threadIdx.x + 1 - off] : 0u;
-      __syncthreads();
-      if (mine) pfx[threadIdx.x + 1] += add;
-      __syncthreads();
+#pragma unroll
+    for (int j = 0; j < per; ++j) {
+      run += v[j];
+      pfx[threadIdx.x * per + j + 1] = run;
     }
   }
+  __syncthreads();
   const unsigned total = pfx[nmaps];
   for (unsigned i = tid; i < total; i += nthreads) {
     const unsigned mi = upper_index(pfx, nmaps, i);

@@ -50,7 +50,7 @@ struct Tuning {
   int apply_ctas_per_sm;
   int esdf_ctas_per_sm;  // resident CTAs per SM of the cooperative ESDF grid
 };
-constexpr Tuning kDefaultTuning = {16, 16, 16, 4};
+constexpr Tuning kDefaultTuning = {16, 16, 16, 8};
 
 struct LaunchCfg {
   int num_sms;
