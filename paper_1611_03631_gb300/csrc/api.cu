@@ -134,7 +134,7 @@ struct vbx_map_s {
   std::vector<void*> allocs;
   MapHook hook;
 
-  vbx::LaunchCfg cfg(void* stream) const { return vbx::LaunchCfg{num_sms, (cudaStream_t)stream, vbx::kDefaultTuning}; }
+  vbx::LaunchCfg cfg(void* stream) const { return vbx::LaunchCfg{num_sms, (cudaStream_t)stream, vbx::kMapTuning}; }
 
   std::vector<size_t> alloc_bytes;
 
@@ -906,7 +906,9 @@ vbx_status vbx_batch_autotune(vbx_batch_t b, const vbx_scan_in* scans, const vbx
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
+  int trials = 0;
   auto time_step = [&](float* ms) -> vbx_status {
+    ++trials;
     cudaEventRecord(e0, s);
     vbx_status st = batch_run(b, scans, queries, f, s);
     if (st != VBX_OK) return st;
@@ -933,10 +935,13 @@ vbx_status vbx_batch_autotune(vbx_batch_t b, const vbx_scan_in* scans, const vbx
   }
   if (st == VBX_OK && (f & VBX_STEP_ESDF)) {
     best_ms = 1e30f;
-    const int esdf_opts[3] = {4, 6, 8};
-    for (int c : esdf_opts) {
+    // (threads per CTA, CTAs per SM) of the cooperative ESDF grid; the grid is clamped to the
+    // kernel's occupancy
+    const int esdf_opts[5][2] = {{256, 4}, {256, 6}, {256, 8}, {512, 2}, {512, 4}};
+    for (const auto& o : esdf_opts) {
       b->tune = best;
-      b->tune.esdf_ctas_per_sm = c;
+      b->tune.esdf_threads = o[0];
+      b->tune.esdf_ctas_per_sm = o[1];
       float ms = 0.0f;
       if ((st = time_step(&ms)) != VBX_OK) break;
       if (ms < best_ms) {
@@ -950,8 +955,8 @@ vbx_status vbx_batch_autotune(vbx_batch_t b, const vbx_scan_in* scans, const vbx
   b->tune = best;
   b->drop_graphs();  // launch shapes changed
   if (report && report_len > 0)
-    snprintf(report, (size_t)report_len, "rays_ctas_per_sm=%d esdf_ctas_per_sm=%d bin_ctas_per_sm=%d apply_ctas_per_sm=%d best_step_ms=%.4f",
-             best.rays_ctas_per_sm, best.esdf_ctas_per_sm, best.bin_ctas_per_sm, best.apply_ctas_per_sm, best_ms);
+    snprintf(report, (size_t)report_len, "rays_ctas_per_sm=%d esdf_ctas_per_sm=%d esdf_threads=%d bin_ctas_per_sm=%d apply_ctas_per_sm=%d best_step_ms=%.4f trial_steps=%d",
+             best.rays_ctas_per_sm, best.esdf_ctas_per_sm, best.esdf_threads, best.bin_ctas_per_sm, best.apply_ctas_per_sm, best_ms, trials);
   return st;
 }
 

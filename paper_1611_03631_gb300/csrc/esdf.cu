@@ -30,7 +30,6 @@ namespace vbx {
 
 namespace {
 
-constexpr int kThreads = 128;
 constexpr unsigned kMaxRounds = 1u << 16;
 constexpr int kMaxLocalIters = 1 << 15;
 
@@ -222,23 +221,66 @@ __device__ __forceinline__ uint32_t neighbor_tile_item(const Tile& t, const Tile
   return (s << 3) | (uint32_t)((tz << 2) | (ty << 1) | tx);
 }
 
-// Stages tile `item` of map m: its words with the one-voxel halo, and the current frontier bits
-// of its interior (cleared in global memory, appended to the active list).
+// Voxel id and tile direction of tile coordinates (x, y, z) in [-1, S] (kInvalid if absent).
 template <int B, int S>
+__device__ __forceinline__ uint32_t coords_vid(const Tile& t, const TileRef& r, int x, int y, int z) {
+  using G = Geo<B, S>;
+  x += r.ox;
+  y += r.oy;
+  z += r.oz;
+  const int bx = x < 0 ? -1 : (x >= B ? 1 : 0);
+  const int by = y < 0 ? -1 : (y >= B ? 1 : 0);
+  const int bz = z < 0 ? -1 : (z >= B ? 1 : 0);
+  const uint32_t s = t.nslot[(bx + 1) * 9 + (by + 1) * 3 + (bz + 1)];
+  if (s == kInvalid) return kInvalid;
+  x -= bx * B;
+  y -= by * B;
+  z -= bz * B;
+  return (s << (3 * G::LOGB)) | (uint32_t)((((z << G::LOGB) | y) << G::LOGB) | x);
+}
+
+template <int S>
+__device__ __forceinline__ int coords_tile_dir(int x, int y, int z) {
+  const int dx = x < 0 ? -1 : (x >= S ? 1 : 0);
+  const int dy = y < 0 ? -1 : (y >= S ? 1 : 0);
+  const int dz = z < 0 ? -1 : (z >= S ? 1 : 0);
+  return (dx + 1) * 9 + (dy + 1) * 3 + (dz + 1);
+}
+
+// Stages tile `item` of map m: its words with the one-voxel halo (one tile row of T words per
+// thread, the S interior words of a row read as 16-byte vectors), and the current frontier bits
+// of its interior (cleared in global memory, appended to the active list).
+template <int NT, int B, int S>
 __device__ void stage_tile(const DevMap& m, const TileRef& r, uint32_t* cur_bits, const Tile& t) {
   using G = Geo<B, S>;
   if (threadIdx.x < 27) t.nslot[threadIdx.x] = threadIdx.x == 13 ? r.slot : __ldcg(&m.nbr[(size_t)r.slot * 27 + threadIdx.x]);
   if (threadIdx.x < 8) t.cnt[threadIdx.x] = 0u;
-  for (int i = threadIdx.x; i < (G::T3 + 31) / 32; i += kThreads) t.chg[i] = 0u;
-  for (int i = threadIdx.x; i < (2 * G::S3 + 31) / 32; i += kThreads) t.in[i] = 0u;
+  for (int i = threadIdx.x; i < (G::T3 + 31) / 32; i += NT) t.chg[i] = 0u;
+  for (int i = threadIdx.x; i < (2 * G::S3 + 31) / 32; i += NT) t.in[i] = 0u;
   __syncthreads();
-#pragma unroll 2
-  for (int c = threadIdx.x; c < G::T3; c += kThreads) {
-    const uint32_t vid = cell_vid<B, S>(t, r, c);
-    t.w[c] = vid == kInvalid ? 0ull : __ldcg(&m.esdf[vid]);
+  for (int row = threadIdx.x; row < G::T * G::T; row += NT) {
+    const int y = row % G::T - 1, z = row / G::T - 1;
+    unsigned long long* dst = &t.w[row * G::T];
+    const uint32_t vl = coords_vid<B, S>(t, r, -1, y, z);
+    const uint32_t v0 = coords_vid<B, S>(t, r, 0, y, z);
+    const uint32_t vr = coords_vid<B, S>(t, r, S, y, z);
+    dst[0] = vl == kInvalid ? 0ull : __ldcg(&m.esdf[vl]);
+    if (v0 == kInvalid) {
+#pragma unroll
+      for (int x = 0; x < S; ++x) dst[1 + x] = 0ull;
+    } else {
+      const ulonglong2* src = reinterpret_cast<const ulonglong2*>(&m.esdf[v0]);
+#pragma unroll
+      for (int j = 0; j < S / 2; ++j) {
+        const ulonglong2 v = __ldcg(&src[j]);
+        dst[1 + 2 * j] = v.x;
+        dst[2 + 2 * j] = v.y;
+      }
+    }
+    dst[S + 1] = vr == kInvalid ? 0ull : __ldcg(&m.esdf[vr]);
   }
   // frontier bits: tile row (z, y) = S consecutive bits of the block bitmap, inside one word
-  for (int row = threadIdx.x; row < S * S; row += kThreads) {
+  for (int row = threadIdx.x; row < S * S; row += NT) {
     const int z = row / S, y = row % S;
     const uint32_t base = (r.slot << (3 * G::LOGB)) + (uint32_t)((((r.oz + z) << G::LOGB) | (r.oy + y)) << G::LOGB) + r.ox;
     uint32_t* wp = &cur_bits[base >> 5];
@@ -266,13 +308,13 @@ struct RoundArgs {
 };
 
 // A7 for one staged tile (all threads of the CTA).
-template <int B, int S>
+template <int NT, int B, int S>
 __device__ void raise_tile(const DevMap& m, uint32_t item, uint32_t* cur_bits, const RoundArgs& ra, EsdfCtl* ctl,
                            unsigned char* smem, unsigned long long* pops) {
   using G = Geo<B, S>;
   const Tile t = carve(smem, S);
   const TileRef r = tile_ref<B, S>(item);
-  stage_tile<B, S>(m, r, cur_bits, t);
+  stage_tile<NT, B, S>(m, r, cur_bits, t);
   const float dmax = m.dmax;
   unsigned iters = 0;
   for (int it = 0;; ++it) {
@@ -291,10 +333,10 @@ __device__ void raise_tile(const DevMap& m, uint32_t item, uint32_t* cur_bits, c
       *pops += na;
       t.cnt[(it + 2) % 3] = 0u;
     }
-    for (int j = threadIdx.x; j < (G::S3 + 31) / 32; j += kThreads)
+    for (int j = threadIdx.x; j < (G::S3 + 31) / 32; j += NT)
       t.in[((it + 1) & 1) * (G::S3 / 32 > 0 ? G::S3 / 32 : 1) + j] = 0u;
     // reset the raised voxels first, so that no child test below sees a stale parent
-    for (unsigned i = threadIdx.x; i < na; i += kThreads) {
+    for (unsigned i = threadIdx.x; i < na; i += NT) {
       const int c = G::cell_of_local(cur[i]);
       const unsigned long long w = t.w[c];
       const unsigned fl = ew_flags(w);
@@ -304,7 +346,7 @@ __device__ void raise_tile(const DevMap& m, uint32_t item, uint32_t* cur_bits, c
       }
     }
     __syncthreads();
-    for (unsigned p = threadIdx.x; p < na * 26u; p += kThreads) {
+    for (unsigned p = threadIdx.x; p < na * 26u; p += NT) {
       const unsigned i = p / 26u;
       const int kk = (int)(p - i * 26u);
       const int k = kk < 13 ? kk : kk + 1;
@@ -331,7 +373,7 @@ __device__ void raise_tile(const DevMap& m, uint32_t item, uint32_t* cur_bits, c
   }
   if (threadIdx.x == 0) atomicAdd(&m.ctr->esdf_local_iters, iters);
   // write back the raised voxels (raise rounds never lower words, plain stores suffice)
-  for (int c = threadIdx.x; c < G::T3; c += kThreads) {
+  for (int c = threadIdx.x; c < G::T3; c += NT) {
     if (!(t.chg[c >> 5] & (1u << (c & 31)))) continue;
     m.esdf[cell_vid<B, S>(t, r, c)] = t.w[c];
   }
@@ -351,13 +393,13 @@ __device__ void raise_tile(const DevMap& m, uint32_t item, uint32_t* cur_bits, c
 }
 
 // A8 for one staged tile (all threads of the CTA).
-template <int B, int S>
+template <int NT, int B, int S>
 __device__ void lower_tile(const DevMap& m, uint32_t item, uint32_t* cur_bits, const RoundArgs& ra, EsdfCtl* ctl,
                            unsigned char* smem, unsigned long long* pops) {
   using G = Geo<B, S>;
   const Tile t = carve(smem, S);
   const TileRef r = tile_ref<B, S>(item);
-  stage_tile<B, S>(m, r, cur_bits, t);
+  stage_tile<NT, B, S>(m, r, cur_bits, t);
   const float L1 = m.L1, L2 = m.L2, L3 = m.L3;
   unsigned iters = 0;
   for (int it = 0;; ++it) {
@@ -376,9 +418,9 @@ __device__ void lower_tile(const DevMap& m, uint32_t item, uint32_t* cur_bits, c
       *pops += na;
       t.cnt[(it + 2) % 3] = 0u;
     }
-    for (int j = threadIdx.x; j < (G::S3 + 31) / 32; j += kThreads)
+    for (int j = threadIdx.x; j < (G::S3 + 31) / 32; j += NT)
       t.in[((it + 1) & 1) * (G::S3 / 32 > 0 ? G::S3 / 32 : 1) + j] = 0u;
-    for (unsigned p = threadIdx.x; p < na * 26u; p += kThreads) {
+    for (unsigned p = threadIdx.x; p < na * 26u; p += NT) {
       const unsigned i = p / 26u;
       const int kk = (int)(p - i * 26u);
       const int k = kk < 13 ? kk : kk + 1;
@@ -411,7 +453,7 @@ __device__ void lower_tile(const DevMap& m, uint32_t item, uint32_t* cur_bits, c
   // write back: the global word keeps the smaller value (fire-and-forget atomicMin); a halo
   // voxel this tile lowered is pushed to its own tile for the next round (a push of a voxel
   // that another tile lowered even further is redundant work, never wrong)
-  for (int c = threadIdx.x; c < G::T3; c += kThreads) {
+  for (int c = threadIdx.x; c < G::T3; c += NT) {
     if (!(t.chg[c >> 5] & (1u << (c & 31)))) continue;
     const uint32_t vid = cell_vid<B, S>(t, r, c);
     atomicMin(&m.esdf[vid], t.w[c]);
@@ -428,21 +470,23 @@ __device__ void lower_tile(const DevMap& m, uint32_t item, uint32_t* cur_bits, c
   __syncthreads();
 }
 
+template <int NT>
 __device__ __forceinline__ void raise_dispatch(const DevMap& m, uint32_t item, uint32_t* cur_bits, const RoundArgs& ra,
                                                EsdfCtl* ctl, unsigned char* smem, unsigned long long* pops) {
   switch (m.B) {
-    case 4: raise_tile<4, 4>(m, item, cur_bits, ra, ctl, smem, pops); break;
-    case 8: raise_tile<8, 8>(m, item, cur_bits, ra, ctl, smem, pops); break;
-    default: raise_tile<16, kTileEdge>(m, item, cur_bits, ra, ctl, smem, pops); break;
+    case 4: raise_tile<NT, 4, 4>(m, item, cur_bits, ra, ctl, smem, pops); break;
+    case 8: raise_tile<NT, 8, 8>(m, item, cur_bits, ra, ctl, smem, pops); break;
+    default: raise_tile<NT, 16, kTileEdge>(m, item, cur_bits, ra, ctl, smem, pops); break;
   }
 }
 
+template <int NT>
 __device__ __forceinline__ void lower_dispatch(const DevMap& m, uint32_t item, uint32_t* cur_bits, const RoundArgs& ra,
                                                EsdfCtl* ctl, unsigned char* smem, unsigned long long* pops) {
   switch (m.B) {
-    case 4: lower_tile<4, 4>(m, item, cur_bits, ra, ctl, smem, pops); break;
-    case 8: lower_tile<8, 8>(m, item, cur_bits, ra, ctl, smem, pops); break;
-    default: lower_tile<16, kTileEdge>(m, item, cur_bits, ra, ctl, smem, pops); break;
+    case 4: lower_tile<NT, 4, 4>(m, item, cur_bits, ra, ctl, smem, pops); break;
+    case 8: lower_tile<NT, 8, 8>(m, item, cur_bits, ra, ctl, smem, pops); break;
+    default: lower_tile<NT, 16, kTileEdge>(m, item, cur_bits, ra, ctl, smem, pops); break;
   }
 }
 
@@ -459,7 +503,8 @@ __device__ __forceinline__ unsigned upper_index(const unsigned* pfx, int n, unsi
   return (unsigned)lo;
 }
 
-__global__ void __launch_bounds__(kThreads) k_esdf(const DevMap* __restrict__ maps, int nmaps, EsdfCtl* ctl) {
+template <int NT>
+__global__ void __launch_bounds__(NT) k_esdf(const DevMap* __restrict__ maps, int nmaps, EsdfCtl* ctl) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ unsigned pfx[kMaxBatch + 1];
   __shared__ unsigned long long cta_pops;
@@ -571,7 +616,7 @@ __global__ void __launch_bounds__(kThreads) k_esdf(const DevMap* __restrict__ ma
       ra.nxt_list = (r & 1) ? ctl->ract0 : ctl->ract1;
       ra.nxt_cnt = &ctl->rcnt[(r + 1) % 3];
       if (threadIdx.x == 0) cta_pops = 0;
-      raise_dispatch(m, e.y, (r & 1) ? m.rbits1 : m.rbits0, ra, ctl, dsm, &cta_pops);
+      raise_dispatch<NT>(m, e.y, (r & 1) ? m.rbits1 : m.rbits0, ra, ctl, dsm, &cta_pops);
       if (threadIdx.x == 0) {
         if (cta_pops) atomicAdd(&m.ctr->raise_pops, cta_pops);
         atomicAdd(&m.ctr->esdf_block_visits, 1u);
@@ -604,7 +649,7 @@ __global__ void __launch_bounds__(kThreads) k_esdf(const DevMap* __restrict__ ma
       ra.nxt_list = (l & 1) ? ctl->lact0 : ctl->lact1;
       ra.nxt_cnt = &ctl->lcnt[(l + 1) % 3];
       if (threadIdx.x == 0) cta_pops = 0;
-      lower_dispatch(m, e.y, (l & 1) ? m.lbits1 : m.lbits0, ra, ctl, dsm, &cta_pops);
+      lower_dispatch<NT>(m, e.y, (l & 1) ? m.lbits1 : m.lbits0, ra, ctl, dsm, &cta_pops);
       if (threadIdx.x == 0) {
         if (cta_pops) atomicAdd(&m.ctr->lower_pops, cta_pops);
         atomicAdd(&m.ctr->esdf_block_visits, 1u);
@@ -631,11 +676,25 @@ __global__ void __launch_bounds__(kThreads) k_esdf(const DevMap* __restrict__ ma
 
 size_t esdf_smem_bytes(int max_B) { return tile_bytes(max_B < kTileEdge ? max_B : kTileEdge); }
 
-int esdf_grid(int num_sms, int max_B, int ctas_per_sm) {
+namespace {
+
+const void* esdf_kernel(int threads) {
+  switch (threads) {
+    case 256: return (const void*)k_esdf<256>;
+    case 512: return (const void*)k_esdf<512>;
+    default: return nullptr;
+  }
+}
+
+}  // namespace
+
+int esdf_grid(int num_sms, int max_B, int ctas_per_sm, int threads) {
+  const void* k = esdf_kernel(threads);
+  if (!k) return 0;
   const size_t smem = esdf_smem_bytes(max_B);
-  if (cudaFuncSetAttribute(k_esdf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_esdf, kThreads, smem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads, smem) != cudaSuccess) return 0;
   if (ctas_per_sm > 0 && nb > ctas_per_sm) nb = ctas_per_sm;
   return nb * num_sms;
 }
@@ -643,12 +702,15 @@ int esdf_grid(int num_sms, int max_B, int ctas_per_sm) {
 cudaError_t launch_esdf(const DevMap* maps_dev, int nmaps, int max_B, EsdfCtl* ctl, const LaunchCfg& cfg,
                         LaunchHook* hook) {
   if (nmaps <= 0 || nmaps > kMaxBatch) return cudaErrorInvalidValue;
-  const int grid = esdf_grid(cfg.num_sms, max_B, cfg.tune.esdf_ctas_per_sm);
+  const int threads = cfg.tune.esdf_threads;
+  const void* k = esdf_kernel(threads);
+  if (!k) return cudaErrorInvalidValue;
+  const int grid = esdf_grid(cfg.num_sms, max_B, cfg.tune.esdf_ctas_per_sm, threads);
   if (grid <= 0) return cudaErrorCooperativeLaunchTooLarge;
   const size_t smem = esdf_smem_bytes(max_B);
   void* args[] = {(void*)&maps_dev, (void*)&nmaps, (void*)&ctl};
   hook->begin(kKEsdf, cfg.stream);
-  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_esdf, dim3(grid), dim3(kThreads), args, smem, cfg.stream);
+  cudaError_t e = cudaLaunchCooperativeKernel(k, dim3(grid), dim3(threads), args, smem, cfg.stream);
   hook->end(kKEsdf, cfg.stream);
   return e;
 }

@@ -49,8 +49,14 @@ struct Tuning {
   int bin_ctas_per_sm;   // CTAs per SM of the point and group kernels
   int apply_ctas_per_sm;
   int esdf_ctas_per_sm;  // resident CTAs per SM of the cooperative ESDF grid
+  int esdf_threads;      // threads per ESDF CTA (256 or 512): one CTA relaxes one tile at a time
 };
-constexpr Tuning kDefaultTuning = {16, 16, 16, 8};
+// Start point of the batch autotuner (the ESDF grid is clamped to the kernel's occupancy).
+constexpr Tuning kDefaultTuning = {16, 16, 16, 8, 256};
+// Calls on one map: its ESDF waves activate few tiles per round (about one per SM), so the
+// round time is the latency of one tile's local relaxation; wide CTAs shorten it, and a small
+// grid shortens each round's grid barrier.
+constexpr Tuning kMapTuning = {16, 16, 16, 2, 512};
 
 struct LaunchCfg {
   int num_sms;
@@ -99,7 +105,7 @@ cudaError_t launch_import(const DevMap& m, const int* vox, const float* D, const
 
 // esdf.cu: one cooperative launch updates the ESDF of nmaps maps (device array of DevMap)
 size_t esdf_smem_bytes(int max_B);
-int esdf_grid(int num_sms, int max_B, int ctas_per_sm);
+int esdf_grid(int num_sms, int max_B, int ctas_per_sm, int threads);
 cudaError_t launch_esdf(const DevMap* maps_dev, int nmaps, int max_B, EsdfCtl* ctl, const LaunchCfg& cfg,
                         LaunchHook* hook);
 
