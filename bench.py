@@ -36,9 +36,25 @@ WORKLOAD = (
 N_QUERIES = 10000
 FLUSH_BYTES = 256 << 20  # > 129 MB L2
 
-# DRAM bytes per launch of the dominant kernel from one ncu capture, keyed by the kernel
-# source it was taken on (None: no capture for the current source).
-NCU_TRAFFIC = {}
+# DRAM bytes (read + write) per launch of a kernel from one ncu capture, keyed by the kernel
+# and the SHA-256 prefix of the source file it was captured on: once that source changes the
+# entry no longer matches and the reported traffic is null.
+NCU_TRAFFIC = {
+    # k_esdf<512>, room workload, one scan (dram__bytes_read.sum 2,291,968 + write 256)
+    ("esdf", "esdf.cu", "bedd3884d1dede1b"): 2292224,
+}
+KERNEL_SOURCE = {"esdf": "esdf.cu", "integrate_rays": "integrate.cu", "apply": "integrate.cu", "bin_points": "integrate.cu", "query": "query.cu"}
+
+
+def _ncu_traffic(kernel: str):
+    import hashlib
+
+    src = KERNEL_SOURCE.get(kernel)
+    if src is None:
+        return None
+    with open(os.path.join(ROOT, "paper_1611_03631_gb300", "csrc", src), "rb") as f:
+        h = hashlib.sha256(f.read()).hexdigest()[:16]
+    return NCU_TRAFFIC.get((kernel, src, h))
 
 
 def _scene(frames: int):
@@ -89,6 +105,9 @@ SERVE_SLOTS = 128
 SERVE_BUDGET = 120e9
 SERVE_CAPACITY = {"room": 2048, "lidar_terrain": 1 << 16}
 SERVE_ARRIVALS = 32.0  # sessions per second
+SERVE_SATURATED_ARRIVALS = 1024.0
+SERVE_C1_ARRIVALS = 64.0
+SERVE_C1_CAPACITY = {"plane_sphere": 45056}  # the 10-frame circle allocates about 42.3k blocks of 8^3
 
 
 def _batch_sets(n_maps: int = BATCH_MAPS):
@@ -219,28 +238,86 @@ def run_batched(args, vbx, torch, dev):
     }
 
 
-def run_served(args, vbx, torch):
-    from paper_1611_03631_gb300 import serve
+def _serve_c1_sets():
+    from paper_1611_03631_gb300 import scenes
 
-    sets = _serve_sets()
+    return {"plane_sphere": [scenes.plane_sphere(seed=60 + i) for i in range(4)]}
+
+
+def _serve_once(serve, sets, arrivals: float, capacity):
     pool = serve.ScanPool(sets, n_queries=N_QUERIES)
-    srv = serve.MapServer(pool, slots=SERVE_SLOTS, hbm_budget=SERVE_BUDGET, capacity=SERVE_CAPACITY, use_graph=True)
+    srv = serve.MapServer(pool, slots=SERVE_SLOTS, hbm_budget=SERVE_BUDGET, capacity=capacity, use_graph=True)
     specs = serve.poisson_sessions(
         SERVE_SESSIONS,
         list(sets),
         {k: len(v) for k, v in sets.items()},
         {k: pool.frames(k) for k in sets},
-        sessions_per_s=SERVE_ARRIVALS,
+        sessions_per_s=arrivals,
         scans_per_session=16,
     )
     res = srv.run(specs)
     srv.close()
-    res["workload"] = (
-        f"{SERVE_SESSIONS} robot sessions arriving as a Poisson process ({SERVE_ARRIVALS:.0f}/s), half room RGB-D 640x480 (v=0.05 m), "
-        "half LiDAR 64x2048 terrain (v=0.2 m), 16 scans each at U(10,30) Hz, each scan followed by 10k "
-        f"distance+gradient queries within 2 m of the sensor; {SERVE_SLOTS} batch slots, {SERVE_BUDGET/1e9:.0f} GB map budget"
-    )
     return res
+
+
+def run_served(args, vbx, torch):
+    """Three served runs of 256 sessions: the mixed room/LiDAR stream at a moderate arrival rate
+    (latency under load), the same stream arriving all but at once (the server's capacity in
+    scans/s, latency then queue-dominated), and sessions of the tiny plane+sphere scene."""
+    from paper_1611_03631_gb300 import serve
+
+    res = _serve_once(serve, _serve_sets(), SERVE_ARRIVALS, SERVE_CAPACITY)
+    common = (
+        f"16 scans each at U(10,30) Hz, each scan followed by {N_QUERIES // 1000}k distance+gradient queries within 2 m of "
+        f"the sensor; {SERVE_SLOTS} batch slots, {SERVE_BUDGET/1e9:.0f} GB map budget"
+    )
+    res["workload"] = (
+        f"{SERVE_SESSIONS} robot sessions arriving as a Poisson process ({SERVE_ARRIVALS:.0f}/s), half room RGB-D 640x480 "
+        f"(v=0.05 m), half LiDAR 64x2048 terrain (v=0.2 m), " + common
+    )
+    sat = _serve_once(serve, _serve_sets(), SERVE_SATURATED_ARRIVALS, SERVE_CAPACITY)
+    sat["workload"] = f"as above, sessions arriving at {SERVE_SATURATED_ARRIVALS:.0f}/s (more scans offered than the GPU serves)"
+    res["saturated"] = sat
+    c1_sets = _serve_c1_sets()
+    c1 = _serve_once(serve, c1_sets, SERVE_C1_ARRIVALS, SERVE_C1_CAPACITY)
+    c1["workload"] = (
+        f"{SERVE_SESSIONS} sessions of the plane+sphere scene (64x48 depth, v=0.1 m, 8^3 blocks) arriving at "
+        f"{SERVE_C1_ARRIVALS:.0f}/s, " + common
+    )
+    c1["plain"] = _plain_plane_sphere(vbx, torch, c1_sets["plane_sphere"][0])
+    res["plane_sphere"] = c1
+    return res
+
+
+def _plain_plane_sphere(vbx, torch, s, steps: int = 40, warmup: int = 3):
+    """The plain per-scan path on one plane+sphere map (integrate, ESDF, 10k queries per scan,
+    one scan at a time), for comparison with the served form at the same scan size."""
+    from paper_1611_03631_gb300 import scenes
+
+    F = len(s.points)
+    pts = [torch.from_numpy(p).cuda() for p in s.points]
+    qs = [torch.from_numpy(scenes.random_queries(s, N_QUERIES, radius=2.0, seed=200 + i, scan_index=i)).cuda() for i in range(F)]
+    out = (
+        torch.empty(N_QUERIES, dtype=torch.float32, device="cuda"),
+        torch.empty((N_QUERIES, 3), dtype=torch.float32, device="cuda"),
+        torch.empty(N_QUERIES, dtype=torch.uint8, device="cuda"),
+    )
+    m = vbx.Map.from_scene_params(s.params, block_capacity=SERVE_C1_CAPACITY["plane_sphere"], max_points=max(int(p.shape[0]) for p in pts))
+    ms = []
+    for k in range(warmup + steps):
+        i = k % F
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        m.integrate_scan(pts[i], s.poses[i])
+        m.update_esdf()
+        m.query(qs[i], out=out)
+        e1.record()
+        e1.synchronize()
+        if k >= warmup:
+            ms.append(e0.elapsed_time(e1))
+    m.close()
+    return dict(scans_per_s=len(ms) / (sum(ms) / 1e3), p50_ms=float(np.percentile(ms, 50)), p99_ms=float(np.percentile(ms, 99)))
 
 
 def _queries(s, frames: int):
@@ -527,7 +604,7 @@ def run_gpu(args):
         "peak": peak,
         "unit": "GB/s",
         "frac": achieved / peak,
-        "traffic": NCU_TRAFFIC.get(dom),
+        "traffic": _ncu_traffic(dom),
         "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6800 GB/s",
         "kernels_ms_per_step": {k: v["ms"] / args.steps for k, v in kt.items() if v["launches"]},
     }
