@@ -246,7 +246,8 @@ def _serve_c1_sets():
 
 def _serve_once(serve, sets, arrivals: float, capacity):
     pool = serve.ScanPool(sets, n_queries=N_QUERIES)
-    srv = serve.MapServer(pool, slots=SERVE_SLOTS, hbm_budget=SERVE_BUDGET, capacity=capacity, use_graph=True)
+    scratch = serve.scratch_for_pool(pool, capacity)
+    srv = serve.MapServer(pool, slots=SERVE_SLOTS, hbm_budget=SERVE_BUDGET, capacity=capacity, use_graph=True, scratch=scratch)
     specs = serve.poisson_sessions(
         SERVE_SESSIONS,
         list(sets),
@@ -257,6 +258,8 @@ def _serve_once(serve, sets, arrivals: float, capacity):
     )
     res = srv.run(specs)
     srv.close()
+    res["scratch_blocks"] = scratch
+    res["map_bytes"] = {k: srv.map_bytes(k) for k in sets}
     return res
 
 

@@ -17,9 +17,9 @@
 #include "vbx_internal.cuh"
 
 namespace vbx {
-const char* const kKernelNames[kNumKernels] = {"reset_counters", "bin_points",  "group_rays", "link_blocks",
-                                               "integrate_rays", "touched",     "apply",      "esdf",
-                                               "query",          "import_alloc", "import_set", "init_groups"};
+const char* const kKernelNames[kNumKernels] = {"reset_counters", "bin_points", "group_rays",   "link_blocks",
+                                               "integrate_rays", "apply",      "esdf",         "query",
+                                               "import_alloc",   "import_set", "init_groups"};
 }  // namespace vbx
 
 namespace {
@@ -131,6 +131,7 @@ struct vbx_map_s {
   int64_t last_points_in = 0;
   uint32_t gtab_entries = 0;
   uint64_t version = 0;  // bumped whenever d (and so d_dev) changes
+  uint32_t scan_epoch = 0;  // epoch of the last integrated scan (claims of scratch blocks)
   std::vector<void*> allocs;
   MapHook hook;
 
@@ -178,6 +179,8 @@ vbx_status read_error(vbx_map_t m, cudaStream_t s) {
   if (err & vbx::kErrPoolFull) return fail(VBX_ERR_OUT_OF_MEMORY, "block pool exhausted (block_capacity)");
   if (err & vbx::kErrHashFull) return fail(VBX_ERR_HASH_FULL, "block hash probe limit reached");
   if (err & vbx::kErrGroupTable) return fail(VBX_ERR_HASH_FULL, "per-scan group table full");
+  if (err & vbx::kErrScratchFull)
+    return fail(VBX_ERR_OUT_OF_MEMORY, "the scan entered more blocks than scratch_blocks; it was not integrated");
   return fail(VBX_ERR_CUDA, "unknown device error 0x%x", err);
 }
 
@@ -207,6 +210,19 @@ vbx_status ensure_scratch(vbx_map_t m, int64_t n, cudaStream_t s) {
   }
   m->version += 1;
   return VBX_OK;
+}
+
+// Epoch of the next scan of m. Epochs only grow, so a block's scratch claim from an earlier
+// scan never matches; on wrap-around the claim and epoch arrays are cleared first.
+cudaError_t next_scan_epoch(vbx_map_t m, cudaStream_t s, unsigned* ep) {
+  if (m->scan_epoch == 0xffffffffu) {
+    cudaError_t e = cudaMemsetAsync(m->d.hclaim, 0, ((size_t)m->d.hmask + 1) * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->d.sepoch, 0, (size_t)m->d.cap_blocks * 4, s);
+    if (e != cudaSuccess) return e;
+    m->scan_epoch = 0;
+  }
+  *ep = ++m->scan_epoch;
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -292,15 +308,21 @@ vbx_status vbx_create_map(float voxel_size, int voxels_per_block, float truncati
       return cuda_fail(e, "allocate " #ptr);                  \
     }                                                         \
   } while (0)
+  const int64_t scr = opt.scratch_blocks > 0 ? std::min<int64_t>(opt.scratch_blocks, cap) : cap;
+  d.scr_cap = (uint32_t)scr;
+  const size_t SV = (size_t)scr * B3;  // scratch voxels
   VBX_ALLOC(d.hkeys, H, 0xff);
   VBX_ALLOC(d.hvals, H, 0xff);
+  VBX_ALLOC(d.hclaim, H, 0);
   VBX_ALLOC(d.bcoord, (size_t)cap, 0);
   VBX_ALLOC(d.nbr, (size_t)cap * 27, 0xff);
+  VBX_ALLOC(d.sepoch, (size_t)cap, 0);
+  VBX_ALLOC(d.sidx, (size_t)cap, 0);
   VBX_ALLOC(d.tsdf, V, 0);
-  VBX_ALLOC(d.acc, 4 * V, 0);
-  VBX_ALLOC(d.touch, V, 0);
-  VBX_ALLOC(d.btouch, (size_t)cap, 0);
-  VBX_ALLOC(d.tlist, (size_t)cap, 0);
+  VBX_ALLOC(d.slist_h, (size_t)scr, 0);
+  VBX_ALLOC(d.slist, (size_t)scr, 0);
+  VBX_ALLOC(d.sacc, 4 * SV, 0);
+  VBX_ALLOC(d.stouch, SV, 0);
   VBX_ALLOC(d.esdf, V, 0);
   VBX_ALLOC(d.vflags, V, 0);
   VBX_ALLOC(d.rbits0, V / 32, 0);
@@ -368,7 +390,9 @@ vbx_status vbx_integrate_scan(vbx_map_t m, const float* points_dev, int64_t n, c
   if (st != VBX_OK) return st;
   vbx::Pose pose;
   std::memcpy(pose.T, T, sizeof(pose.T));
-  e = vbx::launch_integrate(vbx::single_batch(m->d, points_dev, (int)n, pose), m->cfg(stream), &m->hook);
+  unsigned ep = 0;
+  if ((e = next_scan_epoch(m, s, &ep)) != cudaSuccess) return cuda_fail(e, "scan epoch");
+  e = vbx::launch_integrate(vbx::single_batch(m->d, points_dev, (int)n, pose, ep), m->cfg(stream), &m->hook);
   if (e != cudaSuccess) return cuda_fail(e, "integrate launch");
   return VBX_OK;
 }
@@ -395,7 +419,9 @@ vbx_status vbx_integrate_scan_noalloc(vbx_map_t m, const float* points_dev, int6
   if (n == 0) return VBX_OK;
   vbx::Pose pose;
   std::memcpy(pose.T, T, sizeof(pose.T));
-  e = vbx::launch_integrate_noalloc(m->d, scratch, points_dev, (int)n, pose, m->cfg(stream), &m->hook);
+  unsigned ep = 0;
+  if ((e = next_scan_epoch(m, s, &ep)) != cudaSuccess) return cuda_fail(e, "scan epoch");
+  e = vbx::launch_integrate_noalloc(m->d, scratch, points_dev, (int)n, pose, ep, m->cfg(stream), &m->hook);
   if (e != cudaSuccess) return cuda_fail(e, "integrate launch");
   return VBX_OK;
 }
@@ -462,6 +488,7 @@ vbx_status vbx_get_stats(vbx_map_t m, vbx_stats* out, void* stream) {
   out->esdf_classify_ns = c.esdf_phase_ns[0];
   out->esdf_raise_ns = c.esdf_phase_ns[1];
   out->esdf_lower_ns = c.esdf_phase_ns[2];
+  out->touched_blocks = c.ntouched;
   return read_error(m, (cudaStream_t)stream);
 }
 
@@ -692,7 +719,8 @@ vbx_status batch_enqueue(vbx_batch_t b, int k, int flags, cudaStream_t s) {
   return VBX_OK;
 }
 
-vbx_status batch_stage(vbx_batch_t b, const vbx_scan_in* scans, const vbx_query_io* queries, int flags, int* k_out) {
+vbx_status batch_stage(vbx_batch_t b, const vbx_scan_in* scans, const vbx_query_io* queries, int flags, cudaStream_t s,
+                       int* k_out) {
   for (int i = 0; i < b->count; ++i) {
     if (flags & VBX_STEP_INTEGRATE) {
       if (!scans) return fail(VBX_ERR_INVALID_ARG, "scans is NULL");
@@ -720,6 +748,7 @@ vbx_status batch_stage(vbx_batch_t b, const vbx_scan_in* scans, const vbx_query_
     dm[i] = b->maps[i]->d;
     vbx::ScanDesc d{};
     if ((flags & VBX_STEP_INTEGRATE) && scans) {
+      if ((e = next_scan_epoch(b->maps[i], s, &d.epoch)) != cudaSuccess) return cuda_fail(e, "scan epoch");
       d.pts = scans[i].points_dev;
       d.n = (unsigned)scans[i].n;
       std::memcpy(d.T, scans[i].T_world_sensor, sizeof(d.T));
@@ -742,7 +771,7 @@ vbx_status batch_stage(vbx_batch_t b, const vbx_scan_in* scans, const vbx_query_
 
 vbx_status batch_run(vbx_batch_t b, const vbx_scan_in* scans, const vbx_query_io* queries, int flags, cudaStream_t s) {
   int k = 0;
-  vbx_status st = batch_stage(b, scans, queries, flags, &k);
+  vbx_status st = batch_stage(b, scans, queries, flags, s, &k);
   if (st != VBX_OK) return st;
   const int f = flags & 7;
   cudaError_t e;
@@ -1009,10 +1038,12 @@ vbx_status vbx_map_bytes(int B, const vbx_map_options* opt_in, int64_t* out) {
   const uint64_t H = next_pow2(cap * 2);
   const uint64_t pts = next_pow2((uint64_t)std::max<int64_t>(opt.max_points > 0 ? opt.max_points : (int64_t(1) << 20), 1024));
   const uint64_t entries = next_pow2(pts * 2);
+  const uint64_t scr = opt.scratch_blocks > 0 ? std::min<uint64_t>((uint64_t)opt.scratch_blocks, cap) : cap;
   uint64_t bytes = 0;
-  bytes += H * (8 + 4);                                   // block hash
-  bytes += cap * (12 + 27 * 4 + 4 + 4 + 4);               // block coords, links, touch flag, lists
-  bytes += V * (8 + 32 + 4 + 8 + 1 + 4 + 4);              // tsdf, sums, touch, esdf, flags, lists
+  bytes += H * (8 + 4 + 4);                               // block hash, scratch claims
+  bytes += cap * (12 + 27 * 4 + 4 + 4 + 4);               // block coords, links, scratch index/epoch, new list
+  bytes += V * (8 + 8 + 1 + 4 + 4);                       // tsdf, esdf, flags, updated and dirty lists
+  bytes += scr * (4 + 4) + scr * B3 * (32 + 4);           // scratch blocks: lists, sums, touch flags
   bytes += 4 * (V / 32) * 4;                              // frontier bitmasks
   bytes += tiles * (2 * 4 + 4 * 8);                       // tile stamps, active lists
   bytes += entries * sizeof(vbx::GroupEntry) + pts * (4 + 16);  // per-scan scratch
@@ -1040,6 +1071,7 @@ vbx_status vbx_reset_map(vbx_map_t m, void* stream) {
   const size_t V = nb * B3;
   vbx::DevMap& d = m->d;
   const size_t tiles = nb << d.tile_shift;
+  const size_t SV = (size_t)std::min<uint32_t>(c.ntouched, d.scr_cap) * B3;  // scratch of the last scan
   struct Clear {
     void* p;
     size_t bytes;
@@ -1048,11 +1080,12 @@ vbx_status vbx_reset_map(vbx_map_t m, void* stream) {
       {d.hkeys, ((size_t)d.hmask + 1) * 8, 0xff},
       {d.hvals, ((size_t)d.hmask + 1) * 4, 0xff},
       {d.nbr, nb * 27 * 4, 0xff},
+      {d.hclaim, ((size_t)d.hmask + 1) * 4, 0},
       {d.bcoord, nb * 12, 0},
-      {d.btouch, nb * 4, 0},
+      {d.sepoch, nb * 4, 0},
       {d.tsdf, V * 8, 0},
-      {d.acc, V * 32, 0},
-      {d.touch, V * 4, 0},
+      {d.sacc, SV * 32, 0},
+      {d.stouch, SV * 4, 0},
       {d.esdf, V * 8, 0},
       {d.vflags, V, 0},
       {d.rbits0, V / 8, 0},

@@ -2,15 +2,17 @@
 //   k_bin_points     A1+A2  transform, filter, voxel key; grouped raycasting bins points into
 //                           a per-scan hash table with exact integer sums (order-independent)
 //   k_group_rays     A2+A3  group mean and weight -> one ray per group; block-level DDA over
-//                           the ray and lock-free insertion of its blocks into the block hash
-//   k_link_blocks    A3     26-neighbour links of the new blocks (O(1) neighbour access later)
+//                           the ray and lock-free insertion of its blocks into the block hash,
+//                           and a per-scan scratch block for every block the ray enters
+//   k_link_blocks    A3     26-neighbour links of the new blocks (O(1) neighbour access later);
+//                           pool slot <-> scratch block of the blocks entered this scan
 //   k_integrate_rays A4     voxel-level integer DDA; Eq. (1) distance, Eq. (2)/(4) weight;
-//                           per-voxel sums of w and w*d in 2^-28 fixed point with integer
-//                           atomics, pre-aggregated across the warp (order-independent, so
-//                           the result does not depend on scheduling)
-//   k_touched        A5     compacts the blocks the rays entered into a per-map list
+//                           per-voxel sums of w and w*d as exact two-part fixed point numbers
+//                           with integer atomics into the scratch blocks, pre-aggregated across
+//                           the warp (order-independent, so the result does not depend on
+//                           scheduling)
 //   k_apply          A5     Eq. (3) merge of each voxel that received records (one thread per
-//                           voxel of a touched block); queues it for the ESDF
+//                           voxel of a scratch block); queues it for the ESDF
 // All float32 arithmetic that decides a set (keys, endpoints, visited voxels, w > 0) uses
 // explicitly rounded intrinsics, so the compiler cannot contract or reorder it.
 #include <cuda_runtime.h>
@@ -256,6 +258,25 @@ __global__ void __launch_bounds__(kThreads) k_bin_points(Batch b) {
 }
 
 // ------------------------------------------------------------------------------- A2 + A3
+// The first ray of scan `ep` that enters the block of hash entry h gives the block a scratch
+// block for the scan's sums (an entry's claim epoch only grows, so no reset pass is needed).
+__device__ __forceinline__ void claim_scratch(const DevMap& m, uint32_t h, unsigned ep) {
+  if (h == kInvalid || __ldcg(&m.hclaim[h]) == ep) return;
+  if (atomicExch(&m.hclaim[h], ep) == ep) return;
+  const unsigned i = atomicAdd(&m.ctr->ntouched, 1u);
+  if (i < m.scr_cap)
+    m.slist_h[i] = h;
+  else
+    atomicOr(&m.ctr->error, kErrScratchFull);
+}
+
+// Scratch blocks usable by this scan: none if the scan entered more blocks than the scratch
+// holds (the scan is then rejected as a whole and the map keeps its previous state).
+__device__ __forceinline__ unsigned scratch_blocks(const DevMap& m) {
+  const unsigned n = __ldcg(&m.ctr->ntouched);
+  return n <= m.scr_cap ? n : 0u;
+}
+
 __global__ void __launch_bounds__(kThreads) k_group_rays(Batch b) {
   __shared__ unsigned pfx[kMaxBatch + 1];
   const int nm = nmaps_of(b);
@@ -300,10 +321,11 @@ __global__ void __launch_bounds__(kThreads) k_group_rays(Batch b) {
     // voxel traversal, so it visits exactly the blocks of the traversed voxels
     Dda dda;
     dda.init(g.S, g.E, 16 + m.blog);
-    block_insert(m, dda.cx, dda.cy, dda.cz);
+    const unsigned ep = sd.epoch;
+    claim_scratch(m, block_insert(m, dda.cx, dda.cy, dda.cz), ep);
     for (int left = dda.steps(); left > 0; --left) {
       dda.step();
-      block_insert(m, dda.cx, dda.cy, dda.cz);
+      claim_scratch(m, block_insert(m, dda.cx, dda.cy, dda.cz), ep);
     }
   }
 }
@@ -312,12 +334,26 @@ __global__ void __launch_bounds__(kThreads) k_group_rays(Batch b) {
 __global__ void __launch_bounds__(kThreads) k_link_blocks(Batch b) {
   __shared__ unsigned pfx[kMaxBatch + 1];
   const int nm = nmaps_of(b);
-  // one thread per (new block, direction)
-  const unsigned total = cta_prefix(pfx, b, [&](unsigned mi) { return __ldcg(&map_of(b, mi).ctr->nnew) * 27u; });
+  // one thread per (new block, direction), then one per scratch block of the scan
+  const unsigned total = cta_prefix(pfx, b, [&](unsigned mi) {
+    const DevMap& m = map_of(b, mi);
+    return __ldcg(&m.ctr->nnew) * 27u + scratch_blocks(m);
+  });
   for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
     const unsigned mi = map_index(pfx, nm, t);
     const DevMap& m = map_of(b, mi);
+    const unsigned nl = __ldcg(&m.ctr->nnew) * 27u;
     const unsigned u = t - pfx[mi];
+    if (u >= nl) {  // scratch block i <-> pool slot (the slots were published by k_group_rays)
+      const unsigned i = u - nl;
+      const uint32_t slot = __ldcg(&m.hvals[m.slist_h[i]]);
+      m.slist[i] = slot;
+      if (slot < m.cap_blocks) {
+        m.sidx[slot] = i;
+        m.sepoch[slot] = scan_of(b, mi).epoch;
+      }
+      continue;
+    }
     const uint32_t p = m.newblk[u / 27u];
     if (p >= m.cap_blocks) continue;
     const int k = (int)(u % 27u);
@@ -341,13 +377,19 @@ __device__ __forceinline__ void fx_split(float x, long long* hi, long long* lo) 
   *lo = __float2ll_rn(__fmul_rn(__fsub_rn(q, t), kAccLoScale));
 }
 
-// All four parts and the touch flag are fire-and-forget reductions (no returned value), so
-// the ray loop never waits on an atomic.
-__device__ __forceinline__ void accumulate(const DevMap& m, uint32_t vid, const long long v[4]) {
-  unsigned long long* a = &m.acc[4 * (size_t)vid];
+// All four parts and the touch flag of scratch voxel sv are fire-and-forget reductions (no
+// returned value), so the ray loop never waits on an atomic.
+__device__ __forceinline__ void accumulate(const DevMap& m, uint32_t sv, const long long v[4]) {
+  unsigned long long* a = &m.sacc[4 * (size_t)sv];
   for (int j = 0; j < 4; ++j)
     if (v[j] != 0) atomicAdd(&a[j], (unsigned long long)v[j]);
-  atomicOr(&m.touch[vid], 1u);
+  atomicOr(&m.stouch[sv], 1u);
+}
+
+// Scratch block of pool slot `slot` in scan ep (kInvalid if the scan has none for it).
+__device__ __forceinline__ uint32_t scratch_of(const DevMap& m, uint32_t slot, unsigned ep) {
+  if (slot == kInvalid) return kInvalid;
+  return __ldcg(&m.sepoch[slot]) == ep ? __ldcg(&m.sidx[slot]) : kInvalid;
 }
 
 __global__ void __launch_bounds__(kThreads) k_integrate_rays(Batch b) {
@@ -370,15 +412,16 @@ __global__ void __launch_bounds__(kThreads) k_integrate_rays(Batch b) {
     }
     rec_map = mi;
     const float s[3] = {sd.T[3], sd.T[7], sd.T[11]};
+    const unsigned ep = sd.epoch;
     const int B = m.B, blog = m.blog;
     const unsigned gi = base - pfx[mi] + lane;
-    bool active = gi < __ldcg(&m.ctr->ngroups);
+    bool active = gi < __ldcg(&m.ctr->ngroups) && __ldcg(&m.ctr->ntouched) <= m.scr_cap;
     RayGeom g;
     float Wg = 0.0f;
     Dda dda;
     int left = 0;
     int bcx = 0, bcy = 0, bcz = 0;
-    uint32_t slot = kInvalid;
+    uint32_t slot = kInvalid, sb = kInvalid;
     if (active) {
       const float4 r = m.rays[gi];
       const float pbar[3] = {r.x, r.y, r.z};
@@ -391,7 +434,7 @@ __global__ void __launch_bounds__(kThreads) k_integrate_rays(Batch b) {
         bcy = dda.cy >> blog;
         bcz = dda.cz >> blog;
         slot = block_lookup(m, bcx, bcy, bcz);
-        if (slot != kInvalid) atomicOr(&m.btouch[slot], 1u);
+        sb = scratch_of(m, slot, ep);
       }
     }
     while (__any_sync(kFull, active)) {
@@ -419,9 +462,9 @@ __global__ void __launch_bounds__(kThreads) k_integrate_rays(Batch b) {
           else if (d < -m.eps)
             w = __fmul_rn(Wg, __fdiv_rn(__fadd_rn(d, m.delta), __fsub_rn(m.delta, m.eps)));
         }
-        if (w > 0.0f && slot != kInvalid) {
+        if (w > 0.0f && sb != kInvalid) {
           const uint32_t l = (uint32_t)((((dda.cz & (B - 1)) << blog | (dda.cy & (B - 1))) << blog) | (dda.cx & (B - 1)));
-          vid = (slot << m.b3log) | l;
+          vid = (sb << m.b3log) | l;  // scratch voxel
           fx_split(w, &qv[0], &qv[2]);
           fx_split(__fmul_rn(w, d), &qv[1], &qv[3]);
           ++nrec;
@@ -454,7 +497,7 @@ __global__ void __launch_bounds__(kThreads) k_integrate_rays(Batch b) {
           }
           if (k >= 0) {
             slot = slot != kInvalid ? __ldg(&m.nbr[(size_t)slot * 27 + k]) : block_lookup(m, bcx, bcy, bcz);
-            if (slot != kInvalid) atomicOr(&m.btouch[slot], 1u);
+            sb = scratch_of(m, slot, ep);
           }
         }
       }
@@ -494,25 +537,7 @@ __device__ __forceinline__ void append(uint32_t* list, unsigned* count, uint32_t
   list[base + __popc(peers & ((1u << lane) - 1u))] = vid;
 }
 
-// Compacts the blocks whose touch flag the rays set into the map's touched-block list.
-__global__ void __launch_bounds__(kThreads) k_touched(Batch b) {
-  __shared__ unsigned pfx[kMaxBatch + 1];
-  const int nm = nmaps_of(b);
-  const unsigned total = cta_prefix(pfx, b, [&](unsigned mi) {
-    const DevMap& m = map_of(b, mi);
-    return min(__ldcg(&m.ctr->blocks), m.cap_blocks);
-  });
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
-    const unsigned mi = map_index(pfx, nm, i);
-    const DevMap& m = map_of(b, mi);
-    const unsigned blk = i - pfx[mi];
-    if (m.btouch[blk] == 0u) continue;
-    m.btouch[blk] = 0u;
-    append(m.tlist, &m.ctr->ntouched, blk);
-  }
-}
-
-// One thread per voxel of a touched block: every voxel that received records this scan gets
+// One thread per voxel of a scratch block: every voxel that received records this scan gets
 // the Eq. (3) merge, its sums and flag are cleared, and it joins the scan's updated list and
 // (once) the queue of the next ESDF update.
 __global__ void __launch_bounds__(kThreads) k_apply(Batch b) {
@@ -520,19 +545,19 @@ __global__ void __launch_bounds__(kThreads) k_apply(Batch b) {
   const int nm = nmaps_of(b);
   const unsigned total = cta_prefix(pfx, b, [&](unsigned mi) {
     const DevMap& m = map_of(b, mi);
-    return __ldcg(&m.ctr->ntouched) << m.b3log;
+    return scratch_blocks(m) << m.b3log;
   });
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
     const unsigned mi = map_index(pfx, nm, i);
     const DevMap& m = map_of(b, mi);
-    const unsigned u = i - pfx[mi];
-    const uint32_t vid = (m.tlist[u >> m.b3log] << m.b3log) | (u & ((1u << m.b3log) - 1u));
-    if (m.touch[vid] == 0u) continue;
-    m.touch[vid] = 0u;
-    ulonglong2* a = reinterpret_cast<ulonglong2*>(&m.acc[4 * (size_t)vid]);
+    const unsigned sv = i - pfx[mi];  // scratch voxel
+    if (m.stouch[sv] == 0u) continue;
+    m.stouch[sv] = 0u;
+    ulonglong2* a = reinterpret_cast<ulonglong2*>(&m.sacc[4 * (size_t)sv]);
     const ulonglong2 hi = a[0], lo = a[1];
     a[0] = make_ulonglong2(0ull, 0ull);
     a[1] = make_ulonglong2(0ull, 0ull);
+    const uint32_t vid = (m.slist[sv >> m.b3log] << m.b3log) | (sv & ((1u << m.b3log) - 1u));
     const float Sw = __fadd_rn(__fmul_rn(__ll2float_rn((long long)hi.x), kAccInvScale),
                                __fmul_rn(__ll2float_rn((long long)lo.x), kAccLoInvScale));
     const float Swd = __fadd_rn(__fmul_rn(__ll2float_rn((long long)hi.y), kAccInvScale),
@@ -585,7 +610,7 @@ int grid_for(long long items, int num_sms, int per_sm) {
 
 }  // namespace
 
-Batch single_batch(const DevMap& m, const float* pts, int n, const Pose& T) {
+Batch single_batch(const DevMap& m, const float* pts, int n, const Pose& T, unsigned epoch) {
   Batch b;
   std::memset(&b, 0, sizeof(b));
   b.maps = nullptr;
@@ -595,6 +620,7 @@ Batch single_batch(const DevMap& m, const float* pts, int n, const Pose& T) {
   b.one = m;
   b.one_scan.pts = pts;
   b.one_scan.n = (unsigned)n;
+  b.one_scan.epoch = epoch;
   std::memcpy(b.one_scan.T, T.T, sizeof(T.T));
   return b;
 }
@@ -631,9 +657,6 @@ cudaError_t launch_integrate(const Batch& b, const LaunchCfg& cfg, LaunchHook* h
   hook->begin(kKIntegrateRays, s);
   k_integrate_rays<<<grays, kThreads, 0, s>>>(b);
   hook->end(kKIntegrateRays, s);
-  hook->begin(kKTouched, s);
-  k_touched<<<cfg.num_sms * 4, kThreads, 0, s>>>(b);
-  hook->end(kKTouched, s);
   hook->begin(kKApply, s);
   k_apply<<<cfg.num_sms * cfg.tune.apply_ctas_per_sm, kThreads, 0, s>>>(b);
   hook->end(kKApply, s);
@@ -703,7 +726,7 @@ cudaError_t noalloc_scratch_setup(int device, void** ptr) {
 }
 
 cudaError_t launch_integrate_noalloc(const DevMap& m, void* scratch, const float* pts, int n, const Pose& T,
-                                     const LaunchCfg& cfg, LaunchHook* hook) {
+                                     unsigned epoch, const LaunchCfg& cfg, LaunchHook* hook) {
   DevMap ms = m;
   unsigned char* base = static_cast<unsigned char*>(scratch);
   ms.gtab = reinterpret_cast<GroupEntry*>(base);
@@ -712,7 +735,7 @@ cudaError_t launch_integrate_noalloc(const DevMap& m, void* scratch, const float
   ms.rays = reinterpret_cast<float4*>(base + kNoAllocGroupBytes + kNoAllocListBytes);
   cudaError_t e = launch_init_groups(ms.gtab, kNoAllocGroupEntries, cfg.stream, hook);
   if (e != cudaSuccess) return e;
-  return launch_integrate(single_batch(ms, pts, n, T), cfg, hook);
+  return launch_integrate(single_batch(ms, pts, n, T, epoch), cfg, hook);
 }
 
 }  // namespace vbx

@@ -17,7 +17,7 @@ constexpr int kMaxBatch = 256;  // maps per batched launch (one prefix entry per
 struct ScanDesc {
   const float* pts;  // n x 3 float32, sensor frame (device)
   unsigned n;
-  unsigned pad;
+  unsigned epoch;  // scan epoch of the map (> 0, increases by one per integrated scan)
   float T[16];  // row-major T_world_sensor
 };
 
@@ -77,7 +77,6 @@ enum KernelId {
   kKGroupRays,
   kKLink,
   kKIntegrateRays,
-  kKTouched,
   kKApply,
   kKEsdf,
   kKQuery,
@@ -98,8 +97,8 @@ cudaError_t launch_reset_counters(const Batch& b, const LaunchCfg& cfg, LaunchHo
 constexpr int kNoAllocMaxPoints = 1 << 16;
 cudaError_t noalloc_scratch_setup(int device, void** ptr);
 cudaError_t launch_integrate_noalloc(const DevMap& m, void* scratch, const float* pts, int n, const Pose& T,
-                                     const LaunchCfg& cfg, LaunchHook* hook);
-Batch single_batch(const DevMap& m, const float* pts, int n, const Pose& T);
+                                     unsigned epoch, const LaunchCfg& cfg, LaunchHook* hook);
+Batch single_batch(const DevMap& m, const float* pts, int n, const Pose& T, unsigned epoch = 0);
 cudaError_t launch_import(const DevMap& m, const int* vox, const float* D, const float* W, int n,
                           const LaunchCfg& cfg, LaunchHook* hook);
 

@@ -1,23 +1,28 @@
 // vbx_internal.cuh -- device-side layout and helpers of the GB300 map update.
 //
 // HBM layout of one map (all arrays indexed by pool slot or by voxel id):
-//   block hash     : hkeys[H] u64 packed block key (EMPTY = ~0), hvals[H] u32 pool slot
-//   per block      : btouch[slot] u32 flag: a ray of the current scan entered the block
-//                    bcoord[slot] int3, nbr[slot*27 + k] u32 slot of the neighbour block in
-//                    direction k = (dx+1)*9 + (dy+1)*3 + (dz+1) (k = 13 is the block itself)
+//   block hash     : hkeys[H] u64 packed block key (EMPTY = ~0), hvals[H] u32 pool slot,
+//                    hclaim[H] u32 scan epoch of the last scan whose rays entered the block
+//   per block      : bcoord[slot] int3, nbr[slot*27 + k] u32 slot of the neighbour block in
+//                    direction k = (dx+1)*9 + (dy+1)*3 + (dz+1) (k = 13 is the block itself),
+//                    sepoch[slot] / sidx[slot] u32 scan epoch and scratch block of the block
 //   per voxel      : voxel id vid = slot * B^3 + ((lz*B + ly)*B + lx)
 //                    tsdf[vid]   float2 (D, W)                          8 B
-//                    acc[4*vid]  i64 sums of w and w*d, each as an exact two-part fixed
-//                                point number (2^-28 part, 2^-60 part)      32 B (zero between scans)
-//                    touch[vid]  u32 flag: the voxel received a record in the current scan
 //                    esdf[vid]   u64 packed {d f32 | flags u8 | parent u8} 8 B
 //                    vflags[vid] u8 (bit0 queued for the ESDF)
 //                    rbits/lbits[2][vid/32] u32 raise / lower frontier bitmasks (current, next)
+//                    dirty list slot (u32)
 //   per ESDF tile  : bstamp_r/bstamp_l[item] u32 epochs de-duplicating tile activations, item =
 //                    slot << tile_shift | tile (a tile is the block, or an 8^3 octant of a 16^3 one)
+//   per-scan sums  : scratch blocks, one per block the scan's rays enter (scr_cap of them):
+//                    slist_h[i] / slist[i] u32 hash entry and pool slot of scratch block i,
+//                    sacc[4*sv] i64 sums of w and w*d of scratch voxel sv = i * B^3 + local,
+//                    each an exact two-part fixed point number (2^-28 part, 2^-60 part),
+//                    stouch[sv] u32 flag: the voxel received a record; updated list (u32)
+//                    (all zero between scans)
 //   lists          : updated (last scan), dirty (since last ESDF); the ESDF's active
 //                    (map, block) lists live in the launch group's EsdfCtl
-//   per-scan scratch: group hash table (64 B entries), group list, rays (float4)
+//   per-scan points: group hash table (64 B entries), group list, rays (float4)
 #pragma once
 
 #include <cstdint>
@@ -41,6 +46,7 @@ constexpr unsigned kErrPoolFull = 1u;
 constexpr unsigned kErrHashFull = 2u;
 constexpr unsigned kErrTimeout = 4u;
 constexpr unsigned kErrGroupTable = 8u;
+constexpr unsigned kErrScratchFull = 16u;
 
 // ESDF voxel word: bits 63..32 float d, bits 15..8 flags, bits 7..0 parent direction
 constexpr unsigned kObserved = 1u;
@@ -69,7 +75,7 @@ struct Counters {
   unsigned int nnew;
   unsigned int nupdated;
   unsigned int npoints_valid;
-  unsigned int ntouched;  // blocks entered by the scan's rays (compacted list length)
+  unsigned int ntouched;  // blocks entered by the scan's rays (scratch blocks claimed)
   unsigned int pad0;
   unsigned long long nrecords;
   // ---- persistent
@@ -117,16 +123,21 @@ struct DevMap {
   // block hash
   unsigned long long* hkeys;
   uint32_t* hvals;
+  uint32_t* hclaim;
   uint32_t hmask;
   // pool
   uint32_t cap_blocks;
   int3* bcoord;
   uint32_t* nbr;
+  uint32_t* sepoch;
+  uint32_t* sidx;
   float2* tsdf;
-  unsigned long long* acc;
-  uint32_t* touch;
-  uint32_t* btouch;
-  uint32_t* tlist;  // compacted list of the blocks touched by the current scan
+  // per-scan sums (scratch blocks)
+  uint32_t scr_cap;
+  uint32_t* slist_h;
+  uint32_t* slist;
+  unsigned long long* sacc;
+  uint32_t* stouch;
   unsigned long long* esdf;
   uint8_t* vflags;
   uint32_t* rbits0;
@@ -186,13 +197,14 @@ __device__ __forceinline__ uint32_t block_lookup(const DevMap& m, int bx, int by
 
 // Lock-free find-or-insert (Sec. III: O(1) hashed block insertion). The thread that claims an
 // empty slot with atomicCAS takes a pool slot and publishes it; others see the key and move on.
-// Slots are read only by later kernels, so nobody waits here.
-__device__ __forceinline__ void block_insert(const DevMap& m, int bx, int by, int bz) {
+// Slots are read only by later kernels, so nobody waits here. Returns the hash entry of the
+// block (its pool slot may not be published yet), or kInvalid if the table is full.
+__device__ __forceinline__ uint32_t block_insert(const DevMap& m, int bx, int by, int bz) {
   const unsigned long long key = pack_key(bx, by, bz);
   uint32_t h = hash64(key) & m.hmask;
   for (uint32_t probe = 0; probe <= m.hmask; ++probe) {
     unsigned long long k = __ldcg(&m.hkeys[h]);
-    if (k == key) return;
+    if (k == key) return h;
     if (k == kEmptyKey) {
       k = atomicCAS(&m.hkeys[h], kEmptyKey, key);
       if (k == kEmptyKey) {
@@ -200,19 +212,20 @@ __device__ __forceinline__ void block_insert(const DevMap& m, int bx, int by, in
         if (slot >= m.cap_blocks) {
           m.hvals[h] = kInvalid;
           atomicOr(&m.ctr->error, kErrPoolFull);
-          return;
+          return h;
         }
         m.hvals[h] = slot;
         m.bcoord[slot] = make_int3(bx, by, bz);
         const uint32_t i = atomicAdd(&m.ctr->nnew, 1u);
         m.newblk[i] = slot;
-        return;
+        return h;
       }
-      if (k == key) return;
+      if (k == key) return h;
     }
     h = (h + 1) & m.hmask;
   }
   atomicOr(&m.ctr->error, kErrHashFull);
+  return kInvalid;
 }
 
 // ---------------------------------------------------------------------------------------

@@ -98,6 +98,25 @@ class ScanPool:
         return self.points[spec.kind][spec.seq][f], self.poses[spec.kind][spec.seq][f], self.queries[spec.kind][spec.seq][f]
 
 
+def scratch_for_pool(pool: ScanPool, capacity: Dict[str, int], margin: float = 1.1) -> Dict[str, int]:
+    """Scratch blocks per scan kind: the most blocks any scan of the pool enters, times
+    `margin`. The rays of a scan enter the same blocks whatever the map already holds (every
+    block a ray crosses is allocated), so one pass over the pool's scans measures it."""
+    out = {}
+    for kind in pool.kinds:
+        p = pool.params[kind]
+        pts = max(int(t.shape[0]) for seq in pool.points[kind] for t in seq)
+        need = 0
+        for seq, poses in zip(pool.points[kind], pool.poses[kind]):
+            m = vbx.Map.from_scene_params(p, block_capacity=capacity.get(kind, 0), max_points=pts)
+            for x, T in zip(seq, poses):
+                m.integrate_scan(x, T)
+                need = max(need, int(m.stats()["touched_blocks"]))
+            m.close()
+        out[kind] = int(need * margin) + 1
+    return out
+
+
 @dataclasses.dataclass
 class _Active:
     spec: SessionSpec
@@ -114,6 +133,7 @@ class MapServer:
         hbm_budget: float = 120e9,
         capacity: Optional[Dict[str, int]] = None,
         use_graph: bool = True,
+        scratch: Optional[Dict[str, int]] = None,
     ):
         import torch
 
@@ -121,6 +141,8 @@ class MapServer:
         self.slots = slots
         self.budget = float(hbm_budget)
         self.capacity = capacity or {}
+        # blocks one scan of a kind may enter (its per-voxel sums live there); 0: the pool size
+        self.scratch = scratch or {}
         self.use_graph = use_graph
         self.used = 0
         self.peak = 0
@@ -142,19 +164,21 @@ class MapServer:
     def _new_map(self, kind: str) -> vbx.Map:
         p = self.pool.params[kind]
         pts = max(int(t.shape[0]) for seq in self.pool.points[kind] for t in seq)
-        return vbx.Map.from_scene_params(p, block_capacity=self.capacity.get(kind, 0), max_points=pts)
+        return vbx.Map.from_scene_params(
+            p, block_capacity=self.capacity.get(kind, 0), max_points=pts, scratch_blocks=self.scratch.get(kind, 0)
+        )
 
-    def _map_bytes(self, kind: str) -> int:
+    def map_bytes(self, kind: str) -> int:
         p = self.pool.params[kind]
         pts = max(int(t.shape[0]) for seq in self.pool.points[kind] for t in seq)
-        return vbx.map_bytes(int(p["voxels_per_block"]), self.capacity.get(kind, 0), pts)
+        return vbx.map_bytes(int(p["voxels_per_block"]), self.capacity.get(kind, 0), pts, self.scratch.get(kind, 0))
 
     def _acquire(self, kind: str) -> Optional[vbx.Map]:
         if self.free[kind]:
             m = self.free[kind].pop()
             m.reset()
             return m
-        need = self._map_bytes(kind)
+        need = self.map_bytes(kind)
         for other in list(self.free):
             while other != kind and self.free[other] and self.used + need > self.budget:
                 m = self.free[other].pop()

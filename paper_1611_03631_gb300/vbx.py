@@ -44,6 +44,7 @@ class vbx_map_options(ctypes.Structure):
         ("grouped", ctypes.c_int),
         ("block_capacity", ctypes.c_int64),
         ("max_points", ctypes.c_int64),
+        ("scratch_blocks", ctypes.c_int64),
     ]
 
 
@@ -70,6 +71,7 @@ class vbx_stats(ctypes.Structure):
             "esdf_classify_ns",
             "esdf_raise_ns",
             "esdf_lower_ns",
+            "touched_blocks",
         )
     ]
 
@@ -202,6 +204,7 @@ class Map:
         grouped: bool = True,
         block_capacity: int = 0,
         max_points: int = 0,
+        scratch_blocks: int = 0,
     ):
         import torch
 
@@ -218,6 +221,7 @@ class Map:
         o.grouped = 1 if grouped else 0
         o.block_capacity = int(block_capacity)
         o.max_points = int(max_points)
+        o.scratch_blocks = int(scratch_blocks)
         h = ctypes.c_void_p()
         _check(self._lib.vbx_create_map(voxel_size, voxels_per_block, truncation, max_esdf_dist, ctypes.byref(o), ctypes.byref(h)))
         self._h = h
@@ -357,13 +361,14 @@ class Map:
         _check(self._lib.vbx_reset_map(self._h, _stream_ptr(stream)))
 
 
-def map_bytes(voxels_per_block: int, block_capacity: int = 0, max_points: int = 0) -> int:
+def map_bytes(voxels_per_block: int, block_capacity: int = 0, max_points: int = 0, scratch_blocks: int = 0) -> int:
     """Device bytes of a map with these sizes (vbx_map_bytes)."""
     lib = load_library()
     o = vbx_map_options()
     _check(lib.vbx_default_options(ctypes.byref(o)))
     o.block_capacity = int(block_capacity)
     o.max_points = int(max_points)
+    o.scratch_blocks = int(scratch_blocks)
     n = ctypes.c_int64()
     _check(lib.vbx_map_bytes(int(voxels_per_block), ctypes.byref(o), ctypes.byref(n)))
     return int(n.value)

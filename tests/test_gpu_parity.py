@@ -259,6 +259,44 @@ def test_pool_exhaustion_reports_out_of_memory(vbx):
     assert g.num_blocks() == 64
 
 
+def test_scratch_overflow_rejects_the_whole_scan(vbx):
+    """A scan whose rays enter more blocks than scratch_blocks is not integrated at all: the
+    call reports out-of-memory and no voxel is observed (its blocks stay allocated, empty)."""
+    s = scenes.plane_sphere(frames=1)
+    g = vbx.Map.from_scene_params(s.params, scratch_blocks=64)
+    g.integrate_scan(_dev(s.points[0]), s.poses[0])
+    with pytest.raises(vbx.VbxError) as ei:
+        g.sync()
+    assert ei.value.status == 2
+    st = g.stats()
+    assert st["touched_blocks"] > 64 and st["updated"] == 0 and st["records"] == 0
+    ex = g.export()
+    assert not (ex["W"] > 0).any()
+    g.update_esdf()
+    g.sync()
+    assert g.stats()["esdf_in"] == 0
+
+
+def test_tight_scratch_equals_default(vbx):
+    """Scratch sized exactly to the largest scan's touched blocks gives bit-identical maps."""
+    s = scenes.room(frames=3, width=160, height=120, fx=131.25, fy=131.25)
+    a = vbx.Map.from_scene_params(s.params)
+    need = 0
+    for i in range(len(s)):
+        a.integrate_scan(_dev(s.points[i]), s.poses[i])
+        a.update_esdf()
+        need = max(need, a.stats()["touched_blocks"])
+    b = vbx.Map.from_scene_params(s.params, scratch_blocks=need)
+    for i in range(len(s)):
+        b.integrate_scan(_dev(s.points[i]), s.poses[i])
+        b.update_esdf()
+    b.sync()
+    ea, eb = a.export(), b.export()
+    for k in ("keys", "D", "W", "d", "flags"):
+        assert np.array_equal(ea[k], eb[k]), k
+    assert vbx.map_bytes(16, 4096, 1 << 16, scratch_blocks=need) < vbx.map_bytes(16, 4096, 1 << 16)
+
+
 def test_invalid_arguments(vbx):
     with pytest.raises(vbx.VbxError):
         vbx.Map(0.1, 7, 0.3, 2.0)

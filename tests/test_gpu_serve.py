@@ -31,9 +31,16 @@ def test_sessions_alone_equal_sessions_in_the_mix(mods):
     }
     pool = serve.ScanPool(sets, n_queries=600)
     cap = {"room": 1024, "ps": 16384}
+    # served maps hold scratch for the largest scan of their kind only; the maps run alone below
+    # keep the default (whole-pool) scratch
+    scratch = serve.scratch_for_pool(pool, cap, margin=1.0)
+    assert all(0 < scratch[k] < cap[k] for k in sets)
     # a budget for about two maps at a time, three slots: sessions wait, batches change every step
-    one = max(vbx.map_bytes(sets[k][0].params["voxels_per_block"], cap[k], max(p.shape[0] for p in sets[k][0].points)) for k in sets)
-    srv = serve.MapServer(pool, slots=3, hbm_budget=2.5 * one, capacity=cap, use_graph=True)
+    one = max(
+        vbx.map_bytes(sets[k][0].params["voxels_per_block"], cap[k], max(p.shape[0] for p in sets[k][0].points), scratch[k])
+        for k in sets
+    )
+    srv = serve.MapServer(pool, slots=3, hbm_budget=2.5 * one, capacity=cap, use_graph=True, scratch=scratch)
     # fast arrivals (the GPU outpaces 10-30 Hz robots) so that sessions share steps
     specs = serve.poisson_sessions(
         7, ["room", "ps"], {"room": 2, "ps": 2}, {"room": 4, "ps": 4}, 2000.0, 3, rate_range=(500.0, 1000.0), seed=3
