@@ -106,7 +106,9 @@ SERVE_BUDGET = 120e9
 SERVE_CAPACITY = {"room": 2048, "lidar_terrain": 1 << 16}
 SERVE_ARRIVALS = 32.0  # sessions per second
 SERVE_SATURATED_ARRIVALS = 1024.0
-SERVE_C1_ARRIVALS = 64.0
+SERVE_C1_ARRIVALS = 256.0  # enough concurrent robots to offer more scans/s than the plain path serves
+SERVE_C1_SESSIONS = 768
+SERVE_C1_SLOTS = 256
 SERVE_C1_CAPACITY = {"plane_sphere": 45056}  # the 10-frame circle allocates about 42.3k blocks of 8^3
 
 
@@ -238,18 +240,111 @@ def run_batched(args, vbx, torch, dev):
     }
 
 
+def run_batched_plane_sphere(args, vbx, torch, dev, n_maps: int = 64):
+    """64 maps of the plane+sphere scene (4 noise seeds, 16 frame offsets each), one scan per
+    map per step followed by a 10k-point query batch per map: the plain per-scan path (one map
+    at a time) against the batched form (CUDA-graph replay). A scan's latency in the batched
+    form is the step's duration."""
+    from paper_1611_03631_gb300 import scenes
+
+    seqs = [scenes.plane_sphere(seed=60 + i) for i in range(4)]
+    F = len(seqs[0].points)
+    pts = [[torch.from_numpy(p).to(dev) for p in sq.points] for sq in seqs]
+    qs = [
+        [torch.from_numpy(scenes.random_queries(sq, N_QUERIES, radius=2.0, seed=300 + 31 * j + f, scan_index=f)).to(dev) for f in range(F)]
+        for j, sq in enumerate(seqs)
+    ]
+    cap = SERVE_C1_CAPACITY["plane_sphere"]
+    maps = [vbx.Map.from_scene_params(seqs[0].params, block_capacity=cap, max_points=64 * 48) for _ in range(n_maps)]
+    outs = [
+        (
+            torch.empty(N_QUERIES, dtype=torch.float32, device=dev),
+            torch.empty((N_QUERIES, 3), dtype=torch.float32, device=dev),
+            torch.empty(N_QUERIES, dtype=torch.uint8, device=dev),
+        )
+        for _ in range(n_maps)
+    ]
+    stream = torch.cuda.current_stream()
+
+    def frame(i, k):
+        j, f = i % 4, (i // 4 + k) % F
+        return pts[j][f], seqs[j].poses[f], qs[j][f]
+
+    def plain_step(k):
+        for i, m in enumerate(maps):
+            p, T, q = frame(i, k)
+            m.integrate_scan(p, T)
+            m.update_esdf()
+            m.query(q, out=outs[i])
+
+    def timed(fn, k):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn(k)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    for k in range(args.warmup):
+        plain_step(k)
+    plain_ms = [timed(plain_step, args.warmup + k) for k in range(args.steps)]
+    for m in maps:
+        m.sync()
+        m.reset()
+    batch = vbx.MapBatch(maps, max_queries=N_QUERIES)
+    fm = vbx.STEP_INTEGRATE | vbx.STEP_ESDF
+    report = batch.autotune([frame(i, 0)[0] for i in range(n_maps)], [frame(i, 0)[1] for i in range(n_maps)], flags=fm)
+    for m in maps:
+        m.reset()
+
+    def batch_step(k):
+        fr = [frame(i, k) for i in range(n_maps)]
+        batch.step([x[0] for x in fr], [x[1] for x in fr], flags=fm | vbx.STEP_GRAPH)
+        batch.step(queries=[(x[2],) + outs[i] for i, x in enumerate(fr)], flags=vbx.STEP_QUERY | vbx.STEP_GRAPH)
+
+    for k in range(args.warmup):
+        batch_step(k)
+    batch.sync()
+    step_ms = [timed(batch_step, args.warmup + k) for k in range(args.steps)]
+    batch.sync()
+    # per-kernel device time of the step: a few direct (non-graph) steps with events
+    batch.set_profiling(True)
+    prof = 3
+    for k in range(prof):
+        fr = [frame(i, k) for i in range(n_maps)]
+        batch.step([x[0] for x in fr], [x[1] for x in fr], flags=fm)
+        batch.step(queries=[(x[2],) + outs[i] for i, x in enumerate(fr)], flags=vbx.STEP_QUERY)
+    kt = batch.kernel_times()
+    batch.close()
+    for m in maps:
+        m.close()
+    return {
+        "workload": f"{n_maps} maps of the plane+sphere scene (64x48 depth, v=0.1 m, 8^3 blocks), one scan and {N_QUERIES // 1000}k "
+        "distance+gradient queries per map per step",
+        "value": n_maps * args.steps / (sum(step_ms) / 1e3),
+        "unit": "scans/s",
+        "plain_value": n_maps * args.steps / (sum(plain_ms) / 1e3),
+        "plain_scan_ms_mean": float(np.mean(plain_ms)) / n_maps,
+        "step_ms_p50": float(np.percentile(step_ms, 50)),
+        "step_ms_p99": float(np.percentile(step_ms, 99)),
+        "autotune": report,
+        "kernels_ms_per_step": {k: v["ms"] / prof for k, v in kt.items() if v["launches"]},
+    }
+
+
 def _serve_c1_sets():
     from paper_1611_03631_gb300 import scenes
 
     return {"plane_sphere": [scenes.plane_sphere(seed=60 + i) for i in range(4)]}
 
 
-def _serve_once(serve, sets, arrivals: float, capacity):
+def _serve_once(serve, sets, arrivals: float, capacity, slots: int = SERVE_SLOTS, sessions: int = SERVE_SESSIONS):
     pool = serve.ScanPool(sets, n_queries=N_QUERIES)
     scratch = serve.scratch_for_pool(pool, capacity)
-    srv = serve.MapServer(pool, slots=SERVE_SLOTS, hbm_budget=SERVE_BUDGET, capacity=capacity, use_graph=True, scratch=scratch)
+    srv = serve.MapServer(pool, slots=slots, hbm_budget=SERVE_BUDGET, capacity=capacity, use_graph=True, scratch=scratch)
     specs = serve.poisson_sessions(
-        SERVE_SESSIONS,
+        sessions,
         list(sets),
         {k: len(v) for k, v in sets.items()},
         {k: pool.frames(k) for k in sets},
@@ -282,10 +377,11 @@ def run_served(args, vbx, torch):
     sat["workload"] = f"as above, sessions arriving at {SERVE_SATURATED_ARRIVALS:.0f}/s (more scans offered than the GPU serves)"
     res["saturated"] = sat
     c1_sets = _serve_c1_sets()
-    c1 = _serve_once(serve, c1_sets, SERVE_C1_ARRIVALS, SERVE_C1_CAPACITY)
+    c1 = _serve_once(serve, c1_sets, SERVE_C1_ARRIVALS, SERVE_C1_CAPACITY, slots=SERVE_C1_SLOTS, sessions=SERVE_C1_SESSIONS)
     c1["workload"] = (
-        f"{SERVE_SESSIONS} sessions of the plane+sphere scene (64x48 depth, v=0.1 m, 8^3 blocks) arriving at "
-        f"{SERVE_C1_ARRIVALS:.0f}/s, " + common
+        f"{SERVE_C1_SESSIONS} sessions of the plane+sphere scene (64x48 depth, v=0.1 m, 8^3 blocks) arriving at "
+        f"{SERVE_C1_ARRIVALS:.0f}/s, 16 scans each at U(10,30) Hz, each scan followed by {N_QUERIES // 1000}k "
+        f"distance+gradient queries within 2 m of the sensor; {SERVE_C1_SLOTS} batch slots, {SERVE_BUDGET/1e9:.0f} GB map budget"
     )
     c1["plain"] = _plain_plane_sphere(vbx, torch, c1_sets["plane_sphere"][0])
     res["plane_sphere"] = c1
@@ -307,6 +403,7 @@ def _plain_plane_sphere(vbx, torch, s, steps: int = 40, warmup: int = 3):
     )
     m = vbx.Map.from_scene_params(s.params, block_capacity=SERVE_C1_CAPACITY["plane_sphere"], max_points=max(int(p.shape[0]) for p in pts))
     ms = []
+    stats = {"rays": 0, "records": 0, "updated": 0, "esdf_pops": 0, "esdf_rounds": 0}
     for k in range(warmup + steps):
         i = k % F
         e0 = torch.cuda.Event(enable_timing=True)
@@ -319,8 +416,29 @@ def _plain_plane_sphere(vbx, torch, s, steps: int = 40, warmup: int = 3):
         e1.synchronize()
         if k >= warmup:
             ms.append(e0.elapsed_time(e1))
+            st = m.stats()
+            stats["rays"] += st["rays"]
+            stats["records"] += st["records"]
+            stats["updated"] += st["updated"]
+            stats["esdf_pops"] += st["raise_pops"] + st["lower_pops"]
+            stats["esdf_rounds"] += st["raise_rounds"] + st["lower_rounds"]
+    # per-kernel times of the same scans, in a second pass with the library's profiling events
+    m.set_profiling(True)
+    m.reset_kernel_times()
+    for k in range(steps):
+        i = k % F
+        m.integrate_scan(pts[i], s.poses[i])
+        m.update_esdf()
+        m.query(qs[i], out=out)
+    kt = m.kernel_times()
     m.close()
-    return dict(scans_per_s=len(ms) / (sum(ms) / 1e3), p50_ms=float(np.percentile(ms, 50)), p99_ms=float(np.percentile(ms, 99)))
+    return dict(
+        scans_per_s=len(ms) / (sum(ms) / 1e3),
+        p50_ms=float(np.percentile(ms, 50)),
+        p99_ms=float(np.percentile(ms, 99)),
+        per_scan={k: v / steps for k, v in stats.items()},
+        kernels_ms_per_scan={k: v["ms"] / steps for k, v in kt.items() if v["launches"]},
+    )
 
 
 def _queries(s, frames: int):
@@ -490,9 +608,9 @@ def run_gpu(args):
     dist, rank, ws = _dist_init()
     local = int(os.environ.get("LOCAL_RANK", "0"))
     # scene generation uses spawned worker processes: do it before the first CUDA call
-    if not args.no_batched:
+    if not args.no_batched and not args.only_batched_plane_sphere:
         _batch_sets()
-    if not args.no_served:
+    if not args.no_served and not (args.only_batched or args.only_batched_plane_sphere):
         _serve_sets()
     torch.cuda.set_device(local)
     import __graft_entry__
@@ -503,6 +621,10 @@ def run_gpu(args):
     if args.only_batched:
         dev = torch.device("cuda", local)
         print(json.dumps({"batched": run_batched(args, vbx, torch, dev)}), flush=True)
+        return 0
+    if args.only_batched_plane_sphere:
+        dev = torch.device("cuda", local)
+        print(json.dumps({"batched_plane_sphere": run_batched_plane_sphere(args, vbx, torch, dev, n_maps=args.batch_maps)}), flush=True)
         return 0
 
     F = 30
@@ -656,9 +778,10 @@ def run_gpu(args):
         e2e_total = float(t.item())
     e2e_value = ws * args.steps / (e2e_total / 1000.0)
 
-    batched = served = None
+    batched = batched_c1 = served = None
     if not args.no_batched:
         batched = run_batched(args, vbx, torch, dev)
+        batched_c1 = run_batched_plane_sphere(args, vbx, torch, dev)
     if not args.no_served:
         served = run_served(args, vbx, torch)
     if rank != 0:
@@ -701,6 +824,7 @@ def run_gpu(args):
         "gpu_launches": int(gpu_launches),
         "clocks": clk,
         "batched": batched,
+        "batched_plane_sphere": batched_c1,
         "served": served,
     }
     print(json.dumps(line), flush=True)
@@ -720,6 +844,9 @@ def main():
     ap.add_argument("--no-served", action="store_true", help="skip the served-sessions section")
     ap.add_argument("--batch-maps", type=int, default=64, help="maps of the batched section")
     ap.add_argument("--only-batched", action="store_true", help="run the batched section alone (profiling)")
+    ap.add_argument(
+        "--only-batched-plane-sphere", action="store_true", help="run the batched plane+sphere section alone with --batch-maps maps (profiling)"
+    )
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -57,7 +57,7 @@ typedef struct {
   int64_t block_capacity; /* blocks in the voxel pool (device memory budget); 0: 2^25/B^3  */
   int64_t max_points;     /* initial per-scan point capacity; grows on demand; 0: 1<<20     */
   int64_t scratch_blocks; /* blocks one scan may enter (each holds the scan's per-voxel sums,
-                             36 B per voxel); 0 or more than block_capacity: block_capacity.
+                             33 B per voxel); 0 or more than block_capacity: block_capacity.
                              A scan that enters more blocks is not integrated at all and its
                              synchronising call reports VBX_ERR_OUT_OF_MEMORY               */
 } vbx_map_options;
@@ -69,7 +69,7 @@ vbx_status vbx_default_options(vbx_map_options* opt);
  * (4, 8 or 16), truncation distance delta (>= v) and ESDF maximum distance d_max (> 0).
  * Sec. III: layers of fixed-size blocks indexed by block position through a hash table.
  * opt may be NULL (defaults). On success *out holds the new map. Allocates device memory
- * on the current device: about 26 bytes per pool voxel, 36 bytes per scratch voxel
+ * on the current device: about 26 bytes per pool voxel, 33 bytes per scratch voxel
  * (scratch_blocks x B^3) and the per-scan point buffers (vbx_map_bytes gives the total). */
 vbx_status vbx_create_map(float voxel_size, int voxels_per_block, float truncation, float max_esdf_dist,
                           const vbx_map_options* opt, vbx_map_t* out);

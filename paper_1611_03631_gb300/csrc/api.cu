@@ -217,7 +217,7 @@ vbx_status ensure_scratch(vbx_map_t m, int64_t n, cudaStream_t s) {
 cudaError_t next_scan_epoch(vbx_map_t m, cudaStream_t s, unsigned* ep) {
   if (m->scan_epoch == 0xffffffffu) {
     cudaError_t e = cudaMemsetAsync(m->d.hclaim, 0, ((size_t)m->d.hmask + 1) * 4, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(m->d.sepoch, 0, (size_t)m->d.cap_blocks * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->d.sinfo, 0, (size_t)m->d.cap_blocks * 8, s);
     if (e != cudaSuccess) return e;
     m->scan_epoch = 0;
   }
@@ -316,8 +316,7 @@ vbx_status vbx_create_map(float voxel_size, int voxels_per_block, float truncati
   VBX_ALLOC(d.hclaim, H, 0);
   VBX_ALLOC(d.bcoord, (size_t)cap, 0);
   VBX_ALLOC(d.nbr, (size_t)cap * 27, 0xff);
-  VBX_ALLOC(d.sepoch, (size_t)cap, 0);
-  VBX_ALLOC(d.sidx, (size_t)cap, 0);
+  VBX_ALLOC(d.sinfo, (size_t)cap, 0);
   VBX_ALLOC(d.tsdf, V, 0);
   VBX_ALLOC(d.slist_h, (size_t)scr, 0);
   VBX_ALLOC(d.slist, (size_t)scr, 0);
@@ -1041,9 +1040,9 @@ vbx_status vbx_map_bytes(int B, const vbx_map_options* opt_in, int64_t* out) {
   const uint64_t scr = opt.scratch_blocks > 0 ? std::min<uint64_t>((uint64_t)opt.scratch_blocks, cap) : cap;
   uint64_t bytes = 0;
   bytes += H * (8 + 4 + 4);                               // block hash, scratch claims
-  bytes += cap * (12 + 27 * 4 + 4 + 4 + 4);               // block coords, links, scratch index/epoch, new list
+  bytes += cap * (12 + 27 * 4 + 8 + 4);                   // block coords, links, scratch index/epoch, new list
   bytes += V * (8 + 8 + 1 + 4 + 4);                       // tsdf, esdf, flags, updated and dirty lists
-  bytes += scr * (4 + 4) + scr * B3 * (32 + 4);           // scratch blocks: lists, sums, touch flags
+  bytes += scr * (4 + 4) + scr * B3 * (32 + 1);           // scratch blocks: lists, sums, touch flags
   bytes += 4 * (V / 32) * 4;                              // frontier bitmasks
   bytes += tiles * (2 * 4 + 4 * 8);                       // tile stamps, active lists
   bytes += entries * sizeof(vbx::GroupEntry) + pts * (4 + 16);  // per-scan scratch
@@ -1082,10 +1081,10 @@ vbx_status vbx_reset_map(vbx_map_t m, void* stream) {
       {d.nbr, nb * 27 * 4, 0xff},
       {d.hclaim, ((size_t)d.hmask + 1) * 4, 0},
       {d.bcoord, nb * 12, 0},
-      {d.sepoch, nb * 4, 0},
+      {d.sinfo, nb * 8, 0},
       {d.tsdf, V * 8, 0},
       {d.sacc, SV * 32, 0},
-      {d.stouch, SV * 4, 0},
+      {d.stouch, SV, 0},
       {d.esdf, V * 8, 0},
       {d.vflags, V, 0},
       {d.rbits0, V / 8, 0},

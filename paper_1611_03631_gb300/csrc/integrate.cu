@@ -17,6 +17,7 @@
 // explicitly rounded intrinsics, so the compiler cannot contract or reorder it.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -34,6 +35,63 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr unsigned kFull = 0xffffffffu;
+// Long rays are traversed in segments spread over the lanes of a warp (DdaSeg): a voxel
+// segment ends at every kVoxSeg-th crossing of the ray's dominant axis, a block segment at
+// every kBlkSeg-th.
+#ifndef VBX_VOX_SEG
+#define VBX_VOX_SEG 16
+#endif
+#ifndef VBX_SEG_FILL
+#define VBX_SEG_FILL 64
+#endif
+#ifndef VBX_RAYS_MIN_CTAS
+#define VBX_RAYS_MIN_CTAS 4
+#endif
+constexpr int kVoxSeg = VBX_VOX_SEG;
+constexpr int kBlkSeg = 4;
+constexpr unsigned kSegFill = VBX_SEG_FILL;  // segments per 32 lanes aimed at by a warp task
+
+// Segment bookkeeping of the 32 rays of a warp: lane `lane` holds nseg segments of its ray.
+// Returns the warp's total and this lane's first segment index.
+__device__ __forceinline__ int warp_segments(int nseg, int lane, int* first) {
+  int incl = nseg;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int up = __shfl_up_sync(kFull, incl, off);
+    if (lane >= off) incl += up;
+  }
+  *first = incl - nseg;
+  return __shfl_sync(kFull, incl, 31);
+}
+
+// Whether the rays of a launch are cut into segments: only when 32-ray warp tasks would not
+// keep every resident warp busy several times over (then the longest ray of a warp sets the
+// kernel's duration); with plenty of rays each lane walks its whole ray.
+__device__ __forceinline__ bool split_rays(unsigned n, unsigned slots) {
+  return (unsigned long long)n < 32ull * 4ull * slots;
+}
+
+// Rays per warp task when rays are split (a power of two in [1, 32]): at most n / slots, so
+// that n rays keep `slots` resident warps busy, and (when the segment total sg is known) about
+// as many rays as give two segments per lane.
+__device__ __forceinline__ unsigned rays_per_task(unsigned n, unsigned long long sg, unsigned slots) {
+  unsigned R = 32;
+  while (R > 1 && (unsigned long long)n < (unsigned long long)R * slots) R >>= 1;
+  if (sg > 0)
+    while (R > 1 && (unsigned long long)R * sg > (unsigned long long)kSegFill * n) R >>= 1;
+  return R;
+}
+
+// Lane whose ray holds warp segment t: the last lane whose first segment index is <= t.
+__device__ __forceinline__ int segment_owner(int first, int t) {
+  int own = 0;
+#pragma unroll
+  for (int step = 16; step > 0; step >>= 1) {
+    const int e = __shfl_sync(kFull, first, own + step);
+    if (e <= t) own += step;
+  }
+  return own;
+}
 
 // A1 filter and per-point weight. Returns false for a dropped point.
 __device__ __forceinline__ bool accept_point(const DevMap& m, float x, float y, float z, float* w) {
@@ -134,6 +192,7 @@ __global__ void __launch_bounds__(kThreads) k_reset_counters(Batch b) {
     c->nupdated = 0;
     c->npoints_valid = 0;
     c->ntouched = 0;
+    c->nvseg = 0;
     c->nrecords = 0;
     c->raise_rounds = 0;
     c->lower_rounds = 0;
@@ -277,56 +336,96 @@ __device__ __forceinline__ unsigned scratch_blocks(const DevMap& m) {
   return n <= m.scr_cap ? n : 0u;
 }
 
-__global__ void __launch_bounds__(kThreads) k_group_rays(Batch b) {
+__global__ void __launch_bounds__(kThreads) k_group_rays(Batch b, unsigned warp_slots) {
   __shared__ unsigned pfx[kMaxBatch + 1];
+  __shared__ long long sh_se[kWarps][32][6];  // each lane's ray ends S, E (fixed point)
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int nm = nmaps_of(b);
-  const unsigned total = cta_prefix(pfx, b, [&](unsigned mi) { return __ldcg(&map_of(b, mi).ctr->ngroups); });
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
-    const unsigned mi = map_index(pfx, nm, i);
-    const unsigned gi = i - pfx[mi];
+  // warp tasks of R rays of one map; their block-traversal segments are spread over the lanes
+  const unsigned nall = cta_prefix(pfx, b, [&](unsigned mi) { return __ldcg(&map_of(b, mi).ctr->ngroups); });
+  const bool split = split_rays(nall, warp_slots);
+  const unsigned R = split ? rays_per_task(nall, 0, warp_slots) : 32u;
+  const int K = split ? kBlkSeg : (1 << 30);
+  __syncthreads();
+  const unsigned ntask = cta_prefix(pfx, b, [&](unsigned mi) { return (__ldcg(&map_of(b, mi).ctr->ngroups) + R - 1) / R; });
+  for (unsigned task = blockIdx.x * kWarps + wid; task < ntask; task += gridDim.x * kWarps) {
+    const unsigned mi = map_index(pfx, nm, task);
     const DevMap& m = map_of(b, mi);
     const ScanDesc& sd = scan_of(b, mi);
-    const float s[3] = {sd.T[3], sd.T[7], sd.T[11]};
-    float pbar[3];
-    if (m.grouped) {
-      const uint32_t h = m.glist[gi];
-      GroupEntry e = m.gtab[h];
-      GroupEntry z;  // reset the entry for the next scan
-      z.key = kEmptyKey;
-      z.sw = 0;
-      z.swo_lo[0] = z.swo_lo[1] = z.swo_lo[2] = 0;
-      z.swo_hi[0] = z.swo_hi[1] = z.swo_hi[2] = 0;
-      z.n = 0;
-      m.gtab[h] = z;
-      const int3 k = unpack_key(e.key);
-      const int kk[3] = {k.x, k.y, k.z};
-      const unsigned long long half = e.sw >> 1;
-      for (int a = 0; a < 3; ++a) {
-        const unsigned long long lo = e.swo_lo[a] + half;
-        const unsigned long long hi = (unsigned long long)e.swo_hi[a] + (lo < half ? 1ull : 0ull);
-        const unsigned mo = div128_small(lo, hi, e.sw);
-        pbar[a] = __fmul_rn(__fadd_rn((float)kk[a], __fmul_rn((float)mo, 1.0f / 65536.0f)), m.v);
+    const unsigned gi = (task - pfx[mi]) * R + lane;
+    int nseg = 0, nvseg = 0;
+    if (lane < (int)R && gi < __ldcg(&m.ctr->ngroups)) {
+      const float s[3] = {sd.T[3], sd.T[7], sd.T[11]};
+      float pbar[3];
+      if (m.grouped) {
+        const uint32_t h = m.glist[gi];
+        GroupEntry e = m.gtab[h];
+        GroupEntry z;  // reset the entry for the next scan
+        z.key = kEmptyKey;
+        z.sw = 0;
+        z.swo_lo[0] = z.swo_lo[1] = z.swo_lo[2] = 0;
+        z.swo_hi[0] = z.swo_hi[1] = z.swo_hi[2] = 0;
+        z.n = 0;
+        m.gtab[h] = z;
+        const int3 k = unpack_key(e.key);
+        const int kk[3] = {k.x, k.y, k.z};
+        const unsigned long long half = e.sw >> 1;
+        for (int a = 0; a < 3; ++a) {
+          const unsigned long long lo = e.swo_lo[a] + half;
+          const unsigned long long hi = (unsigned long long)e.swo_hi[a] + (lo < half ? 1ull : 0ull);
+          const unsigned mo = div128_small(lo, hi, e.sw);
+          pbar[a] = __fmul_rn(__fadd_rn((float)kk[a], __fmul_rn((float)mo, 1.0f / 65536.0f)), m.v);
+        }
+        const float Wg = m.weighting == 0 ? __uint2float_rn(e.n) : __fmul_rn(__ull2float_rn(e.sw), 1.0f / 1048576.0f);
+        m.rays[gi] = make_float4(pbar[0], pbar[1], pbar[2], Wg);
+      } else {
+        const float4 r = m.rays[gi];
+        pbar[0] = r.x;
+        pbar[1] = r.y;
+        pbar[2] = r.z;
       }
-      const float Wg = m.weighting == 0 ? __uint2float_rn(e.n) : __fmul_rn(__ull2float_rn(e.sw), 1.0f / 1048576.0f);
-      m.rays[gi] = make_float4(pbar[0], pbar[1], pbar[2], Wg);
-    } else {
-      const float4 r = m.rays[gi];
-      pbar[0] = r.x;
-      pbar[1] = r.y;
-      pbar[2] = r.z;
+      RayGeom g;
+      if (ray_setup(pbar, s, m.v, m.delta, &g)) {
+        // block-level traversal: cells of 65536*B fixed-point units; same crossing order as
+        // the voxel traversal, so it visits exactly the blocks of the traversed voxels
+        DdaSeg sg;
+        sg.init(g.S, g.E, 16 + m.blog);
+        nseg = sg.segments(K);
+        DdaSeg sv;  // segments of the voxel traversal (sizes the next kernel's warp tasks)
+        sv.init(g.S, g.E, 16);
+        nvseg = sv.segments(kVoxSeg);
+        for (int a = 0; a < 3; ++a) {
+          sh_se[wid][lane][a] = g.S[a];
+          sh_se[wid][lane][3 + a] = g.E[a];
+        }
+      }
     }
-    RayGeom g;
-    if (!ray_setup(pbar, s, m.v, m.delta, &g)) continue;
-    // block-level traversal: cells of 65536*B fixed-point units; same crossing order as the
-    // voxel traversal, so it visits exactly the blocks of the traversed voxels
-    Dda dda;
-    dda.init(g.S, g.E, 16 + m.blog);
+    int vs = nvseg;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) vs += __shfl_xor_sync(kFull, vs, off);
+    if (lane == 0 && vs) atomicAdd(&m.ctr->nvseg, (unsigned)vs);
+    __syncwarp();
+    int first = 0;
+    const int tot = warp_segments(nseg, lane, &first);
     const unsigned ep = sd.epoch;
-    claim_scratch(m, block_insert(m, dda.cx, dda.cy, dda.cz), ep);
-    for (int left = dda.steps(); left > 0; --left) {
-      dda.step();
+    for (int t0 = 0; t0 < tot; t0 += 32) {
+      const int t = t0 + lane;
+      const int own = segment_owner(first, t);
+      const int seg = t - __shfl_sync(kFull, first, own);
+      if (t >= tot) continue;
+      DdaSeg sg;
+      sg.init(&sh_se[wid][own][0], &sh_se[wid][own][3], 16 + m.blog);
+      int left = 0;
+      Dda dda = sg.seek(seg, K, &left);
       claim_scratch(m, block_insert(m, dda.cx, dda.cy, dda.cz), ep);
+      for (int dk = 0; left > 0;) {
+        const int ax = dda.step();
+        --left;
+        if (ax == sg.d && ++dk == K) break;
+        claim_scratch(m, block_insert(m, dda.cx, dda.cy, dda.cz), ep);
+      }
     }
+    __syncwarp();
   }
 }
 
@@ -348,10 +447,7 @@ __global__ void __launch_bounds__(kThreads) k_link_blocks(Batch b) {
       const unsigned i = u - nl;
       const uint32_t slot = __ldcg(&m.hvals[m.slist_h[i]]);
       m.slist[i] = slot;
-      if (slot < m.cap_blocks) {
-        m.sidx[slot] = i;
-        m.sepoch[slot] = scan_of(b, mi).epoch;
-      }
+      if (slot < m.cap_blocks) m.sinfo[slot] = ((unsigned long long)scan_of(b, mi).epoch << 32) | i;
       continue;
     }
     const uint32_t p = m.newblk[u / 27u];
@@ -377,33 +473,47 @@ __device__ __forceinline__ void fx_split(float x, long long* hi, long long* lo) 
   *lo = __float2ll_rn(__fmul_rn(__fsub_rn(q, t), kAccLoScale));
 }
 
-// All four parts and the touch flag of scratch voxel sv are fire-and-forget reductions (no
-// returned value), so the ray loop never waits on an atomic.
+// The four parts are fire-and-forget reductions (no returned value), so the ray loop never
+// waits on an atomic; the touch flag is a plain byte store (all writers store 1).
 __device__ __forceinline__ void accumulate(const DevMap& m, uint32_t sv, const long long v[4]) {
   unsigned long long* a = &m.sacc[4 * (size_t)sv];
   for (int j = 0; j < 4; ++j)
     if (v[j] != 0) atomicAdd(&a[j], (unsigned long long)v[j]);
-  atomicOr(&m.stouch[sv], 1u);
+  m.stouch[sv] = 1u;
 }
 
 // Scratch block of pool slot `slot` in scan ep (kInvalid if the scan has none for it).
 __device__ __forceinline__ uint32_t scratch_of(const DevMap& m, uint32_t slot, unsigned ep) {
   if (slot == kInvalid) return kInvalid;
-  return __ldcg(&m.sepoch[slot]) == ep ? __ldcg(&m.sidx[slot]) : kInvalid;
+  const unsigned long long w = __ldcg(&m.sinfo[slot]);
+  return (unsigned)(w >> 32) == ep ? (uint32_t)w : kInvalid;
 }
 
-__global__ void __launch_bounds__(kThreads) k_integrate_rays(Batch b) {
+__global__ void __launch_bounds__(kThreads, VBX_RAYS_MIN_CTAS) k_integrate_rays(Batch b, unsigned warp_slots) {
   __shared__ unsigned pfx[kMaxBatch + 1];
   __shared__ long long sh_v[4][kWarps][32];
+  __shared__ long long sh_se[kWarps][32][6];  // each lane's ray ends S, E (fixed point)
+  __shared__ float sh_pg[kWarps][32][7];      // pbar, pbar - s, group weight
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int nm = nmaps_of(b);
-  // each map's rays are padded to whole warps, so a warp never mixes maps
-  const unsigned total = cta_prefix(pfx, b, [&](unsigned mi) { return (__ldcg(&map_of(b, mi).ctr->ngroups) + 31u) & ~31u; });
-  const unsigned warps_total = gridDim.x * kWarps;
+  // a map whose scan overflowed its scratch integrates nothing
+  auto rays_of = [&](unsigned mi) {
+    const DevMap& m = map_of(b, mi);
+    return __ldcg(&m.ctr->ntouched) <= m.scr_cap ? __ldcg(&m.ctr->ngroups) : 0u;
+  };
+  // warp tasks of R rays of one map; their voxel-traversal segments are spread over the lanes
+  const unsigned nall = cta_prefix(pfx, b, rays_of);
+  __syncthreads();
+  const unsigned sall = cta_prefix(pfx, b, [&](unsigned mi) { return rays_of(mi) ? __ldcg(&map_of(b, mi).ctr->nvseg) : 0u; });
+  const bool split = split_rays(nall, warp_slots);
+  const unsigned R = split ? rays_per_task(nall, sall, warp_slots) : 32u;
+  const int K = split ? kVoxSeg : (1 << 30);
+  __syncthreads();
+  const unsigned ntask = cta_prefix(pfx, b, [&](unsigned mi) { return (rays_of(mi) + R - 1) / R; });
   unsigned long long nrec = 0;
   unsigned rec_map = 0;
-  for (unsigned base = (blockIdx.x * kWarps + wid) * 32u; base < total; base += warps_total * 32u) {
-    const unsigned mi = map_index(pfx, nm, base);
+  for (unsigned task = blockIdx.x * kWarps + wid; task < ntask; task += gridDim.x * kWarps) {
+    const unsigned mi = map_index(pfx, nm, task);
     const DevMap& m = map_of(b, mi);
     const ScanDesc& sd = scan_of(b, mi);
     if (nrec && mi != rec_map) {
@@ -414,111 +524,142 @@ __global__ void __launch_bounds__(kThreads) k_integrate_rays(Batch b) {
     const float s[3] = {sd.T[3], sd.T[7], sd.T[11]};
     const unsigned ep = sd.epoch;
     const int B = m.B, blog = m.blog;
-    const unsigned gi = base - pfx[mi] + lane;
-    bool active = gi < __ldcg(&m.ctr->ngroups) && __ldcg(&m.ctr->ntouched) <= m.scr_cap;
-    RayGeom g;
-    float Wg = 0.0f;
-    Dda dda;
-    int left = 0;
-    int bcx = 0, bcy = 0, bcz = 0;
-    uint32_t slot = kInvalid, sb = kInvalid;
-    if (active) {
+    const unsigned gi = (task - pfx[mi]) * R + lane;
+    int nseg = 0;
+    if (lane < (int)R && gi < rays_of(mi)) {
       const float4 r = m.rays[gi];
       const float pbar[3] = {r.x, r.y, r.z};
-      Wg = r.w;
-      active = ray_setup(pbar, s, m.v, m.delta, &g);
+      RayGeom g;
+      if (ray_setup(pbar, s, m.v, m.delta, &g)) {
+        DdaSeg sg;
+        sg.init(g.S, g.E, 16);
+        nseg = sg.segments(K);
+        for (int a = 0; a < 3; ++a) {
+          sh_se[wid][lane][a] = g.S[a];
+          sh_se[wid][lane][3 + a] = g.E[a];
+          sh_pg[wid][lane][a] = g.p[a];
+          sh_pg[wid][lane][3 + a] = g.g[a];
+        }
+        sh_pg[wid][lane][6] = r.w;
+      }
+    }
+    __syncwarp();
+    int first = 0;
+    const int tot = warp_segments(nseg, lane, &first);
+    for (int t0 = 0; t0 < tot; t0 += 32) {
+      const int t = t0 + lane;
+      const int own = segment_owner(first, t);
+      const int seg = t - __shfl_sync(kFull, first, own);
+      bool active = t < tot;
+      float gp[3] = {0.f, 0.f, 0.f}, gg[3] = {0.f, 0.f, 0.f}, Wg = 0.0f;
+      Dda dda;
+      int dsel = 0, left = 0, dk = 0;
+      int bcx = 0, bcy = 0, bcz = 0;
+      uint32_t slot = kInvalid, sb = kInvalid;
       if (active) {
-        dda.init(g.S, g.E, 16);
-        left = dda.steps();
+        for (int a = 0; a < 3; ++a) {
+          gp[a] = sh_pg[wid][own][a];
+          gg[a] = sh_pg[wid][own][3 + a];
+        }
+        Wg = sh_pg[wid][own][6];
+        DdaSeg sg;
+        sg.init(&sh_se[wid][own][0], &sh_se[wid][own][3], 16);
+        dsel = sg.d;
+        dda = sg.seek(seg, K, &left);
         bcx = dda.cx >> blog;
         bcy = dda.cy >> blog;
         bcz = dda.cz >> blog;
         slot = block_lookup(m, bcx, bcy, bcz);
         sb = scratch_of(m, slot, ep);
       }
-    }
-    while (__any_sync(kFull, active)) {
-      uint32_t vid = kInvalid;
-      long long qv[4] = {0, 0, 0, 0};  // w hi, w*d hi, w lo, w*d lo
-      if (active) {
-        // Eq. (1) at the voxel centre, truncated to [-delta, delta]
-        float dx[3];
-        const int cc[3] = {dda.cx, dda.cy, dda.cz};
+      while (__any_sync(kFull, active)) {
+        uint32_t vid = kInvalid;
+        long long qv[4] = {0, 0, 0, 0};  // w hi, w*d hi, w lo, w*d lo
+        if (active) {
+          // Eq. (1) at the voxel centre, truncated to [-delta, delta]
+          float dx[3];
+          const int cc[3] = {dda.cx, dda.cy, dda.cz};
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const float xc = __fmul_rn(__fadd_rn((float)cc[a], 0.5f), m.v);
-          dx[a] = __fsub_rn(g.p[a], xc);
-        }
-        const float dist = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(dx[0], dx[0]), __fmul_rn(dx[1], dx[1])), __fmul_rn(dx[2], dx[2])));
-        const float dot = __fadd_rn(__fadd_rn(__fmul_rn(dx[0], g.g[0]), __fmul_rn(dx[1], g.g[1])), __fmul_rn(dx[2], g.g[2]));
-        float d = dot >= 0.0f ? dist : -dist;
-        if (d > m.delta) d = m.delta;
-        if (d < -m.delta) d = -m.delta;
-        // Eq. (2) / Eq. (4); the 1/z^2 factor is already in the group weight
-        float w = Wg;
-        if (m.weighting == 1) {
-          if (d <= -m.delta)
-            w = 0.0f;
-          else if (d < -m.eps)
-            w = __fmul_rn(Wg, __fdiv_rn(__fadd_rn(d, m.delta), __fsub_rn(m.delta, m.eps)));
-        }
-        if (w > 0.0f && sb != kInvalid) {
-          const uint32_t l = (uint32_t)((((dda.cz & (B - 1)) << blog | (dda.cy & (B - 1))) << blog) | (dda.cx & (B - 1)));
-          vid = (sb << m.b3log) | l;  // scratch voxel
-          fx_split(w, &qv[0], &qv[2]);
-          fx_split(__fmul_rn(w, d), &qv[1], &qv[3]);
-          ++nrec;
-        }
-        if (left == 0) {
-          active = false;
-        } else {
-          const int ax = dda.step();
-          --left;
-          // block transition: a 6-connected step into the face neighbour
-          int k = -1;
-          if (ax == 0) {
-            const int nb = dda.cx >> blog;
-            if (nb != bcx) {
-              bcx = nb;
-              k = (dda.sx + 1) * 9 + 4;
-            }
-          } else if (ax == 1) {
-            const int nb = dda.cy >> blog;
-            if (nb != bcy) {
-              bcy = nb;
-              k = 9 + (dda.sy + 1) * 3 + 1;
-            }
+          for (int a = 0; a < 3; ++a) {
+            const float xc = __fmul_rn(__fadd_rn((float)cc[a], 0.5f), m.v);
+            dx[a] = __fsub_rn(gp[a], xc);
+          }
+          const float dist = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(dx[0], dx[0]), __fmul_rn(dx[1], dx[1])), __fmul_rn(dx[2], dx[2])));
+          const float dot = __fadd_rn(__fadd_rn(__fmul_rn(dx[0], gg[0]), __fmul_rn(dx[1], gg[1])), __fmul_rn(dx[2], gg[2]));
+          float d = dot >= 0.0f ? dist : -dist;
+          if (d > m.delta) d = m.delta;
+          if (d < -m.delta) d = -m.delta;
+          // Eq. (2) / Eq. (4); the 1/z^2 factor is already in the group weight
+          float w = Wg;
+          if (m.weighting == 1) {
+            if (d <= -m.delta)
+              w = 0.0f;
+            else if (d < -m.eps)
+              w = __fmul_rn(Wg, __fdiv_rn(__fadd_rn(d, m.delta), __fsub_rn(m.delta, m.eps)));
+          }
+          if (w > 0.0f && sb != kInvalid) {
+            const uint32_t l = (uint32_t)((((dda.cz & (B - 1)) << blog | (dda.cy & (B - 1))) << blog) | (dda.cx & (B - 1)));
+            vid = (sb << m.b3log) | l;  // scratch voxel
+            fx_split(w, &qv[0], &qv[2]);
+            fx_split(__fmul_rn(w, d), &qv[1], &qv[3]);
+            ++nrec;
+          }
+          if (left == 0) {
+            active = false;
           } else {
-            const int nb = dda.cz >> blog;
-            if (nb != bcz) {
-              bcz = nb;
-              k = 13 + dda.sz;
+            const int ax = dda.step();
+            --left;
+            if (ax == dsel && ++dk == K) {
+              active = false;  // the next cell starts the ray's next segment
+            } else {
+              // block transition: a 6-connected step into the face neighbour
+              int k = -1;
+              if (ax == 0) {
+                const int nb = dda.cx >> blog;
+                if (nb != bcx) {
+                  bcx = nb;
+                  k = (dda.sx + 1) * 9 + 4;
+                }
+              } else if (ax == 1) {
+                const int nb = dda.cy >> blog;
+                if (nb != bcy) {
+                  bcy = nb;
+                  k = 9 + (dda.sy + 1) * 3 + 1;
+                }
+              } else {
+                const int nb = dda.cz >> blog;
+                if (nb != bcz) {
+                  bcz = nb;
+                  k = 13 + dda.sz;
+                }
+              }
+              if (k >= 0) {
+                slot = slot != kInvalid ? __ldg(&m.nbr[(size_t)slot * 27 + k]) : block_lookup(m, bcx, bcy, bcz);
+                sb = scratch_of(m, slot, ep);
+              }
             }
           }
-          if (k >= 0) {
-            slot = slot != kInvalid ? __ldg(&m.nbr[(size_t)slot * 27 + k]) : block_lookup(m, bcx, bcy, bcz);
-            sb = scratch_of(m, slot, ep);
-          }
         }
-      }
-      const unsigned peers = __match_any_sync(kFull, vid);
-      const bool alone = (peers == (1u << lane)) || vid == kInvalid;
-      if (__all_sync(kFull, alone)) {
-        if (vid != kInvalid) accumulate(m, vid, qv);
-      } else {
-        for (int j = 0; j < 4; ++j) sh_v[j][wid][lane] = qv[j];
-        __syncwarp();
-        if (vid != kInvalid && lane == __ffs(peers) - 1) {
-          long long sum[4] = {0, 0, 0, 0};
-          for (unsigned pm = peers; pm; pm &= pm - 1) {
-            const int src = __ffs(pm) - 1;
-            for (int j = 0; j < 4; ++j) sum[j] += sh_v[j][wid][src];
+        const unsigned peers = __match_any_sync(kFull, vid);
+        const bool alone = (peers == (1u << lane)) || vid == kInvalid;
+        if (__all_sync(kFull, alone)) {
+          if (vid != kInvalid) accumulate(m, vid, qv);
+        } else {
+          for (int j = 0; j < 4; ++j) sh_v[j][wid][lane] = qv[j];
+          __syncwarp();
+          if (vid != kInvalid && lane == __ffs(peers) - 1) {
+            long long sum[4] = {0, 0, 0, 0};
+            for (unsigned pm = peers; pm; pm &= pm - 1) {
+              const int src = __ffs(pm) - 1;
+              for (int j = 0; j < 4; ++j) sum[j] += sh_v[j][wid][src];
+            }
+            accumulate(m, vid, sum);
           }
-          accumulate(m, vid, sum);
+          __syncwarp();
         }
-        __syncwarp();
       }
     }
+    __syncwarp();
   }
   if (nrec) atomicAdd(&map_of(b, rec_map).ctr->nrecords, nrec);
 }
@@ -537,40 +678,91 @@ __device__ __forceinline__ void append(uint32_t* list, unsigned* count, uint32_t
   list[base + __popc(peers & ((1u << lane) - 1u))] = vid;
 }
 
-// One thread per voxel of a scratch block: every voxel that received records this scan gets
-// the Eq. (3) merge, its sums and flag are cleared, and it joins the scan's updated list and
-// (once) the queue of the next ESDF update.
-__global__ void __launch_bounds__(kThreads) k_apply(Batch b) {
+// Touch flags per lane in k_apply: 16 (one 16-byte load) where the scan's records are sparse
+// in its scratch blocks (thin lines of voxels per block), 4 where they are dense.
+__device__ __forceinline__ unsigned apply_flags_per_lane(const DevMap& m, bool wide) {
+  const unsigned long long vox = (unsigned long long)scratch_blocks(m) << m.b3log;
+  return wide && 2ull * __ldcg(&m.ctr->nrecords) < vox ? 16u : 4u;
+}
+
+// Every voxel that received records this scan gets the Eq. (3) merge, its sums and touch flag
+// are cleared, and it joins the scan's updated list and (once) the queue of the next ESDF
+// update. Each lane reads the touch flags of 4 or 16 consecutive scratch voxels; the warp
+// compacts the touched ones (possibly of two maps) and gives each lane one at a time.
+__global__ void __launch_bounds__(kThreads) k_apply(Batch b, unsigned warp_slots) {
   __shared__ unsigned pfx[kMaxBatch + 1];
+  const int lane = threadIdx.x & 31;
   const int nm = nmaps_of(b);
+  // 16 flags per lane only when the launch has enough scratch voxels to keep every resident
+  // warp busy several times over with them
+  const unsigned vall = cta_prefix(pfx, b, [&](unsigned mi) { return scratch_blocks(map_of(b, mi)) << map_of(b, mi).b3log; });
+  const bool wide = vall >= 16u * 32u * 4u * warp_slots;
+  __syncthreads();
   const unsigned total = cta_prefix(pfx, b, [&](unsigned mi) {
     const DevMap& m = map_of(b, mi);
-    return scratch_blocks(m) << m.b3log;
+    return (scratch_blocks(m) << m.b3log) / apply_flags_per_lane(m, wide);  // B^3 >= 64
   });
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
-    const unsigned mi = map_index(pfx, nm, i);
-    const DevMap& m = map_of(b, mi);
-    const unsigned sv = i - pfx[mi];  // scratch voxel
-    if (m.stouch[sv] == 0u) continue;
-    m.stouch[sv] = 0u;
-    ulonglong2* a = reinterpret_cast<ulonglong2*>(&m.sacc[4 * (size_t)sv]);
-    const ulonglong2 hi = a[0], lo = a[1];
-    a[0] = make_ulonglong2(0ull, 0ull);
-    a[1] = make_ulonglong2(0ull, 0ull);
-    const uint32_t vid = (m.slist[sv >> m.b3log] << m.b3log) | (sv & ((1u << m.b3log) - 1u));
-    const float Sw = __fadd_rn(__fmul_rn(__ll2float_rn((long long)hi.x), kAccInvScale),
-                               __fmul_rn(__ll2float_rn((long long)lo.x), kAccLoInvScale));
-    const float Swd = __fadd_rn(__fmul_rn(__ll2float_rn((long long)hi.y), kAccInvScale),
-                                __fmul_rn(__ll2float_rn((long long)lo.y), kAccLoInvScale));
-    const float2 t = m.tsdf[vid];
-    // Eq. (3): D <- (W D + sum w d) / (W + sum w), W <- min(W + sum w, W_max)
-    const float Wn = __fadd_rn(t.y, Sw);
-    const float D = __fdiv_rn(__fadd_rn(__fmul_rn(t.y, t.x), Swd), Wn);
-    m.tsdf[vid] = make_float2(D, fminf(Wn, m.wmax));
-    append(m.updated, &m.ctr->nupdated, vid);
-    if (!(m.vflags[vid] & kQueuedForEsdf)) {
-      m.vflags[vid] |= kQueuedForEsdf;
-      append(m.dirty, &m.ctr->ndirty, vid);
+  const unsigned stride = gridDim.x * blockDim.x;
+  for (unsigned base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < total; base += stride) {
+    const unsigned i = base + lane;
+    unsigned mi = 0, v0 = 0, bits = 0;
+    if (i < total) {
+      mi = map_index(pfx, nm, i);
+      const DevMap& m = map_of(b, mi);
+      const unsigned V = apply_flags_per_lane(m, wide);
+      v0 = (i - pfx[mi]) * V;  // first scratch voxel of this lane
+      if (V == 16) {
+        uint4* f = reinterpret_cast<uint4*>(m.stouch + v0);
+        const uint4 w = *f;
+        if (w.x | w.y | w.z | w.w) {
+          *f = make_uint4(0u, 0u, 0u, 0u);
+          const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            bits |= ((ws[q] & 1u) | ((ws[q] >> 7) & 2u) | ((ws[q] >> 14) & 4u) | ((ws[q] >> 21) & 8u)) << (4 * q);
+        }
+      } else {
+        uint32_t* f = reinterpret_cast<uint32_t*>(m.stouch + v0);
+        const uint32_t w = *f;
+        if (w) {
+          *f = 0u;
+          bits = (w & 1u) | ((w >> 7) & 2u) | ((w >> 14) & 4u) | ((w >> 21) & 8u);
+        }
+      }
+    }
+    int first = 0;
+    const int tot = warp_segments(__popc(bits), lane, &first);
+    for (int t0 = 0; t0 < tot; t0 += 32) {
+      const int t = t0 + lane;
+      const int own = segment_owner(first, t);
+      int n = t - __shfl_sync(kFull, first, own);
+      const unsigned ob = __shfl_sync(kFull, bits, own);
+      const unsigned omi = __shfl_sync(kFull, mi, own);
+      const unsigned ov0 = __shfl_sync(kFull, v0, own);
+      if (t >= tot) continue;
+      int j = 0;  // position of the (n+1)-th set bit of ob
+      while (!(ob >> j & 1u) || n-- > 0) ++j;
+      const DevMap& m = map_of(b, omi);
+      const unsigned sv = ov0 + (unsigned)j;  // scratch voxel
+      ulonglong2* a = reinterpret_cast<ulonglong2*>(&m.sacc[4 * (size_t)sv]);
+      const ulonglong2 hi = a[0], lo = a[1];
+      a[0] = make_ulonglong2(0ull, 0ull);
+      a[1] = make_ulonglong2(0ull, 0ull);
+      const uint32_t vid = (m.slist[sv >> m.b3log] << m.b3log) | (sv & ((1u << m.b3log) - 1u));
+      const float Sw = __fadd_rn(__fmul_rn(__ll2float_rn((long long)hi.x), kAccInvScale),
+                                 __fmul_rn(__ll2float_rn((long long)lo.x), kAccLoInvScale));
+      const float Swd = __fadd_rn(__fmul_rn(__ll2float_rn((long long)hi.y), kAccInvScale),
+                                  __fmul_rn(__ll2float_rn((long long)lo.y), kAccLoInvScale));
+      const float2 tv = m.tsdf[vid];
+      // Eq. (3): D <- (W D + sum w d) / (W + sum w), W <- min(W + sum w, W_max)
+      const float Wn = __fadd_rn(tv.y, Sw);
+      const float D = __fdiv_rn(__fadd_rn(__fmul_rn(tv.y, tv.x), Swd), Wn);
+      m.tsdf[vid] = make_float2(D, fminf(Wn, m.wmax));
+      append(m.updated, &m.ctr->nupdated, vid);
+      if (!(m.vflags[vid] & kQueuedForEsdf)) {
+        m.vflags[vid] |= kQueuedForEsdf;
+        append(m.dirty, &m.ctr->ndirty, vid);
+      }
     }
   }
 }
@@ -644,21 +836,37 @@ cudaError_t launch_integrate(const Batch& b, const LaunchCfg& cfg, LaunchHook* h
   // single-map launches size the point grid by the scan; batched launches use the tuned grid
   // (all kernels stride over their device-side work counts)
   const int gpts = b.maps ? cfg.num_sms * cfg.tune.bin_ctas_per_sm : grid_for(b.one_scan.n, cfg.num_sms, cfg.tune.bin_ctas_per_sm);
-  const int grays = b.maps ? cfg.num_sms * cfg.tune.rays_ctas_per_sm : grid_for(b.one_scan.n, cfg.num_sms, cfg.tune.rays_ctas_per_sm);
+  // the ray kernels run a grid of at most their resident CTAs over all SMs and cut the rays
+  // into warp tasks sized for that many warps
+  static int occ_group = 0, occ_rays = 0;
+  if (!occ_group) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_group, k_group_rays, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_rays, k_integrate_rays, kThreads, 0);
+    if (occ_group < 1) occ_group = 1;
+    if (occ_rays < 1) occ_rays = 1;
+  }
+  const int ggroup = cfg.num_sms * std::min(occ_group, cfg.tune.bin_ctas_per_sm);
+  const int grays = cfg.num_sms * std::min(occ_rays, cfg.tune.rays_ctas_per_sm);
   hook->begin(kKBin, s);
   k_bin_points<<<gpts, kThreads, 0, s>>>(b);
   hook->end(kKBin, s);
   hook->begin(kKGroupRays, s);
-  k_group_rays<<<gpts, kThreads, 0, s>>>(b);
+  k_group_rays<<<ggroup, kThreads, 0, s>>>(b, (unsigned)(ggroup * kWarps));
   hook->end(kKGroupRays, s);
   hook->begin(kKLink, s);
   k_link_blocks<<<cfg.num_sms * 4, kThreads, 0, s>>>(b);
   hook->end(kKLink, s);
   hook->begin(kKIntegrateRays, s);
-  k_integrate_rays<<<grays, kThreads, 0, s>>>(b);
+  k_integrate_rays<<<grays, kThreads, 0, s>>>(b, (unsigned)(grays * kWarps));
   hook->end(kKIntegrateRays, s);
   hook->begin(kKApply, s);
-  k_apply<<<cfg.num_sms * cfg.tune.apply_ctas_per_sm, kThreads, 0, s>>>(b);
+  static int occ_apply = 0;
+  if (!occ_apply) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_apply, k_apply, kThreads, 0);
+    if (occ_apply < 1) occ_apply = 1;
+  }
+  const int gapply = cfg.num_sms * cfg.tune.apply_ctas_per_sm;
+  k_apply<<<gapply, kThreads, 0, s>>>(b, (unsigned)(cfg.num_sms * std::min(occ_apply, cfg.tune.apply_ctas_per_sm) * kWarps));
   hook->end(kKApply, s);
   return cudaGetLastError();
 }

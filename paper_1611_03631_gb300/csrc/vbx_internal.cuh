@@ -5,7 +5,7 @@
 //                    hclaim[H] u32 scan epoch of the last scan whose rays entered the block
 //   per block      : bcoord[slot] int3, nbr[slot*27 + k] u32 slot of the neighbour block in
 //                    direction k = (dx+1)*9 + (dy+1)*3 + (dz+1) (k = 13 is the block itself),
-//                    sepoch[slot] / sidx[slot] u32 scan epoch and scratch block of the block
+//                    sinfo[slot] u64 {scan epoch << 32 | scratch block} of the block
 //   per voxel      : voxel id vid = slot * B^3 + ((lz*B + ly)*B + lx)
 //                    tsdf[vid]   float2 (D, W)                          8 B
 //                    esdf[vid]   u64 packed {d f32 | flags u8 | parent u8} 8 B
@@ -18,8 +18,7 @@
 //                    slist_h[i] / slist[i] u32 hash entry and pool slot of scratch block i,
 //                    sacc[4*sv] i64 sums of w and w*d of scratch voxel sv = i * B^3 + local,
 //                    each an exact two-part fixed point number (2^-28 part, 2^-60 part),
-//                    stouch[sv] u32 flag: the voxel received a record; updated list (u32)
-//                    (all zero between scans)
+//                    stouch[sv] u8: the voxel received a record (all zero between scans)
 //   lists          : updated (last scan), dirty (since last ESDF); the ESDF's active
 //                    (map, block) lists live in the launch group's EsdfCtl
 //   per-scan points: group hash table (64 B entries), group list, rays (float4)
@@ -76,7 +75,7 @@ struct Counters {
   unsigned int nupdated;
   unsigned int npoints_valid;
   unsigned int ntouched;  // blocks entered by the scan's rays (scratch blocks claimed)
-  unsigned int pad0;
+  unsigned int nvseg;     // voxel-traversal segments of the scan's rays
   unsigned long long nrecords;
   // ---- persistent
   unsigned int blocks;
@@ -129,15 +128,14 @@ struct DevMap {
   uint32_t cap_blocks;
   int3* bcoord;
   uint32_t* nbr;
-  uint32_t* sepoch;
-  uint32_t* sidx;
+  unsigned long long* sinfo;
   float2* tsdf;
   // per-scan sums (scratch blocks)
   uint32_t scr_cap;
   uint32_t* slist_h;
   uint32_t* slist;
   unsigned long long* sacc;
-  uint32_t* stouch;
+  uint8_t* stouch;
   unsigned long long* esdf;
   uint8_t* vflags;
   uint32_t* rbits0;
@@ -292,7 +290,8 @@ __device__ __forceinline__ bool ray_setup(const float pbar[3], const float s[3],
 // 65536*B for blocks). The next face crossing of axis a is at t_a = num_a / den_a; instead of
 // comparing the ratios at every step, the three pairwise cross differences
 // C_ab = num_a*den_b - num_b*den_a are kept and updated by additions when an axis steps.
-// Ties go to x, then y, then z.
+// Ties go to x, then y, then z. With ray ends at most 2^14 voxels apart (points farther away
+// are dropped) every numerator, denominator and product stays below 2^62.
 struct Dda {
   int cx, cy, cz;     // current cell
   int sx, sy, sz;     // step direction per axis (+1 / -1)
@@ -300,8 +299,13 @@ struct Dda {
   long long ix, iy, iz;  // F * den per axis
   long long cxy, cxz, cyz;
 
-  __device__ __forceinline__ void init(const long long S[3], const long long E[3], int log2F) {
+  __host__ __device__ __forceinline__ void init(const long long S[3], const long long E[3], int log2F) {
     long long num[3], den[3];
+    init(S, E, log2F, num, den);
+  }
+  // Also returns the first-crossing numerators and the denominators (for seeking).
+  __host__ __device__ __forceinline__ void init(const long long S[3], const long long E[3], int log2F, long long num[3],
+                                                long long den[3]) {
     int c[3], st[3], rem[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -320,9 +324,9 @@ struct Dda {
     cxz = num[0] * den[2] - num[2] * den[0];
     cyz = num[1] * den[2] - num[2] * den[1];
   }
-  __device__ __forceinline__ int steps() const { return rx + ry + rz; }
+  __host__ __device__ __forceinline__ int steps() const { return rx + ry + rz; }
   // Advances one cell; returns the axis stepped (0, 1, 2).
-  __device__ __forceinline__ int step() {
+  __host__ __device__ __forceinline__ int step() {
     const bool vx = rx > 0, vy = ry > 0, vz = rz > 0;
     if (vx && (!vy || cxy <= 0) && (!vz || cxz <= 0)) {
       cxy += iy;
@@ -343,6 +347,76 @@ struct Dda {
     cz += sz;
     rz -= 1;
     return 2;
+  }
+};
+
+// Work splitting of long rays: the traversal of a ray is cut at every K-th crossing of its
+// dominant axis d (the axis with the most steps, ties to the lower axis); segment s starts in
+// the cell entered by the (s*K)-th crossing of d and ends before the ((s+1)*K)-th. The state at
+// a cut has a closed form: after n_a crossings per axis, cell_a = c_a + s_a n_a,
+// rem_a -= n_a and C_ab += n_a F den_b - n_b F den_a, and n_b for b != d counts the crossings
+// of b that the DDA orders before the cut (earlier, or at the same parameter on a lower axis).
+struct DdaSeg {
+  Dda q0;  // state at the start of the ray
+  long long num0[3], den[3];
+  int log2F;
+  int d;  // dominant axis
+
+  __host__ __device__ __forceinline__ void init(const long long S[3], const long long E[3], int lf) {
+    log2F = lf;
+    q0.init(S, E, lf, num0, den);
+    d = 0;
+    if (q0.ry > q0.rx) d = 1;
+    if (q0.rz > (d == 0 ? q0.rx : q0.ry)) d = 2;
+  }
+  __host__ __device__ __forceinline__ int rem(int a) const { return a == 0 ? q0.rx : (a == 1 ? q0.ry : q0.rz); }
+  __host__ __device__ __forceinline__ int segments(int K) const { return rem(d) / K + 1; }
+  // DDA state at the start of segment s (0 <= s < segments(K)); *left = steps after it.
+  __host__ __device__ __forceinline__ Dda seek(int s, int K, int* left) const {
+    Dda q = q0;
+    if (s == 0) {
+      *left = q0.steps();
+      return q;
+    }
+    const long long F = 1ll << log2F;
+    // (selected without indexing by d, so that the arrays stay in registers)
+    const long long num_d = d == 0 ? num0[0] : (d == 1 ? num0[1] : num0[2]);
+    const long long den_d = d == 0 ? den[0] : (d == 1 ? den[1] : den[2]);
+    const long long j = (long long)s * K;     // crossings of d up to and including the cut
+    const long long tn = num_d + (j - 1) * F;  // the cut is at t = tn / den_d
+    const long long fd = den_d << log2F;
+    long long n[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      if (b == d) {
+        n[b] = j;
+        continue;
+      }
+      const int rb = rem(b);
+      long long cnt = 0;
+      if (rb > 0) {
+        // crossing i of b precedes the cut iff (num0_b + i F) den_d < tn den_b
+        // (or equal, for b before d in the tie order)
+        const long long r = tn * den[b] - num0[b] * den_d;
+        if (b < d)
+          cnt = r < 0 ? 0 : r / fd + 1;
+        else
+          cnt = r <= 0 ? 0 : (r - 1) / fd + 1;
+        if (cnt > rb) cnt = rb;
+      }
+      n[b] = cnt;
+    }
+    q.cx += q.sx * (int)n[0];
+    q.cy += q.sy * (int)n[1];
+    q.cz += q.sz * (int)n[2];
+    q.rx -= (int)n[0];
+    q.ry -= (int)n[1];
+    q.rz -= (int)n[2];
+    q.cxy += n[0] * q.iy - n[1] * q.ix;
+    q.cxz += n[0] * q.iz - n[2] * q.ix;
+    q.cyz += n[1] * q.iz - n[2] * q.iy;
+    *left = q.steps();
+    return q;
   }
 };
 
