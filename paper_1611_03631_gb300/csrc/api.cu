@@ -294,7 +294,10 @@ vbx_status vbx_create_map(float voxel_size, int voxels_per_block, float truncati
   d.B = B;
   d.blog = ilog2(B);
   d.b3log = 3 * d.blog;
-  d.tile_shift = B == 16 ? 3 : 0;
+#ifndef VBX_TILE_EDGE
+#define VBX_TILE_EDGE 8
+#endif
+  d.tile_shift = (B == 16 && VBX_TILE_EDGE == 8) ? 3 : 0;  // ESDF tiles of 8^3 voxels
   d.weighting = opt.weighting;
   d.grouped = opt.grouped ? 1 : 0;
   d.cap_blocks = (uint32_t)cap;

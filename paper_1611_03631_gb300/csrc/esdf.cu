@@ -49,7 +49,10 @@ struct Tile {
                           // k of the neighbour tile relative to this one)
 };
 
-constexpr int kTileEdge = 8;  // sub-block edge S for B >= 8
+#ifndef VBX_TILE_EDGE
+#define VBX_TILE_EDGE 8
+#endif
+constexpr int kTileEdge = VBX_TILE_EDGE;  // sub-block edge S for B >= 8
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
@@ -119,7 +122,8 @@ struct Geo {
   static constexpr int S3 = S * S * S;
   static constexpr int O = B / S;  // tiles per block and axis (1 or 2)
   static constexpr int LOGB = B == 4 ? 2 : (B == 8 ? 3 : 4);
-  static constexpr int LOGS = S == 4 ? 2 : 3;
+  static constexpr int LOGS = S == 4 ? 2 : (S == 8 ? 3 : 4);
+  static_assert((1 << LOGB) == B && (1 << LOGS) == S && S <= B, "tile and block edges are 4, 8 or 16");
   __device__ static __forceinline__ int cell_of_local(int l) {
     return (((l >> (2 * LOGS)) + 1) * T + (((l >> LOGS) & (S - 1)) + 1)) * T + ((l & (S - 1)) + 1);
   }
@@ -508,6 +512,7 @@ __global__ void __launch_bounds__(NT) k_esdf(const DevMap* __restrict__ maps, in
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ unsigned pfx[kMaxBatch + 1];
   __shared__ unsigned long long cta_pops;
+  __shared__ unsigned sh_item;
   const unsigned tid = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned nthreads = gridDim.x * blockDim.x;
   const unsigned long long t_start = global_ns();
@@ -603,9 +608,17 @@ __global__ void __launch_bounds__(NT) k_esdf(const DevMap* __restrict__ maps, in
       if (tid == 0) atomicOr(&ctl->error, kErrTimeout);
       break;
     }
-    if (tid == 0) ctl->rcnt[(r + 2) % 3] = 0;
+    if (tid == 0) {
+      ctl->rcnt[(r + 2) % 3] = 0;
+      ctl->rnext[(r + 2) % 3] = 0;
+    }
     const uint2* cur = (r & 1) ? ctl->ract1 : ctl->ract0;
-    for (unsigned item = blockIdx.x; item < cnt; item += gridDim.x) {
+    for (;;) {
+      if (threadIdx.x == 0) sh_item = atomicAdd(&ctl->rnext[r % 3], 1u);
+      __syncthreads();
+      const unsigned item = sh_item;
+      __syncthreads();
+      if (item >= cnt) break;
       const uint2 e = cur[item];
       const DevMap& m = maps[e.x];
       RoundArgs ra;
@@ -636,9 +649,17 @@ __global__ void __launch_bounds__(NT) k_esdf(const DevMap* __restrict__ maps, in
       if (tid == 0) atomicOr(&ctl->error, kErrTimeout);
       break;
     }
-    if (tid == 0) ctl->lcnt[(l + 2) % 3] = 0;
+    if (tid == 0) {
+      ctl->lcnt[(l + 2) % 3] = 0;
+      ctl->lnext[(l + 2) % 3] = 0;
+    }
     const uint2* cur = (l & 1) ? ctl->lact1 : ctl->lact0;
-    for (unsigned item = blockIdx.x; item < cnt; item += gridDim.x) {
+    for (;;) {
+      if (threadIdx.x == 0) sh_item = atomicAdd(&ctl->lnext[l % 3], 1u);
+      __syncthreads();
+      const unsigned item = sh_item;
+      __syncthreads();
+      if (item >= cnt) break;
       const uint2 e = cur[item];
       const DevMap& m = maps[e.x];
       RoundArgs ra;

@@ -102,6 +102,8 @@ struct EsdfCtl {
   GridBarrier bar;
   unsigned int rcnt[3];
   unsigned int lcnt[3];
+  unsigned int rnext[3];  // next unclaimed entry of the round's raise / lower list (CTAs claim
+  unsigned int lnext[3];  // tiles one at a time, so a round is not paced by a static split)
   unsigned int error;
   unsigned int cap;  // capacity of each active list
   uint2* ract0;
