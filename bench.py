@@ -255,7 +255,20 @@ def run_batched_plane_sphere(args, vbx, torch, dev, n_maps: int = 64):
         for j, sq in enumerate(seqs)
     ]
     cap = SERVE_C1_CAPACITY["plane_sphere"]
-    maps = [vbx.Map.from_scene_params(seqs[0].params, block_capacity=cap, max_points=64 * 48) for _ in range(n_maps)]
+    # scratch for the largest scan of the sequences (a scan's rays enter the same blocks
+    # whatever the map holds, so one pass measures it)
+    probe = vbx.Map.from_scene_params(seqs[0].params, block_capacity=cap, max_points=64 * 48)
+    need = 0
+    for j in range(4):
+        probe.reset()
+        for f in range(F):
+            probe.integrate_scan(pts[j][f], seqs[j].poses[f])
+            need = max(need, int(probe.stats()["touched_blocks"]))
+    probe.close()
+    maps = [
+        vbx.Map.from_scene_params(seqs[0].params, block_capacity=cap, max_points=64 * 48, scratch_blocks=need + 1)
+        for _ in range(n_maps)
+    ]
     outs = [
         (
             torch.empty(N_QUERIES, dtype=torch.float32, device=dev),

@@ -34,6 +34,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
+static_assert(kThreads >= kMaxBatch, "one thread per map of a batch builds the per-map prefix");
 constexpr unsigned kFull = 0xffffffffu;
 // Long rays are traversed in segments spread over the lanes of a warp (DdaSeg): a voxel
 // segment ends at every kVoxSeg-th crossing of the ray's dominant axis, a block segment at
@@ -146,15 +147,33 @@ __device__ __forceinline__ unsigned cta_prefix(unsigned* pfx, const Batch& b, F 
     __syncthreads();
     return pfx[1];
   }
+  // every thread reads one map's count; warp 0 scans them (kMaxBatch / 32 per lane)
   pfx[t + 1] = t < nm ? count((unsigned)t) : 0u;
-  if (t == 0) pfx[0] = 0u;
   __syncthreads();
-  for (int off = 1; off < kMaxBatch; off <<= 1) {
-    const unsigned add = t >= off ? pfx[t + 1 - off] : 0u;
-    __syncthreads();
-    pfx[t + 1] += add;
-    __syncthreads();
+  if (t < 32) {
+    constexpr int per = kMaxBatch / 32;
+    unsigned v[per];
+    unsigned sum = 0;
+#pragma unroll
+    for (int j = 0; j < per; ++j) {
+      v[j] = pfx[t * per + j + 1];
+      sum += v[j];
+    }
+    unsigned incl = sum;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const unsigned up = __shfl_up_sync(kFull, incl, off);
+      if (t >= off) incl += up;
+    }
+    unsigned run = incl - sum;
+    if (t == 0) pfx[0] = 0u;
+#pragma unroll
+    for (int j = 0; j < per; ++j) {
+      run += v[j];
+      pfx[t * per + j + 1] = run;
+    }
   }
+  __syncthreads();
   return pfx[nm];
 }
 
@@ -835,7 +854,14 @@ cudaError_t launch_integrate(const Batch& b, const LaunchCfg& cfg, LaunchHook* h
   const cudaStream_t s = cfg.stream;
   // single-map launches size the point grid by the scan; batched launches use the tuned grid
   // (all kernels stride over their device-side work counts)
-  const int gpts = b.maps ? cfg.num_sms * cfg.tune.bin_ctas_per_sm : grid_for(b.one_scan.n, cfg.num_sms, cfg.tune.bin_ctas_per_sm);
+  static int occ_bin = 0;
+  if (!occ_bin) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_bin, k_bin_points, kThreads, 0);
+    if (occ_bin < 1) occ_bin = 1;
+  }
+  // grids of at most the resident CTAs (every CTA first builds the per-map prefix)
+  const int bin_per_sm = std::min(occ_bin, cfg.tune.bin_ctas_per_sm);
+  const int gpts = b.maps ? cfg.num_sms * bin_per_sm : grid_for(b.one_scan.n, cfg.num_sms, bin_per_sm);
   // the ray kernels run a grid of at most their resident CTAs over all SMs and cut the rays
   // into warp tasks sized for that many warps
   static int occ_group = 0, occ_rays = 0;
@@ -865,8 +891,8 @@ cudaError_t launch_integrate(const Batch& b, const LaunchCfg& cfg, LaunchHook* h
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_apply, k_apply, kThreads, 0);
     if (occ_apply < 1) occ_apply = 1;
   }
-  const int gapply = cfg.num_sms * cfg.tune.apply_ctas_per_sm;
-  k_apply<<<gapply, kThreads, 0, s>>>(b, (unsigned)(cfg.num_sms * std::min(occ_apply, cfg.tune.apply_ctas_per_sm) * kWarps));
+  const int gapply = cfg.num_sms * std::min(occ_apply, cfg.tune.apply_ctas_per_sm);
+  k_apply<<<gapply, kThreads, 0, s>>>(b, (unsigned)(gapply * kWarps));
   hook->end(kKApply, s);
   return cudaGetLastError();
 }
