@@ -355,7 +355,9 @@ def _serve_c1_sets():
 def _serve_once(serve, sets, arrivals: float, capacity, slots: int = SERVE_SLOTS, sessions: int = SERVE_SESSIONS):
     pool = serve.ScanPool(sets, n_queries=N_QUERIES)
     scratch = serve.scratch_for_pool(pool, capacity)
-    srv = serve.MapServer(pool, slots=slots, hbm_budget=SERVE_BUDGET, capacity=capacity, use_graph=True, scratch=scratch)
+    srv = serve.MapServer(
+        pool, slots=slots, hbm_budget=SERVE_BUDGET, capacity=capacity, use_graph=True, scratch=scratch, prealloc="fill"
+    )
     specs = serve.poisson_sessions(
         sessions,
         list(sets),
@@ -795,6 +797,8 @@ def run_gpu(args):
     if not args.no_batched:
         batched = run_batched(args, vbx, torch, dev)
         batched_c1 = run_batched_plane_sphere(args, vbx, torch, dev)
+        # a smaller batch: lower step latency at a lower throughput
+        batched_c1["with_32_maps"] = run_batched_plane_sphere(args, vbx, torch, dev, n_maps=32)
     if not args.no_served:
         served = run_served(args, vbx, torch)
     if rank != 0:

@@ -250,7 +250,9 @@ vbx_status vbx_map_bytes(int voxels_per_block, const vbx_map_options* opt, int64
 vbx_status vbx_map_device_bytes(vbx_map_t map, int64_t* bytes_out);
 
 /* Empties the map (no blocks, no observed voxels, nothing queued) without freeing its memory,
- * so that it can serve a new session. Synchronises `stream`. */
+ * so that it can serve a new session. Enqueued on `stream` (one kernel and one memset, sized on
+ * the device by the map's own counters); the host does not wait. Work enqueued on the same
+ * stream afterwards sees the empty map. */
 vbx_status vbx_reset_map(vbx_map_t map, void* stream);
 
 /* Kernels launched by all maps of this process (a running counter). */

@@ -1063,44 +1063,8 @@ vbx_status vbx_map_device_bytes(vbx_map_t m, int64_t* out) {
 
 vbx_status vbx_reset_map(vbx_map_t m, void* stream) {
   if (!m) return fail(VBX_ERR_INVALID_ARG, "map is NULL");
-  cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return cuda_fail(e, "reset sync");
-  vbx::Counters c;
-  if ((e = cudaMemcpy(&c, m->d.ctr, sizeof(c), cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_fail(e, "reset counters");
-  const size_t nb = std::min<size_t>(c.blocks, m->d.cap_blocks);
-  const size_t B3 = (size_t)m->B * m->B * m->B;
-  const size_t V = nb * B3;
-  vbx::DevMap& d = m->d;
-  const size_t tiles = nb << d.tile_shift;
-  const size_t SV = (size_t)std::min<uint32_t>(c.ntouched, d.scr_cap) * B3;  // scratch of the last scan
-  struct Clear {
-    void* p;
-    size_t bytes;
-    int fill;
-  } clears[] = {
-      {d.hkeys, ((size_t)d.hmask + 1) * 8, 0xff},
-      {d.hvals, ((size_t)d.hmask + 1) * 4, 0xff},
-      {d.nbr, nb * 27 * 4, 0xff},
-      {d.hclaim, ((size_t)d.hmask + 1) * 4, 0},
-      {d.bcoord, nb * 12, 0},
-      {d.sinfo, nb * 8, 0},
-      {d.tsdf, V * 8, 0},
-      {d.sacc, SV * 32, 0},
-      {d.stouch, SV, 0},
-      {d.esdf, V * 8, 0},
-      {d.vflags, V, 0},
-      {d.rbits0, V / 8, 0},
-      {d.rbits1, V / 8, 0},
-      {d.lbits0, V / 8, 0},
-      {d.lbits1, V / 8, 0},
-      {d.bstamp_r, tiles * 4, 0},
-      {d.bstamp_l, tiles * 4, 0},
-      {d.ctr, sizeof(vbx::Counters), 0},
-  };
-  for (const Clear& x : clears)
-    if (x.bytes && (e = cudaMemsetAsync(x.p, x.fill, x.bytes, s)) != cudaSuccess) return cuda_fail(e, "reset clear");
-  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "reset sync");
+  cudaError_t e = vbx::launch_reset_map(m->d, m->cfg(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "reset");
   m->last_points_in = 0;
   return VBX_OK;
 }

@@ -786,6 +786,49 @@ __global__ void __launch_bounds__(kThreads) k_apply(Batch b, unsigned warp_slots
   }
 }
 
+// ------------------------------------------------------------------------------ reset
+// Empties a map for reuse without a host round trip: the used sizes (blocks, the last scan's
+// scratch blocks) are read on the device; the counters are cleared after this kernel.
+__global__ void __launch_bounds__(kThreads) k_reset_map(DevMap m) {
+  const size_t nb = min(__ldcg(&m.ctr->blocks), m.cap_blocks);
+  const size_t B3 = (size_t)1 << m.b3log;
+  const size_t V = nb * B3;
+  const size_t SV = (size_t)min(__ldcg(&m.ctr->ntouched), m.scr_cap) * B3;
+  const size_t H = (size_t)m.hmask + 1;
+  const size_t tiles = nb << m.tile_shift;
+  const size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x, st = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = i0; i < H; i += st) {
+    m.hkeys[i] = kEmptyKey;
+    m.hvals[i] = kInvalid;
+    m.hclaim[i] = 0u;
+  }
+  for (size_t i = i0; i < nb; i += st) {
+    m.bcoord[i] = make_int3(0, 0, 0);
+    m.sinfo[i] = 0ull;
+  }
+  for (size_t i = i0; i < nb * 27; i += st) m.nbr[i] = kInvalid;
+  for (size_t i = i0; i < tiles; i += st) {
+    m.bstamp_r[i] = 0u;
+    m.bstamp_l[i] = 0u;
+  }
+  for (size_t i = i0; i < V; i += st) {
+    m.tsdf[i] = make_float2(0.0f, 0.0f);
+    m.esdf[i] = 0ull;
+    m.vflags[i] = 0u;
+  }
+  for (size_t i = i0; i < V / 32; i += st) {
+    m.rbits0[i] = 0u;
+    m.rbits1[i] = 0u;
+    m.lbits0[i] = 0u;
+    m.lbits1[i] = 0u;
+  }
+  for (size_t i = i0; i < SV; i += st) {
+    m.stouch[i] = 0u;
+    reinterpret_cast<ulonglong2*>(m.sacc)[2 * i] = make_ulonglong2(0ull, 0ull);
+    reinterpret_cast<ulonglong2*>(m.sacc)[2 * i + 1] = make_ulonglong2(0ull, 0ull);
+  }
+}
+
 // ------------------------------------------------------------------------ import (restore)
 __global__ void __launch_bounds__(kThreads) k_import_alloc(DevMap m, const int* __restrict__ vox, int n) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
@@ -895,6 +938,13 @@ cudaError_t launch_integrate(const Batch& b, const LaunchCfg& cfg, LaunchHook* h
   k_apply<<<gapply, kThreads, 0, s>>>(b, (unsigned)(gapply * kWarps));
   hook->end(kKApply, s);
   return cudaGetLastError();
+}
+
+cudaError_t launch_reset_map(const DevMap& m, const LaunchCfg& cfg) {
+  k_reset_map<<<cfg.num_sms * 8, kThreads, 0, cfg.stream>>>(m);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return cudaMemsetAsync(m.ctr, 0, sizeof(Counters), cfg.stream);
 }
 
 cudaError_t launch_import(const DevMap& m, const int* vox, const float* D, const float* W, int n,

@@ -101,6 +101,8 @@ cudaError_t launch_integrate_noalloc(const DevMap& m, void* scratch, const float
 Batch single_batch(const DevMap& m, const float* pts, int n, const Pose& T, unsigned epoch = 0);
 cudaError_t launch_import(const DevMap& m, const int* vox, const float* D, const float* W, int n,
                           const LaunchCfg& cfg, LaunchHook* hook);
+// empties the map on cfg.stream (no host synchronisation)
+cudaError_t launch_reset_map(const DevMap& m, const LaunchCfg& cfg);
 
 // esdf.cu: one cooperative launch updates the ESDF of nmaps maps (device array of DevMap)
 size_t esdf_smem_bytes(int max_B);

@@ -134,6 +134,7 @@ class MapServer:
         capacity: Optional[Dict[str, int]] = None,
         use_graph: bool = True,
         scratch: Optional[Dict[str, int]] = None,
+        prealloc=None,
     ):
         import torch
 
@@ -150,6 +151,22 @@ class MapServer:
         # idle placeholder maps keep unbound slots valid (a slot always holds a map)
         self.idle = [vbx.Map(0.5, 4, 0.5, 1.0, block_capacity=8, max_points=1024) for _ in range(slots)]
         self.batch = vbx.MapBatch(self.idle, max_queries=pool.n_queries)
+        # warm pool: maps created before the run (creation allocates and synchronises the
+        # device, which would stall the step loop); they count against the budget.
+        # prealloc = {kind: count}, or "fill": an equal share of the budget per kind, at most
+        # one map per slot
+        if prealloc == "fill":
+            share = self.budget / max(len(pool.kinds), 1)
+            prealloc = {k: min(slots, int(share // self.map_bytes(k))) for k in pool.kinds}
+        for kind, n in (prealloc or {}).items():
+            for _ in range(n):
+                need = self.map_bytes(kind)
+                if self.used + need > self.budget:
+                    break
+                m = self._new_map(kind)
+                self.used += m.device_bytes()
+                self.peak = max(self.peak, self.used)
+                self.free[kind].append(m)
         q = pool.n_queries
         self.out = [
             (

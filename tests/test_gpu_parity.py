@@ -297,6 +297,27 @@ def test_tight_scratch_equals_default(vbx):
     assert vbx.map_bytes(16, 4096, 1 << 16, scratch_blocks=need) < vbx.map_bytes(16, 4096, 1 << 16)
 
 
+def test_reset_map_equals_fresh_map(vbx):
+    """A reset map (device-side, stream-ordered) integrates a new sequence exactly like a new map."""
+    a_seq = scenes.room(frames=3, width=160, height=120, fx=131.25, fy=131.25, seed=11)
+    b_seq = scenes.room(frames=3, width=160, height=120, fx=131.25, fy=131.25, seed=12)
+    m = vbx.Map.from_scene_params(a_seq.params, block_capacity=4096)
+    for i in range(len(a_seq)):
+        m.integrate_scan(_dev(a_seq.points[i]), a_seq.poses[i])
+        m.update_esdf()
+    m.reset()
+    fresh = vbx.Map.from_scene_params(b_seq.params, block_capacity=4096)
+    for g in (m, fresh):
+        for i in range(len(b_seq)):
+            g.integrate_scan(_dev(b_seq.points[i]), b_seq.poses[i])
+            g.update_esdf()
+        g.sync()
+    ea, eb = m.export(), fresh.export()
+    for k in ("keys", "D", "W", "d", "flags"):
+        assert np.array_equal(ea[k], eb[k]), k
+    assert m.stats()["blocks"] == fresh.stats()["blocks"]
+
+
 def test_invalid_arguments(vbx):
     with pytest.raises(vbx.VbxError):
         vbx.Map(0.1, 7, 0.3, 2.0)
