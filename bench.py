@@ -793,6 +793,16 @@ def run_gpu(args):
         e2e_total = float(t.item())
     e2e_value = ws * args.steps / (e2e_total / 1000.0)
 
+    esdf_cmp = None
+    if args.esdf_methods and rank == 0:
+        from paper_1611_03631_gb300 import esdf_methods, scenes as _sc
+
+        esdf_cmp = esdf_methods.compare(_sc.esdf_benchmark())
+        esdf_cmp["workload"] = (
+            "simulated ESDF benchmark of Sec. VI-B: ground, walls x=0 and y=10, sphere r=1.5 m, 2 m cube in a 10 m space; "
+            "50 noiseless 320x240 depth images (fx=262.5, max 5 m) from random 6-DoF poses >= 1 m from obstacles; "
+            "delta=4v, constant weight, d_max=2 m; errors over observed free voxels with true distance in (0, 1.5] m"
+        )
     batched = batched_c1 = served = None
     if not args.no_batched:
         batched = run_batched(args, vbx, torch, dev)
@@ -842,6 +852,7 @@ def run_gpu(args):
         "clocks": clk,
         "batched": batched,
         "batched_plane_sphere": batched_c1,
+        "esdf_methods": esdf_cmp,
         "served": served,
     }
     print(json.dumps(line), flush=True)
@@ -859,6 +870,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-map batched section")
     ap.add_argument("--no-served", action="store_true", help="skip the served-sessions section")
+    ap.add_argument(
+        "--esdf-methods", action=argparse.BooleanOptionalAction, default=True,
+        help="the ESDF-method comparison on the simulated benchmark scene (occupancy, half band, one-voxel band)",
+    )
     ap.add_argument("--batch-maps", type=int, default=64, help="maps of the batched section")
     ap.add_argument("--only-batched", action="store_true", help="run the batched section alone (profiling)")
     ap.add_argument(

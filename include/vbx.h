@@ -60,6 +60,10 @@ typedef struct {
                              33 B per voxel); 0 or more than block_capacity: block_capacity.
                              A scan that enters more blocks is not integrated at all and its
                              synchronising call reports VBX_ERR_OUT_OF_MEMORY               */
+  int esdf_mode;          /* ESDF seeds: 0 the fixed band |D| < fixed_band (Sec. V-A); 1 the
+                             occupancy ESDF compared in Sec. VI-B: observed voxels with D < 0
+                             are occupied at distance 0 and every other observed voxel holds
+                             its unsigned distance to them                                   */
 } vbx_map_options;
 
 /* Fills *opt with the defaults above (weighting 0, grouped 1). */

@@ -36,6 +36,7 @@ class orc_params(ctypes.Structure):
         ("max_range", ctypes.c_float),
         ("grouped", ctypes.c_int),
         ("esdf_fp32", ctypes.c_int),
+        ("esdf_mode", ctypes.c_int),
     ]
 
 
@@ -114,6 +115,7 @@ def make_params(
     max_range: float = math.inf,
     grouped: int = 1,
     esdf_fp32: int = 0,
+    esdf_mode: int = 0,
 ) -> orc_params:
     return orc_params(
         voxel_size,
@@ -127,6 +129,7 @@ def make_params(
         max_range,
         grouped,
         esdf_fp32,
+        esdf_mode,
     )
 
 

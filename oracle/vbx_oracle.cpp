@@ -54,6 +54,12 @@
 //      cand = |d_v| + L_k, accepted iff cand < |d_n|; values never exceed d_max.
 //   R9 query: the 8 voxel centres around q are selected in float32 (t = fl(fl(q/v) - 0.5),
 //      i0 = floor(t), f = t - i0); any unobserved corner gives status "unknown".
+//   R10 the one-voxel fixed band that Sec. VI-B and VIII recommend has no stated value:
+//      gamma = v unless given; the half-truncation band of Sec. VI-B is |D| < delta / 2.
+//   R11 Sec. VI-B compares the fixed band with an occupancy ESDF that treats negative TSDF
+//      voxels as occupied at distance 0: in that mode (esdf_mode = 1) the seeds are the
+//      observed voxels with fl32(D) < 0, fixed at +0, and every other observed voxel is
+//      positive, so the field is the unsigned quasi-Euclidean distance to occupied voxels.
 
 #include <algorithm>
 #include <cmath>
@@ -124,6 +130,7 @@ struct Params {
   float max_range;
   int grouped;
   int esdf_fp32;  // 1: ESDF values computed in float32 (bit-exact mode), 0: float64
+  int esdf_mode;  // 0: fixed band |D| < gamma (Sec. V-A); 1: occupancy (R11, Sec. VI-B)
 };
 
 // 26-neighbourhood; index k = (dx+1)*9 + (dy+1)*3 + (dz+1); 13 is the voxel itself, and the
@@ -446,11 +453,12 @@ void update_esdf(Map& m, int fifo) {
     EsdfVoxel* e = m.esdf_at(c);
     if (!t || !e || !(t->W > 0.0)) continue;
     float Df = (float)t->D;
-    double sT = Df >= 0.0f ? 1.0 : -1.0;
-    bool fixed_now = std::fabs(Df) < p.gamma;  // R6: isFixed on the TSDF voxel
+    const bool occ = p.esdf_mode == 1;  // R11
+    double sT = occ ? 1.0 : (Df >= 0.0f ? 1.0 : -1.0);
+    bool fixed_now = occ ? Df < 0.0f : std::fabs(Df) < p.gamma;  // R6: isFixed on the TSDF voxel
     if (fixed_now) {
       m.st.seeds++;
-      double val = seed_value(p, t->D);
+      double val = occ ? 0.0 : seed_value(p, t->D);
       bool lower_only = !e->observed || (sgn(e->d) == sT && std::fabs(val) <= std::fabs(e->d));
       e->observed = true;
       e->fixed = true;
@@ -573,10 +581,11 @@ void full_esdf(Map& m, std::vector<Key3>* keys_sorted, std::vector<double>* out)
       if (!(t.W > 0.0)) continue;
       observed[f] = 1;
       float Df = (float)t.D;
-      sign[f] = Df >= 0.0f ? 1 : -1;
-      if (std::fabs(Df) < p.gamma) {
+      const bool occ = p.esdf_mode == 1;  // R11
+      sign[f] = occ || Df >= 0.0f ? 1 : -1;
+      if (occ ? Df < 0.0f : std::fabs(Df) < p.gamma) {
         fixed[f] = 1;
-        dist[f] = std::fabs(seed_value(p, t.D));
+        dist[f] = occ ? 0.0 : std::fabs(seed_value(p, t.D));
         pq.push({dist[f], f});
       }
     }
@@ -675,13 +684,14 @@ struct orc_params {
   float max_range;
   int grouped;
   int esdf_fp32;
+  int esdf_mode;
 };
 
 void* orc_create(const orc_params* op) {
   Map* m = new Map();
   m->p = Params{op->voxel_size, op->voxels_per_block, op->truncation, op->max_esdf_dist, op->weighting,
                 op->eps,        op->fixed_band,       op->w_max,      op->max_range,     op->grouped,
-                op->esdf_fp32};
+                op->esdf_fp32,  op->esdf_mode};
   return m;
 }
 
@@ -799,7 +809,7 @@ float orc_projective_distance(const float* pbar, const float* s, const int32_t* 
 
 float orc_record_weight(const orc_params* op, float Wg, float d) {
   Params p{op->voxel_size, op->voxels_per_block, op->truncation, op->max_esdf_dist, op->weighting, op->eps,
-           op->fixed_band, op->w_max,            op->max_range,  op->grouped,       op->esdf_fp32};
+           op->fixed_band, op->w_max,            op->max_range,  op->grouped,       op->esdf_fp32, op->esdf_mode};
   return record_weight(p, Wg, d);
 }
 
@@ -808,7 +818,7 @@ float orc_record_weight(const orc_params* op, float Wg, float d) {
 int64_t orc_group(const orc_params* op, const float* pts, int64_t n, const float* T16, int32_t* keys, float* pbar,
                   float* Wg, int64_t* count, int64_t cap) {
   Params p{op->voxel_size, op->voxels_per_block, op->truncation, op->max_esdf_dist, op->weighting, op->eps,
-           op->fixed_band, op->w_max,            op->max_range,  1,                 op->esdf_fp32};
+           op->fixed_band, op->w_max,            op->max_range,  1,                 op->esdf_fp32, op->esdf_mode};
   std::vector<std::pair<Key3, Group>> gs;
   {
     std::unordered_map<Key3, Group, Key3Hash> groups;

@@ -253,6 +253,7 @@ vbx_status vbx_create_map(float voxel_size, int voxels_per_block, float truncati
   vbx_default_options(&opt);
   if (opt_in) opt = *opt_in;
   if (opt.weighting != 0 && opt.weighting != 1) return fail(VBX_ERR_INVALID_ARG, "weighting must be 0 or 1");
+  if (opt.esdf_mode != 0 && opt.esdf_mode != 1) return fail(VBX_ERR_INVALID_ARG, "esdf_mode must be 0 or 1");
   const float eps = opt.eps > 0.0f ? opt.eps : voxel_size;
   if (opt.weighting == 1 && !(eps < truncation)) return fail(VBX_ERR_INVALID_ARG, "eps must be below truncation");
   const int B = voxels_per_block;
@@ -299,6 +300,7 @@ vbx_status vbx_create_map(float voxel_size, int voxels_per_block, float truncati
 #endif
   d.tile_shift = (B == 16 && VBX_TILE_EDGE == 8) ? 3 : 0;  // ESDF tiles of 8^3 voxels
   d.weighting = opt.weighting;
+  d.esdf_mode = opt.esdf_mode;
   d.grouped = opt.grouped ? 1 : 0;
   d.cap_blocks = (uint32_t)cap;
   const uint32_t H = next_pow2((uint64_t)cap * 2);

@@ -555,17 +555,22 @@ __global__ void __launch_bounds__(NT) k_esdf(const DevMap* __restrict__ maps, in
     const float2 t = m.tsdf[vid];
     if (!(t.y > 0.0f)) continue;
     const float Df = t.x == 0.0f ? 0.0f : t.x;  // sign(0) = +1
-    const bool neg = Df < 0.0f;
+    // fixed band |D| < gamma (Sec. V-A), or occupancy: D < 0 is occupied at distance 0 and
+    // every other observed voxel is positive (the occupancy ESDF of Sec. VI-B)
+    const bool occ = m.esdf_mode == 1;
+    const bool neg = !occ && Df < 0.0f;
+    const bool fixed_now = occ ? Df < 0.0f : fabsf(Df) < m.gamma;
+    const float seedv = occ ? 0.0f : Df;
     const float sdmax = neg ? -dmax : dmax;
     const unsigned long long w = __ldcg(&m.esdf[vid]);
     const unsigned fl = ew_flags(w);
     const bool obs = (fl & kObserved) != 0;
     const float de = ew_d(w);
     const uint32_t slot = tile_item_of(m, vid);
-    if (fabsf(Df) < m.gamma) {  // isFixed, evaluated on the TSDF voxel
+    if (fixed_now) {  // isFixed, evaluated on the TSDF voxel
       atomicAdd(&m.ctr->seeds, 1u);
-      const bool lower_only = !obs || (((de < 0.0f) == neg) && fabsf(Df) <= fabsf(de));
-      m.esdf[vid] = ew_pack(Df, kObserved | kFixed, kNoParent);
+      const bool lower_only = !obs || (((de < 0.0f) == neg) && fabsf(seedv) <= fabsf(de));
+      m.esdf[vid] = ew_pack(seedv, kObserved | kFixed, kNoParent);
       if (!lower_only) {
         set_bit(m.rbits0, vid);
         activate(ctl->ract0, &ctl->rcnt[0], m.bstamp_r, slot, e0, mi);

@@ -121,6 +121,7 @@ struct DevMap {
   int B, blog, b3log;
   int tile_shift;  // log2 of the ESDF tiles per block: 3 for B = 16 (8^3 octants), else 0
   int weighting, grouped;
+  int esdf_mode;  // 0: fixed band |D| < gamma; 1: occupancy (D < 0 occupied at distance 0)
   // block hash
   unsigned long long* hkeys;
   uint32_t* hvals;

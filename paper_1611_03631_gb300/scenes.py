@@ -38,6 +38,8 @@ __all__ = [
     "room",
     "lidar_terrain",
     "random_queries",
+    "esdf_benchmark",
+    "esdf_benchmark_sdf",
     "make_scene",
 ]
 
@@ -574,5 +576,89 @@ def batch_mix(n_maps: int = 64, frames: int = 4, seed: int = 4, kinds=("room", "
     return [_mix_one(x) for x in specs]
 
 
+# --------------------------------------------------------------------------------------
+# scene 4: the simulated ESDF benchmark of Sec. VI-B (three planes, a sphere and a cube in a
+# 10 x 10 x 10 m space; noiseless RGB-D from random free-space poses)
+
+_EB_SPHERE = (np.array([6.5, 4.0, 2.0]), 1.5)
+_EB_CUBE = (np.array([2.0, 5.5, 0.0]), np.array([4.0, 7.5, 2.0]))  # lo, hi (resting on the ground)
+
+
+def esdf_benchmark_sdf(x: np.ndarray) -> np.ndarray:
+    """True signed distance of the ESDF benchmark scene (positive in free space): the union of
+    the ground z = 0, the walls x = 0 and y = 10, the sphere and the cube."""
+    x = np.asarray(x, np.float64)
+    d = np.minimum(np.minimum(x[..., 2], x[..., 0]), 10.0 - x[..., 1])
+    c, r = _EB_SPHERE
+    d = np.minimum(d, np.linalg.norm(x - c, axis=-1) - r)
+    lo, hi = _EB_CUBE
+    ctr, half = (lo + hi) / 2.0, (hi - lo) / 2.0
+    q = np.abs(x - ctr) - half
+    box = np.linalg.norm(np.maximum(q, 0.0), axis=-1) + np.minimum(np.max(q, axis=-1), 0.0)
+    return np.minimum(d, box)
+
+
+def _random_rotation(rng: np.random.Generator) -> np.ndarray:
+    q = rng.normal(size=4)
+    q /= np.linalg.norm(q)
+    w, x, y, z = q
+    return np.array(
+        [
+            [1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+            [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+            [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)],
+        ]
+    )
+
+
+def esdf_benchmark(
+    poses: int = 50,
+    width: int = 320,
+    height: int = 240,
+    fx: float = 262.5,
+    voxel_size: float = 0.10,
+    max_depth: float = 5.0,
+    min_clearance: float = 1.0,
+    seed: int = 4,
+) -> ScanSet:
+    """Noiseless 320x240 depth images from `poses` random 6-DoF poses at least
+    `min_clearance` from every obstacle, depth beyond `max_depth` invalid. Map: B = 8,
+    delta = 4 v, constant weight, d_max = 2 m, gamma = v (the one-voxel band)."""
+    rng = np.random.default_rng(seed)
+    dirs = _pinhole_dirs(width, height, fx, fx, (width - 1) / 2.0, (height - 1) / 2.0)
+    dn = dirs / np.linalg.norm(dirs, axis=1, keepdims=True)
+    pts, Ts = [], []
+    while len(pts) < poses:
+        pos = rng.uniform(0.0, 10.0, 3)
+        if esdf_benchmark_sdf(pos[None])[0] < min_clearance:
+            continue
+        R = _random_rotation(rng)
+        uw = dn @ R.T
+        o = np.broadcast_to(pos, uw.shape)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            tx = np.where(uw[:, 0] < 0, -o[:, 0] / uw[:, 0], np.inf)  # wall x = 0
+            ty = np.where(uw[:, 1] > 0, (10.0 - o[:, 1]) / uw[:, 1], np.inf)  # wall y = 10
+        t = np.minimum(_hit_plane_z(o, uw), np.minimum(tx, ty))
+        t = np.minimum(t, _hit_sphere(o, uw, *_EB_SPHERE))
+        t = np.minimum(t, _hit_box_outside(o, uw, *_EB_CUBE))
+        depth = t * dn[:, 2]
+        p = dn * t[:, None]
+        p[~(np.isfinite(t) & (depth <= max_depth))] = np.nan
+        pts.append(p.astype(np.float32))
+        Ts.append(_pose(R, pos))
+    v = float(voxel_size)
+    params = dict(
+        voxel_size=v,
+        voxels_per_block=8,
+        truncation=4.0 * v,
+        max_esdf_dist=2.0,
+        weighting=0,
+        eps=v,
+        fixed_band=v,
+        max_range=math.inf,
+    )
+    return ScanSet("esdf_benchmark", pts, Ts, params)
+
+
 def make_scene(name: str, **kw) -> ScanSet:
-    return {"plane_sphere": plane_sphere, "room": room, "lidar_terrain": lidar_terrain}[name](**kw)
+    return {"plane_sphere": plane_sphere, "room": room, "lidar_terrain": lidar_terrain, "esdf_benchmark": esdf_benchmark}[name](**kw)

@@ -45,6 +45,7 @@ class vbx_map_options(ctypes.Structure):
         ("block_capacity", ctypes.c_int64),
         ("max_points", ctypes.c_int64),
         ("scratch_blocks", ctypes.c_int64),
+        ("esdf_mode", ctypes.c_int),
     ]
 
 
@@ -205,6 +206,7 @@ class Map:
         block_capacity: int = 0,
         max_points: int = 0,
         scratch_blocks: int = 0,
+        esdf_mode: int = 0,
     ):
         import torch
 
@@ -222,6 +224,7 @@ class Map:
         o.block_capacity = int(block_capacity)
         o.max_points = int(max_points)
         o.scratch_blocks = int(scratch_blocks)
+        o.esdf_mode = int(esdf_mode)
         h = ctypes.c_void_p()
         _check(self._lib.vbx_create_map(voxel_size, voxels_per_block, truncation, max_esdf_dist, ctypes.byref(o), ctypes.byref(h)))
         self._h = h

@@ -105,12 +105,13 @@ def test_integration_is_deterministic(vbx):
 # ------------------------------------------------------------------------------ ESDF
 
 
-def _esdf_same_input(vbx, s, frames):
+def _esdf_same_input(vbx, s, frames, **esdf_opts):
     """GPU and oracle (float32 ESDF mode) run the ESDF update on identical float32 TSDF
-    values taken from a reference oracle integration: ESDF values must agree bit-exactly."""
+    values taken from a reference oracle integration: ESDF values must agree bit-exactly.
+    esdf_opts (fixed_band, esdf_mode) go to both sides."""
     ref = oracle.OracleMap.from_scene_params(s.params)
-    o32 = oracle.OracleMap.from_scene_params(s.params, esdf_fp32=1)
-    g = vbx.Map.from_scene_params(s.params)
+    o32 = oracle.OracleMap.from_scene_params(s.params, esdf_fp32=1, **esdf_opts)
+    g = vbx.Map.from_scene_params(s.params, **esdf_opts)
     B = s.params["voxels_per_block"]
     v = np.float32(s.params["voxel_size"])
     L = (0.0, v, np.float32(v * np.float32(1.41421356237309515)), np.float32(v * np.float32(1.73205080756887719)))
@@ -119,7 +120,7 @@ def _esdf_same_input(vbx, s, frames):
         ex = ref.export()
         upd = ref.last_updated()
         idx = {tuple(k): j for j, k in enumerate(ex["keys"])}
-        bj = np.array([idx[(x // B, y // B, z // B)] for x, y, z in upd])
+        bj = np.array([idx[(x // B, y // B, z // B)] for x, y, z in upd], dtype=np.int64)
         loc = ((upd[:, 2] % B) * B + (upd[:, 1] % B)) * B + (upd[:, 0] % B)
         D32 = ex["D"][bj, loc].astype(np.float32)
         W32 = ex["W"][bj, loc].astype(np.float32)
@@ -135,7 +136,7 @@ def _esdf_same_input(vbx, s, frames):
         gs, os_ = g.stats(), o32.stats()
         assert gs["seeds"] == os_["seeds"]
         bad, checked = check_parents(gex, B, L)
-        assert bad == 0 and checked > 0
+        assert bad == 0 and (checked > 0 or not obs.any())
     return g, o32
 
 
@@ -147,6 +148,42 @@ def test_esdf_parity_same_tsdf_plane_sphere(vbx):
 def test_esdf_parity_same_tsdf_room(vbx):
     s = scenes.room(frames=3, width=160, height=120, fx=131.25, fy=131.25)
     _esdf_same_input(vbx, s, len(s))
+
+
+def test_esdf_parity_same_tsdf_occupancy_mode(vbx):
+    """The occupancy ESDF of Sec. VI-B (negative TSDF voxels occupied at distance 0)."""
+    s = scenes.room(frames=3, width=160, height=120, fx=131.25, fy=131.25)
+    g, _ = _esdf_same_input(vbx, s, len(s), esdf_mode=1)
+    ex = g.export()
+    obs = (ex["flags"] & 1) > 0
+    assert (ex["d"][obs] >= 0).all()
+
+
+def test_esdf_parity_same_tsdf_half_truncation_band(vbx):
+    """The half-truncation fixed band of Sec. VI-B, |D| < delta / 2."""
+    s = scenes.plane_sphere(frames=4)
+    _esdf_same_input(vbx, s, len(s), fixed_band=0.5 * s.params["truncation"])
+
+
+@pytest.mark.parametrize("method", ["occupancy", "half_band", "one_voxel_band"])
+def test_esdf_parity_same_tsdf_benchmark_scene(vbx, method):
+    """The three ESDF methods of Sec. VI-B on the simulated benchmark scene."""
+    from paper_1611_03631_gb300 import esdf_methods
+
+    s = scenes.esdf_benchmark(poses=5, width=80, height=60, fx=65.625, voxel_size=0.2)
+    _esdf_same_input(vbx, s, len(s), **esdf_methods.method_options(method, s.params))
+
+
+def test_esdf_methods_evaluation_runs(vbx):
+    from paper_1611_03631_gb300 import esdf_methods
+
+    s = scenes.esdf_benchmark(poses=5, width=80, height=60, fx=65.625, voxel_size=0.2)
+    for method in esdf_methods.METHODS:
+        r = esdf_methods.run(s, method)
+        assert r["esdf_voxels_scored"] > 1000
+        assert np.isfinite(r["esdf_mean_abs_err_m"]) and r["esdf_mean_abs_err_m"] < 1.0
+    g = esdf_methods.run(s, "one_voxel_band", grouped=False)
+    assert np.isfinite(g["tsdf_mean_abs_err_m"])
 
 
 def test_esdf_end_to_end_plane_sphere(vbx):

@@ -16,17 +16,23 @@ def _offsets():
     return [(dx, dy, dz) for dx in (-1, 0, 1) for dy in (-1, 0, 1) for dz in (-1, 0, 1) if (dx, dy, dz) != (0, 0, 0)]
 
 
-def brute_esdf(D, W, v, gamma, dmax, fp32=False):
+def brute_esdf(D, W, v, gamma, dmax, fp32=False, occupancy=False):
     """26-connected quasi-Euclidean distance by plain Bellman-Ford sweeps to a fixpoint.
 
-    Sources: observed voxels with |D| < gamma (value |D|). Relaxation runs only into observed,
-    non-fixed voxels of the same TSDF sign. Values are capped at dmax. Unobserved -> NaN."""
+    Sources: observed voxels with |D| < gamma (value |D|); with occupancy=True, observed voxels
+    with D < 0 (value 0, every observed voxel positive). Relaxation runs only into observed,
+    non-fixed voxels of the same sign. Values are capped at dmax. Unobserved -> NaN."""
     dt = np.float32 if fp32 else np.float64
     Df = D.astype(np.float32)
     obs = W > 0
-    sign = np.where(Df >= 0, 1.0, -1.0)
-    fixed = obs & (np.abs(Df) < np.float32(gamma))
-    seed = np.where(Df == 0, 0.0, np.abs(Df).astype(np.float64) if fp32 else np.abs(D))
+    if occupancy:
+        sign = np.ones(D.shape)
+        fixed = obs & (Df < 0)
+        seed = np.zeros(D.shape)
+    else:
+        sign = np.where(Df >= 0, 1.0, -1.0)
+        fixed = obs & (np.abs(Df) < np.float32(gamma))
+        seed = np.where(Df == 0, 0.0, np.abs(Df).astype(np.float64) if fp32 else np.abs(D))
     dist = np.full(D.shape, dt(np.float32(dmax)), dtype=dt)  # the map holds d_max as float32
     dist[fixed] = seed[fixed].astype(dt)
     if fp32:
@@ -180,6 +186,57 @@ def test_incremental_matches_bellman_ford_over_updates(fp32, B):
         W = newW
         grid_to_map(pq, D, W, mask=changed)
         grid_to_map(ff, D, W, mask=changed)
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+def test_occupancy_mode_matches_bellman_ford_over_updates(fp32):
+    """Occupancy ESDF (negative TSDF voxels occupied at distance 0, Sec. VI-B): incremental
+    updates with moved spheres and new voxels equal Bellman-Ford from the occupied voxels."""
+    rng = np.random.default_rng(31 + fp32)
+    v, G, delta, dmax = 0.1, (16, 16, 16), 0.3, 1.2
+    W = (rng.uniform(size=G) > 0.08).astype(np.float64)
+    cs = [rng.uniform(2, 14, 3) for _ in range(3)]
+    rs = list(rng.uniform(1.5, 4.0, 3))
+    D = _spheres_tsdf(G, v, delta, cs, rs) + rng.normal(0, 0.01, G)
+    m = oracle.OracleMap(v, 8, delta, dmax, esdf_fp32=int(fp32), esdf_mode=1)
+    grid_to_map(m, D, W, mask=W > 0)
+    for step in range(5):
+        m.update_esdf()
+        exp = brute_esdf(D, W, v, 0.0, dmax, fp32=fp32, occupancy=True)
+        got, ex = map_to_grid(m, G)
+        both = ~np.isnan(exp)
+        assert np.array_equal(np.isnan(got), np.isnan(exp))
+        assert np.max(np.abs(got[both] - exp[both])) <= (0.0 if fp32 else 1e-12), step
+        assert (got[both] >= 0).all()  # unsigned
+        occ = both & (D.astype(np.float32) < 0)
+        assert (got[occ] == 0).all()
+        full = m.full_esdf()
+        obs = (ex["flags"] & 1) > 0
+        assert np.max(np.abs(full[obs] - ex["d"][obs])) <= (0.0 if fp32 else 1e-12)
+        cs[step % 3] = cs[step % 3] + rng.normal(0, 1.5, 3)
+        newW = np.maximum(W, (rng.uniform(size=G) > 0.5).astype(np.float64))
+        D2 = _spheres_tsdf(G, v, delta, cs, rs) + rng.normal(0, 0.01, G)
+        changed = (newW > 0) & ((W == 0) | (rng.uniform(size=G) < 0.6))
+        D = np.where(changed, D2, D)
+        W = newW
+        grid_to_map(m, D, W, mask=changed)
+
+
+def test_occupancy_single_occupied_voxel_gives_chamfer_ball_from_zero():
+    v, G = 0.1, (16, 16, 16)
+    D = np.full(G, 0.5)
+    D[8, 8, 8] = -0.05  # the one occupied voxel
+    W = np.ones(G)
+    m = oracle.OracleMap(v, 16, 0.5, 10.0, esdf_mode=1)
+    grid_to_map(m, D, W)
+    m.update_esdf()
+    got, _ = map_to_grid(m, G)
+    v32 = float(np.float32(v))
+    for i in range(16):
+        for j in range(16):
+            for k in range(16):
+                a, b, c = sorted([abs(i - 8), abs(j - 8), abs(k - 8)], reverse=True)
+                assert got[i, j, k] == pytest.approx(v32 * (c * SQ3 + (b - c) * SQ2 + (a - b)), abs=1e-12)
 
 
 def test_parent_directions_are_valid():
