@@ -573,6 +573,45 @@ def cpu_baseline(s, qs, budget_s: float = 15.0, max_frames: int = 8):
     }
 
 
+def _oracle_map_worker(args):
+    """One oracle map integrating its first scans and updating the ESDF after each (run in a
+    spawned worker process); returns the scans done and the seconds they took."""
+    s, n_scans = args
+    import oracle
+
+    m = oracle.OracleMap.from_scene_params(s.params)
+    t0 = time.perf_counter()
+    for p, T in list(zip(s.points, s.poses))[:n_scans]:
+        m.integrate(p, T)
+        m.update_esdf()
+    return min(n_scans, len(s.points)), time.perf_counter() - t0
+
+
+def cpu_baseline_batched(sets, scans_per_map: int = 1):
+    """The batched workload on the host cores: one oracle process per core, each running
+    independent maps of the mix (the CPU counterpart of the batched form). A bounded sample:
+    the first scans of as many maps as there are cores; the rate is what all cores sustain
+    when each always has a map to work on (cores x scans / busy core-seconds)."""
+    import multiprocessing as mp
+
+    cores = max(1, len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count() or 1)
+    sample = sets[:cores]
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(min(cores, len(sample))) as pool:
+        res = pool.map(_oracle_map_worker, [(s, scans_per_map) for s in sample], chunksize=1)
+    wall = time.perf_counter() - t0
+    scans = sum(n for n, _ in res)
+    busy = sum(t for _, t in res)
+    return {
+        "value": cores * scans / busy,
+        "unit": "scans/s",
+        "cores": cores,
+        "kind": "oracle",
+        "sample": f"first {scans_per_map} scan(s) of the first {len(sample)} maps of the mix (TSDF + ESDF), one process per core; "
+        f"{scans} scans in {busy:.1f} core-seconds ({wall:.1f} s wall); value = cores x scans / core-seconds",
+    }
+
+
 def run_reference(args):
     dist, rank, ws = _dist_init()
     if rank != 0:
@@ -806,6 +845,8 @@ def run_gpu(args):
     batched = batched_c1 = served = None
     if not args.no_batched:
         batched = run_batched(args, vbx, torch, dev)
+        if not args.no_cpu_baseline and rank == 0:
+            batched["cpu_baseline"] = cpu_baseline_batched(_batch_sets(args.batch_maps))
         batched_c1 = run_batched_plane_sphere(args, vbx, torch, dev)
         # a smaller batch: lower step latency at a lower throughput
         batched_c1["with_32_maps"] = run_batched_plane_sphere(args, vbx, torch, dev, n_maps=32)
