@@ -954,13 +954,31 @@ vbx_status vbx_batch_autotune(vbx_batch_t b, const vbx_scan_in* scans, const vbx
   vbx::Tuning best = b->tune;
   float best_ms = 1e30f;
   vbx_status st = VBX_OK;
+  // one untimed step first: the first step on fresh maps builds them from scratch, the later
+  // ones (the same scans again) see comparable work
+  {
+    float ms = 0.0f;
+    if ((st = time_step(&ms)) != VBX_OK) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return st;
+    }
+  }
+  // a candidate's time is the better of two steps
+  auto time_candidate = [&](float* ms) -> vbx_status {
+    float a = 0.0f, c = 0.0f;
+    vbx_status s2 = time_step(&a);
+    if (s2 == VBX_OK) s2 = time_step(&c);
+    *ms = std::min(a, c);
+    return s2;
+  };
   // coordinate search: traversal grid first, then the cooperative ESDF grid
   const int rays_opts[3] = {8, 16, 32};
   for (int r : rays_opts) {
     b->tune = best;
     b->tune.rays_ctas_per_sm = r;
     float ms = 0.0f;
-    if ((st = time_step(&ms)) != VBX_OK) break;
+    if ((st = time_candidate(&ms)) != VBX_OK) break;
     if (ms < best_ms) {
       best_ms = ms;
       best = b->tune;
@@ -976,7 +994,7 @@ vbx_status vbx_batch_autotune(vbx_batch_t b, const vbx_scan_in* scans, const vbx
       b->tune.esdf_threads = o[0];
       b->tune.esdf_ctas_per_sm = o[1];
       float ms = 0.0f;
-      if ((st = time_step(&ms)) != VBX_OK) break;
+      if ((st = time_candidate(&ms)) != VBX_OK) break;
       if (ms < best_ms) {
         best_ms = ms;
         best = b->tune;

@@ -507,8 +507,13 @@ __device__ __forceinline__ unsigned upper_index(const unsigned* pfx, int n, unsi
   return (unsigned)lo;
 }
 
+// 256-thread CTAs (batches) are held to 6 per SM worth of registers: more tiles in flight
+// per SM outweigh the few spilled registers
+#ifndef VBX_ESDF_MINB_256
+#define VBX_ESDF_MINB_256 6
+#endif
 template <int NT>
-__global__ void __launch_bounds__(NT) k_esdf(const DevMap* __restrict__ maps, int nmaps, EsdfCtl* ctl) {
+__global__ void __launch_bounds__(NT, NT == 256 ? VBX_ESDF_MINB_256 : 1) k_esdf(const DevMap* __restrict__ maps, int nmaps, EsdfCtl* ctl) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ unsigned pfx[kMaxBatch + 1];
   __shared__ unsigned long long cta_pops;
