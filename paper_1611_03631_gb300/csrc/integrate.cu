@@ -684,17 +684,24 @@ __global__ void __launch_bounds__(kThreads, VBX_RAYS_MIN_CTAS) k_integrate_rays(
 }
 
 // ------------------------------------------------------------------------------------ A5
-// Appends vid to a list with one atomic per group of active lanes that append to the same list
-// (lanes of one warp may belong to different maps of a batch).
-__device__ __forceinline__ void append(uint32_t* list, unsigned* count, uint32_t vid) {
+// Appends vid to the scan's updated list and, if `queue`, to the ESDF dirty list: one leader
+// per group of lanes of the same map issues both counter atomics back to back.
+__device__ __forceinline__ void append_updated_dirty(const DevMap& m, uint32_t vid, bool queue) {
   const unsigned active = __activemask();
-  const unsigned peers = __match_any_sync(active, (unsigned long long)(uintptr_t)count);
+  const unsigned peers = __match_any_sync(active, (unsigned long long)(uintptr_t)m.ctr);
+  const unsigned qpeers = peers & __ballot_sync(active, queue);
   const int lane = threadIdx.x & 31;
   const int leader = __ffs(peers) - 1;
-  unsigned base = 0;
-  if (lane == leader) base = atomicAdd(count, (unsigned)__popc(peers));
-  base = __shfl_sync(peers, base, leader);
-  list[base + __popc(peers & ((1u << lane) - 1u))] = vid;
+  const unsigned below = (1u << lane) - 1u;
+  unsigned bu = 0, bd = 0;
+  if (lane == leader) {
+    bu = atomicAdd(&m.ctr->nupdated, (unsigned)__popc(peers));
+    if (qpeers) bd = atomicAdd(&m.ctr->ndirty, (unsigned)__popc(qpeers));
+  }
+  bu = __shfl_sync(peers, bu, leader);
+  bd = __shfl_sync(peers, bd, leader);
+  m.updated[bu + __popc(peers & below)] = vid;
+  if (queue) m.dirty[bd + __popc(qpeers & below)] = vid;
 }
 
 // Touch flags per lane in k_apply: 16 (one 16-byte load) where the scan's records are sparse
@@ -725,11 +732,13 @@ __global__ void __launch_bounds__(kThreads) k_apply(Batch b, unsigned warp_slots
   for (unsigned base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < total; base += stride) {
     const unsigned i = base + lane;
     unsigned mi = 0, v0 = 0, bits = 0;
+    uint32_t slot = 0;
     if (i < total) {
       mi = map_index(pfx, nm, i);
       const DevMap& m = map_of(b, mi);
       const unsigned V = apply_flags_per_lane(m, wide);
-      v0 = (i - pfx[mi]) * V;  // first scratch voxel of this lane
+      v0 = (i - pfx[mi]) * V;  // first scratch voxel of this lane (V voxels of one scratch block)
+      slot = m.slist[v0 >> m.b3log];  // loaded with the flags, not after them
       if (V == 16) {
         uint4* f = reinterpret_cast<uint4*>(m.stouch + v0);
         const uint4 w = *f;
@@ -758,30 +767,31 @@ __global__ void __launch_bounds__(kThreads) k_apply(Batch b, unsigned warp_slots
       const unsigned ob = __shfl_sync(kFull, bits, own);
       const unsigned omi = __shfl_sync(kFull, mi, own);
       const unsigned ov0 = __shfl_sync(kFull, v0, own);
+      const uint32_t oslot = __shfl_sync(kFull, slot, own);
       if (t >= tot) continue;
       int j = 0;  // position of the (n+1)-th set bit of ob
       while (!(ob >> j & 1u) || n-- > 0) ++j;
       const DevMap& m = map_of(b, omi);
       const unsigned sv = ov0 + (unsigned)j;  // scratch voxel
+      const uint32_t vid = (oslot << m.b3log) | (sv & ((1u << m.b3log) - 1u));
+      // the sums, {D, W} and the queue flag are independent loads, issued together
       ulonglong2* a = reinterpret_cast<ulonglong2*>(&m.sacc[4 * (size_t)sv]);
       const ulonglong2 hi = a[0], lo = a[1];
+      const float2 tv = m.tsdf[vid];
+      const uint8_t vf = m.vflags[vid];
       a[0] = make_ulonglong2(0ull, 0ull);
       a[1] = make_ulonglong2(0ull, 0ull);
-      const uint32_t vid = (m.slist[sv >> m.b3log] << m.b3log) | (sv & ((1u << m.b3log) - 1u));
       const float Sw = __fadd_rn(__fmul_rn(__ll2float_rn((long long)hi.x), kAccInvScale),
                                  __fmul_rn(__ll2float_rn((long long)lo.x), kAccLoInvScale));
       const float Swd = __fadd_rn(__fmul_rn(__ll2float_rn((long long)hi.y), kAccInvScale),
                                   __fmul_rn(__ll2float_rn((long long)lo.y), kAccLoInvScale));
-      const float2 tv = m.tsdf[vid];
       // Eq. (3): D <- (W D + sum w d) / (W + sum w), W <- min(W + sum w, W_max)
       const float Wn = __fadd_rn(tv.y, Sw);
       const float D = __fdiv_rn(__fadd_rn(__fmul_rn(tv.y, tv.x), Swd), Wn);
       m.tsdf[vid] = make_float2(D, fminf(Wn, m.wmax));
-      append(m.updated, &m.ctr->nupdated, vid);
-      if (!(m.vflags[vid] & kQueuedForEsdf)) {
-        m.vflags[vid] |= kQueuedForEsdf;
-        append(m.dirty, &m.ctr->ndirty, vid);
-      }
+      const bool queue = !(vf & kQueuedForEsdf);
+      if (queue) m.vflags[vid] = (uint8_t)(vf | kQueuedForEsdf);
+      append_updated_dirty(m, vid, queue);
     }
   }
 }
