@@ -507,13 +507,16 @@ __device__ __forceinline__ unsigned upper_index(const unsigned* pfx, int n, unsi
   return (unsigned)lo;
 }
 
-// 256-thread CTAs (batches) are held to 6 per SM worth of registers: more tiles in flight
-// per SM outweigh the few spilled registers
+// 256- and 128-thread CTAs (batches) are held to 6 and 12 per SM worth of registers: more tiles
+// in flight per SM outweigh the few spilled registers
 #ifndef VBX_ESDF_MINB_256
 #define VBX_ESDF_MINB_256 6
 #endif
+#ifndef VBX_ESDF_MINB_128
+#define VBX_ESDF_MINB_128 12
+#endif
 template <int NT>
-__global__ void __launch_bounds__(NT, NT == 256 ? VBX_ESDF_MINB_256 : 1) k_esdf(const DevMap* __restrict__ maps, int nmaps, EsdfCtl* ctl) {
+__global__ void __launch_bounds__(NT, NT == 256 ? VBX_ESDF_MINB_256 : (NT == 128 ? VBX_ESDF_MINB_128 : 2)) k_esdf(const DevMap* __restrict__ maps, int nmaps, EsdfCtl* ctl) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ unsigned pfx[kMaxBatch + 1];
   __shared__ unsigned long long cta_pops;
@@ -711,6 +714,7 @@ namespace {
 
 const void* esdf_kernel(int threads) {
   switch (threads) {
+    case 128: return (const void*)k_esdf<128>;
     case 256: return (const void*)k_esdf<256>;
     case 512: return (const void*)k_esdf<512>;
     default: return nullptr;

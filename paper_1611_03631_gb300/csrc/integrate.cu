@@ -68,8 +68,11 @@ __device__ __forceinline__ int warp_segments(int nseg, int lane, int* first) {
 // Whether the rays of a launch are cut into segments: only when 32-ray warp tasks would not
 // keep every resident warp busy several times over (then the longest ray of a warp sets the
 // kernel's duration); with plenty of rays each lane walks its whole ray.
+#ifndef VBX_SPLIT_TASKS_PER_WARP
+#define VBX_SPLIT_TASKS_PER_WARP 4
+#endif
 __device__ __forceinline__ bool split_rays(unsigned n, unsigned slots) {
-  return (unsigned long long)n < 32ull * 4ull * slots;
+  return (unsigned long long)n < 32ull * VBX_SPLIT_TASKS_PER_WARP * slots;
 }
 
 // Rays per warp task when rays are split (a power of two in [1, 32]): at most n / slots, so

@@ -49,7 +49,7 @@ struct Tuning {
   int bin_ctas_per_sm;   // CTAs per SM of the point and group kernels
   int apply_ctas_per_sm;
   int esdf_ctas_per_sm;  // resident CTAs per SM of the cooperative ESDF grid
-  int esdf_threads;      // threads per ESDF CTA (256 or 512): one CTA relaxes one tile at a time
+  int esdf_threads;      // threads per ESDF CTA (128, 256 or 512): one CTA relaxes one tile at a time
 };
 // Start point of the batch autotuner (the ESDF grid is clamped to the kernel's occupancy).
 constexpr Tuning kDefaultTuning = {16, 16, 16, 8, 256};
