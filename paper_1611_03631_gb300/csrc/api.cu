@@ -988,7 +988,7 @@ vbx_status vbx_batch_autotune(vbx_batch_t b, const vbx_scan_in* scans, const vbx
     best_ms = 1e30f;
     // (threads per CTA, CTAs per SM) of the cooperative ESDF grid; the grid is clamped to the
     // kernel's occupancy
-    const int esdf_opts[6][2] = {{128, 12}, {256, 4}, {256, 6}, {512, 2}, {512, 4}, {128, 8}};
+    const int esdf_opts[5][2] = {{128, 12}, {128, 8}, {256, 6}, {256, 4}, {512, 2}};
     for (const auto& o : esdf_opts) {
       b->tune = best;
       b->tune.esdf_threads = o[0];
