@@ -516,7 +516,7 @@ __device__ __forceinline__ unsigned upper_index(const unsigned* pfx, int n, unsi
 #define VBX_ESDF_MINB_128 12
 #endif
 template <int NT>
-__global__ void __launch_bounds__(NT, NT == 256 ? VBX_ESDF_MINB_256 : (NT == 128 ? VBX_ESDF_MINB_128 : 2)) k_esdf(const DevMap* __restrict__ maps, int nmaps, EsdfCtl* ctl) {
+__global__ void __launch_bounds__(NT, NT == 256 ? VBX_ESDF_MINB_256 : (NT == 128 ? VBX_ESDF_MINB_128 : (NT == 512 ? 2 : 1))) k_esdf(const DevMap* __restrict__ maps, int nmaps, EsdfCtl* ctl) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ unsigned pfx[kMaxBatch + 1];
   __shared__ unsigned long long cta_pops;
@@ -717,6 +717,7 @@ const void* esdf_kernel(int threads) {
     case 128: return (const void*)k_esdf<128>;
     case 256: return (const void*)k_esdf<256>;
     case 512: return (const void*)k_esdf<512>;
+    case 1024: return (const void*)k_esdf<1024>;
     default: return nullptr;
   }
 }

@@ -49,14 +49,20 @@ struct Tuning {
   int bin_ctas_per_sm;   // CTAs per SM of the point and group kernels
   int apply_ctas_per_sm;
   int esdf_ctas_per_sm;  // resident CTAs per SM of the cooperative ESDF grid
-  int esdf_threads;      // threads per ESDF CTA (128, 256 or 512): one CTA relaxes one tile at a time
+  int esdf_threads;      // threads per ESDF CTA (128 to 1024): one CTA relaxes one tile at a time
 };
 // Start point of the batch autotuner (the ESDF grid is clamped to the kernel's occupancy).
 constexpr Tuning kDefaultTuning = {16, 16, 16, 8, 256};
 // Calls on one map: its ESDF waves activate few tiles per round (about one per SM), so the
 // round time is the latency of one tile's local relaxation; wide CTAs shorten it, and a small
 // grid shortens each round's grid barrier.
-constexpr Tuning kMapTuning = {16, 16, 16, 2, 512};
+#ifndef VBX_MAP_ESDF_THREADS
+#define VBX_MAP_ESDF_THREADS 1024
+#endif
+#ifndef VBX_MAP_ESDF_CTAS
+#define VBX_MAP_ESDF_CTAS 1
+#endif
+constexpr Tuning kMapTuning = {16, 16, 16, VBX_MAP_ESDF_CTAS, VBX_MAP_ESDF_THREADS};
 
 struct LaunchCfg {
   int num_sms;
