@@ -40,8 +40,8 @@ FLUSH_BYTES = 256 << 20  # > 129 MB L2
 # and the SHA-256 prefix of the source file it was captured on: once that source changes the
 # entry no longer matches and the reported traffic is null.
 NCU_TRAFFIC = {
-    # k_esdf<512>, room workload, one scan (dram__bytes_read.sum 2,292,992 + write 256)
-    ("esdf", "esdf.cu", "b97838ee4de72bc7"): 2293248,
+    # k_esdf<1024>, room workload, one scan (dram__bytes_read.sum 2,293,248 + write 512)
+    ("esdf", "esdf.cu", "6701305c164ce8c3"): 2293760,
 }
 KERNEL_SOURCE = {"esdf": "esdf.cu", "integrate_rays": "integrate.cu", "apply": "integrate.cu", "bin_points": "integrate.cu", "query": "query.cu"}
 
