@@ -525,6 +525,19 @@ def _dist_init():
     return None, 0, 1
 
 
+def whole_job_rate(dist, local_ms: float, steps: int, ws: int, device):
+    """The timed region's duration as the maximum over ranks, and the whole-job rate: every
+    rank processed `steps` scans of its own map in that time (replicas, no exchange)."""
+    max_ms = local_ms
+    if dist is not None:
+        import torch
+
+        t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        max_ms = float(t.item())
+    return max_ms, ws * steps / (max_ms / 1000.0)
+
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -738,14 +751,9 @@ def run_gpu(args):
     torch.cuda.synchronize()
     gpu_launches = vbx.total_launches() - launches0 - 0
     clk = clocks.stop()
-    total_ms = float(sum(step_ms))
-    max_ms = total_ms
+    max_ms, value = whole_job_rate(dist, float(sum(step_ms)), args.steps, ws, dev)
     if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        max_ms = float(t.item())
         dist.barrier()
-    value = ws * args.steps / (max_ms / 1000.0)
     m.close()
 
     # ------------------------------------------------------- per-kernel timing pass
@@ -825,12 +833,7 @@ def run_gpu(args):
     me.close()
     h2d = int(np.mean([pin_pts[i].numel() * 4 for i in order[args.warmup:]])) + N_QUERIES * 12
     d2h = N_QUERIES * (4 + 12 + 1)
-    e2e_total = float(sum(e2e_ms))
-    if dist is not None:
-        t = torch.tensor([e2e_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = ws * args.steps / (e2e_total / 1000.0)
+    e2e_total, e2e_value = whole_job_rate(dist, float(sum(e2e_ms)), args.steps, ws, dev)
 
     esdf_cmp = None
     if args.esdf_methods and rank == 0:
