@@ -95,6 +95,8 @@ def _load():
     lib.orc_record_weight.argtypes = [P(orc_params), ctypes.c_float, ctypes.c_float]
     lib.orc_group.restype = i64
     lib.orc_group.argtypes = [P(orc_params), vp, i64, vp, vp, vp, vp, vp, i64]
+    lib.orc_extract_mesh.restype = i64
+    lib.orc_extract_mesh.argtypes = [vp, vp, vp, i64]
     _lib = lib
     return lib
 
@@ -236,6 +238,15 @@ class OracleMap:
         status = np.zeros(n, dtype=np.uint8)
         self._lib.orc_query(self._h, _ptr(q), n, _ptr(dist), _ptr(grad), _ptr(status))
         return dist, grad, status
+
+    def extract_mesh(self):
+        """Triangles of the TSDF iso-surface (reading R12), sorted by (cell, index in cell):
+        cells (n, 4) int32 = cell min-corner voxel and index, verts (n, 3, 3) float32."""
+        n = int(self._lib.orc_extract_mesh(self._h, None, None, 0))
+        cells = np.zeros((max(n, 1), 4), np.int32)
+        verts = np.zeros((max(n, 1), 3, 3), np.float32)
+        self._lib.orc_extract_mesh(self._h, _ptr(cells), _ptr(verts), n)
+        return cells[:n], verts[:n]
 
     def set_tsdf(self, vox: np.ndarray, D: np.ndarray, W: np.ndarray) -> None:
         vox = np.ascontiguousarray(vox, dtype=np.int32).reshape(-1, 3)

@@ -60,6 +60,11 @@
 //      voxels as occupied at distance 0: in that mode (esdf_mode = 1) the seeds are the
 //      observed voxels with fl32(D) < 0, fixed at +0, and every other observed voxel is
 //      positive, so the field is the unsigned quasi-Euclidean distance to occupied voxels.
+//   R12 mesh layer (Sec. III names meshes as a layer built from the TSDF, for display, but
+//      gives no algorithm): marching cells over each cube of 8 observed voxel centres, inside
+//      iff fl32(D) < 0, float32 edge interpolation, ambiguous faces resolved by cutting off
+//      each inside corner, loops longer than 3 fanned around their centroid, normals towards
+//      positive D; triangles keyed by (cell min corner, index in cell). See mesh_cell.
 
 #include <algorithm>
 #include <cmath>
@@ -668,6 +673,132 @@ void query(Map& m, const float* q, int64_t n, double* dist, double* grad, uint8_
 }  // namespace
 
 // ------------------------------------------------------------------------------------------
+// Iso-surface of the TSDF (the mesh layer of Sec. III), reading R12: marching cells over every
+// cube of 8 observed voxel centres, a corner being inside iff fl32(D) < 0. Each edge with a
+// sign change carries the vertex pa + t (pb - pa), t = Da / (Da - Db) (float32). On each face
+// (corners counter-clockwise seen from outside the cube) the edge crossings are joined by
+// directed segments, each with the inside corners on its left: from the edge where the
+// counter-clockwise walk leaves the inside to the edge where it enters it; a face with four
+// crossings cuts off each inside corner by its own segment. Two cells sharing a face see it
+// from opposite sides, so they make the same segments in opposite directions, and the surface
+// is closed and consistently oriented. The segments chain into loops, each starting at its
+// smallest edge, and each loop is emitted against its direction, so that triangle normals
+// (b - a) x (c - a) point towards positive D. A loop of three vertices is one triangle, a
+// longer one a fan of triangles
+// around the float32 mean of its vertices (a fan from a loop vertex could put a triangle inside
+// a cube face, where the neighbouring cell would put its mirror image).
+
+// cube corners c = x + 2 y + 4 z; edges 0-3 along x, 4-7 along y, 8-11 along z
+const int kCubeEdge[12][2] = {{0, 1}, {2, 3}, {4, 5}, {6, 7}, {0, 2}, {1, 3}, {4, 6}, {5, 7}, {0, 4}, {1, 5}, {2, 6}, {3, 7}};
+// faces x = 0, x = 1, y = 0, y = 1, z = 0, z = 1: corners counter-clockwise seen from outside
+const int kCubeFace[6][4] = {{0, 4, 6, 2}, {1, 3, 7, 5}, {0, 1, 5, 4}, {2, 6, 7, 3}, {0, 2, 3, 1}, {4, 5, 7, 6}};
+
+int edge_of(int a, int b) {
+  for (int e = 0; e < 12; ++e)
+    if ((kCubeEdge[e][0] == a && kCubeEdge[e][1] == b) || (kCubeEdge[e][0] == b && kCubeEdge[e][1] == a)) return e;
+  return -1;
+}
+
+struct MeshTri {
+  int32_t cell[4];  // min-corner voxel of the cell, triangle index within the cell
+  float v[9];
+};
+
+// Triangles of one cell (corner values Dc, corner positions pc[8][3]); appends to out.
+void mesh_cell(const float Dc[8], const float pc[8][3], const int32_t cell[3], std::vector<MeshTri>& out) {
+  bool in[8];
+  for (int c = 0; c < 8; ++c) in[c] = Dc[c] < 0.0f;
+  float vx[12][3];
+  bool cross[12];
+  for (int e = 0; e < 12; ++e) {
+    const int a = kCubeEdge[e][0], b = kCubeEdge[e][1];
+    cross[e] = in[a] != in[b];
+    if (cross[e]) {
+      const float t = Dc[a] / (Dc[a] - Dc[b]);
+      for (int k = 0; k < 3; ++k) vx[e][k] = pc[a][k] + t * (pc[b][k] - pc[a][k]);
+    }
+  }
+  // directed segments: next[e] = the edge the surface boundary goes to from crossing edge e
+  int next[12];
+  for (int e = 0; e < 12; ++e) next[e] = -1;
+  for (int f = 0; f < 6; ++f) {
+    int fe[4];  // fe[i]: edge from corner i to corner i + 1 of the face
+    for (int i = 0; i < 4; ++i) fe[i] = edge_of(kCubeFace[f][i], kCubeFace[f][(i + 1) % 4]);
+    int n = 0;
+    for (int i = 0; i < 4; ++i) n += cross[fe[i]] ? 1 : 0;
+    for (int i = 0; i < 4; ++i) {
+      const bool in_i = in[kCubeFace[f][i]], in_n = in[kCubeFace[f][(i + 1) % 4]];
+      if (n == 4) {
+        if (in_i) next[fe[i]] = fe[(i + 3) % 4];  // cut off inside corner i
+      } else if (n == 2 && in_i && !in_n) {  // the walk leaves the inside at fe[i] ...
+        int j = (i + 1) % 4;  // ... and enters it again at the next crossing
+        while (!cross[fe[j]]) j = (j + 1) % 4;
+        next[fe[i]] = fe[j];
+      }
+    }
+  }
+  bool used[12] = {false};
+  int tri_in_cell = 0;
+  auto emit = [&](const float* a, const float* b, const float* c) {
+    MeshTri t;
+    t.cell[0] = cell[0], t.cell[1] = cell[1], t.cell[2] = cell[2], t.cell[3] = tri_in_cell++;
+    for (int q = 0; q < 3; ++q) t.v[q] = a[q], t.v[3 + q] = b[q], t.v[6 + q] = c[q];
+    out.push_back(t);
+  };
+  for (int e0 = 0; e0 < 12; ++e0) {
+    if (!cross[e0] || used[e0]) continue;
+    int loop[12], k = 0;
+    for (int e = e0; k < 12 && !used[e]; e = next[e]) {
+      loop[k++] = e;
+      used[e] = true;
+    }
+    if (k == 3) {
+      emit(vx[loop[0]], vx[loop[2]], vx[loop[1]]);
+    } else {  // a fan around the loop's centroid, which lies inside the cube
+      float cen[3] = {0.0f, 0.0f, 0.0f};
+      for (int i = 0; i < k; ++i)
+        for (int a = 0; a < 3; ++a) cen[a] += vx[loop[i]][a];
+      for (int a = 0; a < 3; ++a) cen[a] = cen[a] / (float)k;
+      for (int i = 0; i < k; ++i) emit(cen, vx[loop[(i + 1) % k]], vx[loop[i]]);
+    }
+  }
+}
+
+std::vector<MeshTri> extract_mesh(Map& m) {
+  const Params& p = m.p;
+  std::vector<Key3> keys;
+  for (auto& kv : m.blocks) keys.push_back(kv.first);
+  std::sort(keys.begin(), keys.end());
+  std::vector<MeshTri> out;
+  const float v = p.v;
+  for (const Key3& bk : keys) {
+    for (int l = 0; l < m.B3(); ++l) {
+      const Key3 c0{bk.x * p.B + l % p.B, bk.y * p.B + (l / p.B) % p.B, bk.z * p.B + l / (p.B * p.B)};
+      float Dc[8], pc[8][3];
+      bool ok = true;
+      for (int c = 0; c < 8 && ok; ++c) {
+        const Key3 q{c0.x + (c & 1), c0.y + ((c >> 1) & 1), c0.z + ((c >> 2) & 1)};
+        TsdfVoxel* t = m.tsdf_at(q);
+        if (!t || !(t->W > 0.0)) {
+          ok = false;
+          break;
+        }
+        Dc[c] = (float)t->D;
+        const int32_t qi[3] = {q.x, q.y, q.z};
+        for (int a = 0; a < 3; ++a) pc[c][a] = ((float)qi[a] + 0.5f) * v;  // voxel centre
+      }
+      if (!ok) continue;
+      const int32_t cell[3] = {c0.x, c0.y, c0.z};
+      mesh_cell(Dc, pc, cell, out);
+    }
+  }
+  std::sort(out.begin(), out.end(), [](const MeshTri& a, const MeshTri& b) {
+    return std::lexicographical_compare(a.cell, a.cell + 4, b.cell, b.cell + 4);
+  });
+  return out;
+}
+
+// ------------------------------------------------------------------------------------------
 // C interface used by the tests (ctypes).
 
 extern "C" {
@@ -864,6 +995,18 @@ int64_t orc_group(const orc_params* op, const float* pts, int64_t n, const float
     count[i] = g.n;
   }
   return (int64_t)gs.size();
+}
+
+// Mesh of the TSDF (R12): writes min(n, cap) triangles sorted by (cell, index in cell):
+// cells cap x 4 int32 (cell min corner, index), verts cap x 9 float32; returns n.
+int64_t orc_extract_mesh(void* h, int32_t* cells, float* verts, int64_t cap) {
+  std::vector<MeshTri> tris = extract_mesh(*(Map*)h);
+  const int64_t n = (int64_t)tris.size();
+  for (int64_t i = 0; i < n && i < cap; ++i) {
+    std::memcpy(cells + 4 * i, tris[i].cell, sizeof(tris[i].cell));
+    std::memcpy(verts + 9 * i, tris[i].v, sizeof(tris[i].v));
+  }
+  return n;
 }
 
 }  // extern "C"
