@@ -1,7 +1,7 @@
 /* vbx.h -- C ABI of the GB300 (sm_103a) per-scan map update of Voxblox
  * (Oleynikova et al., arXiv 1611.03631): grouped-raycast TSDF fusion into a block-hashed
- * map, the incremental ESDF update from the changed TSDF voxels, and trilinear
- * distance/gradient queries.
+ * map, the incremental ESDF update from the changed TSDF voxels, trilinear
+ * distance/gradient queries, and the incremental mesh of the TSDF iso-surface.
  *
  * Conventions for every entry point:
  *  - All pointers named *_dev are device pointers (CUDA global memory) owned by the caller;
@@ -39,7 +39,9 @@ typedef enum {
   VBX_ERR_OUT_OF_MEMORY = 2, /* device allocation failed or the block pool is exhausted */
   VBX_ERR_HASH_FULL = 3,     /* block hash probe limit reached */
   VBX_ERR_TIMEOUT = 4,       /* a device loop exceeded its round budget or a wait its limit */
-  VBX_ERR_CUDA = 5           /* a CUDA runtime call failed (message in vbx_last_error) */
+  VBX_ERR_CUDA = 5,          /* a CUDA runtime call failed (message in vbx_last_error) */
+  VBX_ERR_CAPACITY = 6       /* an output buffer is too small: the sizes needed are reported
+                                and the map is unchanged                                     */
 } vbx_status;
 
 /* Map options (Sec. IV-A weighting, Sec. IV-B merging, Sec. V-A fixed band). */
@@ -175,6 +177,47 @@ vbx_status vbx_export_updated(vbx_map_t map, int32_t* vox, int64_t cap, int64_t*
  * Duplicate voxels in one call are not allowed. Synchronises `stream`. */
 vbx_status vbx_import_tsdf(vbx_map_t map, const int32_t* vox, const float* D, const float* W, int64_t n,
                            void* stream);
+
+/* One block of an extracted mesh: its key (the block holds voxels key*B .. key*B + B - 1 on
+   each axis), the number of triangles of the cells whose minimum corner it holds, and the
+   index of the first of them in the triangle arrays (a block's triangles are contiguous). */
+typedef struct {
+  int32_t key[3];
+  uint32_t num_triangles;
+  int64_t first_triangle;
+} vbx_mesh_block;
+
+/* Iso-surface D = 0 of the TSDF as triangles: the mesh layer that Sec. III builds from updated
+   TSDF voxels on demand (marching cubes, Sec. II; the paper fixes no variant, so this is the
+   rule below).
+   A cell is the cube between 8 neighbouring voxel centres, ((float)index + 0.5f) * voxel_size;
+   it is meshed when all 8 voxels are observed (W > 0) and belongs to the block holding its
+   minimum corner. A corner is inside when D < 0 (so -0 and +0 are outside). Every cube edge
+   whose ends differ carries the vertex pa + t (pb - pa), t = Da / (Da - Db), each float32
+   operation rounded to nearest. On each face the crossings are joined so that the inside
+   corners lie to the left of the boundary walked counter-clockwise seen from outside; a face
+   with four crossings cuts off each inside corner alone. The joined segments form loops (each
+   started at its lowest-numbered edge: edges 0-3 along x, 4-7 along y, 8-11 along z, corner
+   c = x + 2y + 4z); a loop of 3 vertices is one triangle, a loop of k > 3 the k triangles
+   (centroid, vertex i+1, vertex i) around the float32 mean of its vertices. Triangles are wound
+   so that (b - a) x (c - a) points to positive D. The surface is closed wherever it stays
+   inside observed space, and neighbouring cells share its edges with opposite directions.
+   updated_only = 0 meshes every block. updated_only = 1 meshes only the blocks whose mesh may
+   have changed since the last successful call: those with a cell that has a voxel in a block
+   that a scan's rays entered or vbx_import_tsdf wrote since then. A caller that keeps the
+   meshes per block replaces the listed blocks' meshes with the returned ones (a listed block
+   with no triangles has none). vbx_reset_map clears every mark.
+   Outputs, device memory, blocks in any order:
+     cells_dev  int32 [tri_cap][4], 16-byte aligned: the cell's minimum-corner voxel (x, y, z)
+                and the triangle's index within the cell;
+     verts_dev  float32 [tri_cap][3][3]: vertices a, b, c in world coordinates;
+     blocks_dev vbx_mesh_block [block_cap].
+   *n_tri_out and *n_blocks_out receive the sizes needed. If either exceeds its capacity the
+   call returns VBX_ERR_CAPACITY, the outputs are incomplete and no mark is cleared, so a call
+   with larger buffers returns the same set. Synchronises the stream. */
+vbx_status vbx_extract_mesh(vbx_map_t map, int updated_only, int32_t* cells_dev, float* verts_dev, int64_t tri_cap,
+                            vbx_mesh_block* blocks_dev, int64_t block_cap, int64_t* n_tri_out, int64_t* n_blocks_out,
+                            void* stream);
 
 /* Per-kernel timing with CUDA events recorded on the launch stream around each kernel of
  * this map (off by default). */

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libvbx.so")
-SOURCES = ["api.cu", "integrate.cu", "esdf.cu", "query.cu"]
+SOURCES = ["api.cu", "integrate.cu", "esdf.cu", "query.cu", "mesh.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -17,9 +17,10 @@
 #include "vbx_internal.cuh"
 
 namespace vbx {
-const char* const kKernelNames[kNumKernels] = {"reset_counters", "bin_points", "group_rays",   "link_blocks",
-                                               "integrate_rays", "apply",      "esdf",         "query",
-                                               "import_alloc",   "import_set", "init_groups"};
+const char* const kKernelNames[kNumKernels] = {"reset_counters", "bin_points",  "group_rays",  "link_blocks",
+                                               "integrate_rays", "apply",       "esdf",        "query",
+                                               "import_alloc",   "import_set",  "init_groups", "mesh_select",
+                                               "mesh_blocks",    "mesh_clear"};
 }  // namespace vbx
 
 namespace {
@@ -339,6 +340,8 @@ vbx_status vbx_create_map(float voxel_size, int voxels_per_block, float truncati
   VBX_ALLOC(d.updated, V, 0);
   VBX_ALLOC(d.dirty, V, 0);
   VBX_ALLOC(d.newblk, (size_t)cap, 0);
+  VBX_ALLOC(d.mdirty, (size_t)cap, 0);
+  VBX_ALLOC(d.mlist, (size_t)cap, 0);
   VBX_ALLOC(d.ctr, 1, 0);
   VBX_ALLOC(m->d_dev, 1, 0);
   VBX_ALLOC(m->ctl_dev, 1, 0);
@@ -605,6 +608,46 @@ vbx_status vbx_import_tsdf(vbx_map_t m, const int32_t* vox, const float* D, cons
   if (e != cudaSuccess) return cuda_fail(e, "import launch");
   if (e2 != cudaSuccess) return cuda_fail(e2, "import sync");
   return read_error(m, s);
+}
+
+static_assert(sizeof(vbx_mesh_block) == sizeof(vbx::MeshBlockRec), "vbx_mesh_block layout");
+static_assert(offsetof(vbx_mesh_block, first_triangle) == offsetof(vbx::MeshBlockRec, first), "vbx_mesh_block layout");
+
+vbx_status vbx_extract_mesh(vbx_map_t m, int updated_only, int32_t* cells, float* verts, int64_t tri_cap,
+                            vbx_mesh_block* blocks, int64_t block_cap, int64_t* n_tri_out, int64_t* n_blocks_out,
+                            void* stream) {
+  if (!m || !n_tri_out || !n_blocks_out) return fail(VBX_ERR_INVALID_ARG, "map or an output count is NULL");
+  if (tri_cap < 0 || block_cap < 0) return fail(VBX_ERR_INVALID_ARG, "negative capacity");
+  if (tri_cap > 0 && (!cells || !verts)) return fail(VBX_ERR_INVALID_ARG, "triangle buffers are NULL");
+  if (block_cap > 0 && !blocks) return fail(VBX_ERR_INVALID_ARG, "block buffer is NULL");
+  if (((uintptr_t)cells & 15u) || ((uintptr_t)blocks & 7u) || ((uintptr_t)verts & 3u))
+    return fail(VBX_ERR_INVALID_ARG, "cells_dev must be 16-byte aligned (blocks_dev 8, verts_dev 4)");
+  const cudaStream_t s = (cudaStream_t)stream;
+  const size_t off = offsetof(vbx::Counters, mesh_tris);
+  cudaError_t e = cudaMemsetAsync((char*)m->d.ctr + off, 0, sizeof(vbx::Counters) - off, s);
+  if (e != cudaSuccess) return cuda_fail(e, "clear mesh counters");
+  vbx::MeshOut o;
+  o.cells = reinterpret_cast<int4*>(cells);
+  o.verts = verts;
+  o.tri_cap = (unsigned long long)tri_cap;
+  o.blocks = reinterpret_cast<vbx::MeshBlockRec*>(blocks);
+  o.block_cap = (unsigned long long)block_cap;
+  if ((e = vbx::launch_mesh(m->d, updated_only == 0, o, m->cfg(stream), &m->hook)) != cudaSuccess)
+    return cuda_fail(e, "mesh launch");
+  vbx_status st = read_error(m, s);  // synchronises the stream
+  if (st != VBX_OK) return st;
+  unsigned long long ntri = 0;
+  unsigned nblk = 0;
+  if ((e = cudaMemcpy(&ntri, &m->d.ctr->mesh_tris, sizeof(ntri), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+      (e = cudaMemcpy(&nblk, &m->d.ctr->mesh_blocks, sizeof(nblk), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(e, "read mesh sizes");
+  *n_tri_out = (int64_t)ntri;
+  *n_blocks_out = (int64_t)nblk;
+  if ((int64_t)ntri > tri_cap || (int64_t)nblk > block_cap)
+    return fail(VBX_ERR_CAPACITY, "mesh needs %llu triangles and %u blocks (capacities %lld, %lld)", ntri, nblk,
+                (long long)tri_cap, (long long)block_cap);
+  if ((e = vbx::launch_mesh_clear(m->d, m->cfg(stream), &m->hook)) != cudaSuccess) return cuda_fail(e, "mesh clear");
+  return VBX_OK;
 }
 
 vbx_status vbx_set_profiling(vbx_map_t m, int enable) {
@@ -1063,7 +1106,8 @@ vbx_status vbx_map_bytes(int B, const vbx_map_options* opt_in, int64_t* out) {
   const uint64_t scr = opt.scratch_blocks > 0 ? std::min<uint64_t>((uint64_t)opt.scratch_blocks, cap) : cap;
   uint64_t bytes = 0;
   bytes += H * (8 + 4 + 4);                               // block hash, scratch claims
-  bytes += cap * (12 + 27 * 4 + 8 + 4);                   // block coords, links, scratch index/epoch, new list
+  bytes += cap * (12 + 27 * 4 + 8 + 4 + 1 + 4);           // block coords, links, scratch index/epoch, new list,
+                                                          // mesh marks and list
   bytes += V * (8 + 8 + 1 + 4 + 4);                       // tsdf, esdf, flags, updated and dirty lists
   bytes += scr * (4 + 4) + scr * B3 * (32 + 1);           // scratch blocks: lists, sums, touch flags
   bytes += 4 * (V / 32) * 4;                              // frontier bitmasks

@@ -5,7 +5,8 @@
 //                           the ray and lock-free insertion of its blocks into the block hash,
 //                           and a per-scan scratch block for every block the ray enters
 //   k_link_blocks    A3     26-neighbour links of the new blocks (O(1) neighbour access later);
-//                           pool slot <-> scratch block of the blocks entered this scan
+//                           pool slot <-> scratch block of the blocks entered this scan, whose
+//                           meshes it marks stale
 //   k_integrate_rays A4     voxel-level integer DDA; Eq. (1) distance, Eq. (2)/(4) weight;
 //                           per-voxel sums of w and w*d as exact two-part fixed point numbers
 //                           with integer atomics into the scratch blocks, pre-aggregated across
@@ -469,7 +470,10 @@ __global__ void __launch_bounds__(kThreads) k_link_blocks(Batch b) {
       const unsigned i = u - nl;
       const uint32_t slot = __ldcg(&m.hvals[m.slist_h[i]]);
       m.slist[i] = slot;
-      if (slot < m.cap_blocks) m.sinfo[slot] = ((unsigned long long)scan_of(b, mi).epoch << 32) | i;
+      if (slot < m.cap_blocks) {
+        m.sinfo[slot] = ((unsigned long long)scan_of(b, mi).epoch << 32) | i;
+        m.mdirty[slot] = 1u;  // the scan may change the block's TSDF: its mesh is stale
+      }
       continue;
     }
     const uint32_t p = m.newblk[u / 27u];
@@ -818,6 +822,7 @@ __global__ void __launch_bounds__(kThreads) k_reset_map(DevMap m) {
   for (size_t i = i0; i < nb; i += st) {
     m.bcoord[i] = make_int3(0, 0, 0);
     m.sinfo[i] = 0ull;
+    m.mdirty[i] = 0u;
   }
   for (size_t i = i0; i < nb * 27; i += st) m.nbr[i] = kInvalid;
   for (size_t i = i0; i < tiles; i += st) {
@@ -857,6 +862,7 @@ __global__ void __launch_bounds__(kThreads) k_import_set(DevMap m, const int* __
     const int B = m.B;
     const uint32_t vid = (slot << m.b3log) | (uint32_t)((((z & (B - 1)) << m.blog | (y & (B - 1))) << m.blog) | (x & (B - 1)));
     m.tsdf[vid] = make_float2(D[i], W[i]);
+    m.mdirty[slot] = 1u;
     const unsigned u = atomicAdd(&m.ctr->nupdated, 1u);
     m.updated[u] = vid;
     if (!(m.vflags[vid] & kQueuedForEsdf)) {

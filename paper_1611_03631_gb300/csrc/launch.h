@@ -89,6 +89,9 @@ enum KernelId {
   kKImportAlloc,
   kKImportSet,
   kKInitGroups,
+  kKMeshSelect,
+  kKMeshBlocks,
+  kKMeshClear,
   kNumKernels
 };
 
@@ -115,6 +118,26 @@ size_t esdf_smem_bytes(int max_B);
 int esdf_grid(int num_sms, int max_B, int ctas_per_sm, int threads);
 cudaError_t launch_esdf(const DevMap* maps_dev, int nmaps, int max_B, EsdfCtl* ctl, const LaunchCfg& cfg,
                         LaunchHook* hook);
+
+// mesh.cu: triangles of the TSDF iso-surface, per block
+struct MeshBlockRec {  // same layout as vbx_mesh_block
+  int32_t key[3];
+  uint32_t ntri;
+  long long first;
+};
+struct MeshOut {
+  int4* cells;  // [tri_cap] cell minimum-corner voxel x, y, z and index in the cell
+  float* verts;  // [tri_cap][3][3]
+  unsigned long long tri_cap;
+  MeshBlockRec* blocks;  // [block_cap]
+  unsigned long long block_cap;
+};
+// Lists the blocks to mesh (all, or those with a stale cell) and writes their triangles; the
+// sizes needed are left in the map's counters (mesh_tris, mesh_blocks), cleared beforehand by
+// the caller.
+cudaError_t launch_mesh(const DevMap& m, bool all, const MeshOut& o, const LaunchCfg& cfg, LaunchHook* hook);
+// Drops the stale marks of the blocks the last launch_mesh listed.
+cudaError_t launch_mesh_clear(const DevMap& m, const LaunchCfg& cfg, LaunchHook* hook);
 
 // query.cu: b.queries (or b.one_query) give each map's query points and outputs
 cudaError_t launch_query(const Batch& b, unsigned max_total, const LaunchCfg& cfg, LaunchHook* hook);

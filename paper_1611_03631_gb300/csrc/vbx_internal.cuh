@@ -5,7 +5,9 @@
 //                    hclaim[H] u32 scan epoch of the last scan whose rays entered the block
 //   per block      : bcoord[slot] int3, nbr[slot*27 + k] u32 slot of the neighbour block in
 //                    direction k = (dx+1)*9 + (dy+1)*3 + (dz+1) (k = 13 is the block itself),
-//                    sinfo[slot] u64 {scan epoch << 32 | scratch block} of the block
+//                    sinfo[slot] u64 {scan epoch << 32 | scratch block} of the block,
+//                    mdirty[slot] u8 (TSDF changed since the last mesh extraction),
+//                    mlist[i] u32 blocks listed by the current mesh extraction
 //   per voxel      : voxel id vid = slot * B^3 + ((lz*B + ly)*B + lx)
 //                    tsdf[vid]   float2 (D, W)                          8 B
 //                    esdf[vid]   u64 packed {d f32 | flags u8 | parent u8} 8 B
@@ -92,6 +94,10 @@ struct Counters {
   unsigned int esdf_block_visits;  // staged tile-rounds
   unsigned int esdf_local_iters;   // local relaxation iterations summed over tile-rounds
   unsigned int esdf_phase_ns[3];   // device time of classification, raise and lower phases
+  // ---- per mesh extraction (cleared by vbx_extract_mesh)
+  unsigned long long mesh_tris;    // triangles of the listed blocks
+  unsigned int mesh_blocks;        // blocks listed for meshing
+  unsigned int mesh_pad;
 };
 
 // Control block of one ESDF launch: one map, or a batch of maps updated by the same
@@ -147,6 +153,10 @@ struct DevMap {
   uint32_t* lbits1;
   uint32_t* bstamp_r;
   uint32_t* bstamp_l;
+  // mesh: per block, whether its TSDF may have changed since the last extraction; the blocks
+  // listed by the current extraction
+  uint8_t* mdirty;
+  uint32_t* mlist;
   // lists
   uint32_t* updated;
   uint32_t* dirty;

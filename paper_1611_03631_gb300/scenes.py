@@ -23,6 +23,10 @@ are not available; these stand in for them):
 
 Invalid measurements are emitted as NaN rows so that the map's input filter
 (non-finite points are dropped) sees them.
+
+For the mesh, ``synthetic_tsdf`` stands in for a fused map: per-voxel (D, W) values sampled
+from the ESDF benchmark scene's analytic distance with noise, clipped to the truncation band,
+with unobserved voxels, missing blocks and exact zeros (it is not the fusion of Eq. (1)-(3)).
 """
 from __future__ import annotations
 
@@ -40,6 +44,7 @@ __all__ = [
     "random_queries",
     "esdf_benchmark",
     "esdf_benchmark_sdf",
+    "synthetic_tsdf",
     "make_scene",
 ]
 
@@ -658,6 +663,44 @@ def esdf_benchmark(
         max_range=math.inf,
     )
     return ScanSet("esdf_benchmark", pts, Ts, params)
+
+
+def synthetic_tsdf(
+    lo=(-8, 30, -4),
+    shape=(70, 60, 44),
+    voxel_size: float = 0.1,
+    voxels_per_block: int = 8,
+    truncation: float = 0.4,
+    noise: float = 0.01,
+    p_unobserved: float = 0.05,
+    p_missing_block: float = 0.04,
+    p_zero: float = 0.02,
+    seed: int = 7,
+):
+    """Seeded (vox, D, W) voxels of a truncated distance field over the voxel box
+    [lo, lo + shape): the ESDF benchmark scene's distance at the voxel centres
+    ((i + 1/2) voxel_size) plus N(0, noise) noise, kept where it lies within 1.5 truncation
+    distances and clipped to [-truncation, truncation]; W ~ U(0.5, 4), zero for a fraction
+    p_unobserved of the voxels; whole blocks dropped with probability p_missing_block; a
+    fraction p_zero of the D values set to +0 or -0. Returns int32 (n, 3), float32 (n,),
+    float32 (n,)."""
+    rng = np.random.default_rng(seed)
+    lo = np.asarray(lo, np.int64)
+    idx = np.stack(np.meshgrid(*[np.arange(n) for n in shape], indexing="ij"), -1).reshape(-1, 3) + lo
+    d = esdf_benchmark_sdf((idx + 0.5) * float(np.float32(voxel_size))) + rng.normal(0.0, noise, idx.shape[0])
+    keep = np.abs(d) < 1.5 * truncation
+    idx, d = idx[keep], d[keep]
+    blocks = np.floor_divide(idx, voxels_per_block)
+    ub, inv = np.unique(blocks, axis=0, return_inverse=True)
+    dropped = rng.random(ub.shape[0]) < p_missing_block
+    keep = ~dropped[inv.reshape(-1)]
+    idx, d = idx[keep], d[keep]
+    D = np.clip(d, -truncation, truncation).astype(np.float32)
+    W = rng.uniform(0.5, 4.0, D.shape[0]).astype(np.float32)
+    W[rng.random(D.shape[0]) < p_unobserved] = 0.0
+    z = rng.random(D.shape[0]) < p_zero
+    D[z] = np.where(rng.random(D.shape[0]) < 0.5, np.float32(0.0), np.float32(-0.0))[z]
+    return idx.astype(np.int32), D, W
 
 
 def make_scene(name: str, **kw) -> ScanSet:

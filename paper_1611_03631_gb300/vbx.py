@@ -25,7 +25,12 @@ STATUS_NAMES = {
     3: "VBX_ERR_HASH_FULL",
     4: "VBX_ERR_TIMEOUT",
     5: "VBX_ERR_CUDA",
+    6: "VBX_ERR_CAPACITY",
 }
+VBX_ERR_CAPACITY = 6
+
+# vbx_mesh_block
+MESH_BLOCK_DTYPE = np.dtype([("key", "<i4", (3,)), ("num_triangles", "<u4"), ("first_triangle", "<i8")])
 
 
 class VbxError(RuntimeError):
@@ -125,6 +130,10 @@ _SIGS = {
     "vbx_map_bytes": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(vbx_map_options), ctypes.POINTER(_i64)]),
     "vbx_map_device_bytes": (ctypes.c_int, [_vp, ctypes.POINTER(_i64)]),
     "vbx_reset_map": (ctypes.c_int, [_vp, _vp]),
+    "vbx_extract_mesh": (
+        ctypes.c_int,
+        [_vp, ctypes.c_int, _vp, _vp, _i64, _vp, _i64, ctypes.POINTER(_i64), ctypes.POINTER(_i64), _vp],
+    ),
     "vbx_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, _i64, ctypes.POINTER(_vp)]),
     "vbx_batch_bind": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
     "vbx_batch_step": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp]),
@@ -362,6 +371,43 @@ class Map:
 
     def reset(self, stream=None) -> None:
         _check(self._lib.vbx_reset_map(self._h, _stream_ptr(stream)))
+
+    # -------------------------------------------------------------------- mesh
+    def extract_mesh(self, updated_only: bool = False, stream=None):
+        """Triangles of the TSDF iso-surface (vbx_extract_mesh): every block, or only the blocks
+        whose mesh may have changed since the last call. Returns (cells, verts, blocks): cells an
+        int32 (n, 4) CUDA tensor (cell minimum-corner voxel, index in the cell), verts a float32
+        (n, 3, 3) CUDA tensor, blocks a host array of MESH_BLOCK_DTYPE. cells and verts are views
+        of buffers that the next call on this map overwrites."""
+        import torch
+
+        bufs = getattr(self, "_mesh_bufs", None)
+        nb = max(self.num_blocks(stream), 1)
+        tri_cap = bufs[0].shape[0] if bufs is not None else 1 << 16
+        blk_cap = bufs[2].shape[0] if bufs is not None else 0
+        n_tri, n_blk = ctypes.c_int64(), ctypes.c_int64()
+        for _ in range(2):
+            if bufs is None or bufs[0].shape[0] < tri_cap or bufs[2].shape[0] < blk_cap or blk_cap < nb:
+                blk_cap = max(blk_cap, nb)
+                dev = torch.device("cuda", torch.cuda.current_device())
+                bufs = (
+                    torch.empty((tri_cap, 4), dtype=torch.int32, device=dev),
+                    torch.empty((tri_cap, 3, 3), dtype=torch.float32, device=dev),
+                    torch.empty((blk_cap, 3), dtype=torch.int64, device=dev),
+                )
+                self._mesh_bufs = bufs
+            st = self._lib.vbx_extract_mesh(
+                self._h, 1 if updated_only else 0, bufs[0].data_ptr(), bufs[1].data_ptr(), bufs[0].shape[0],
+                bufs[2].data_ptr(), bufs[2].shape[0], ctypes.byref(n_tri), ctypes.byref(n_blk), _stream_ptr(stream),
+            )
+            if st != VBX_ERR_CAPACITY:
+                break
+            tri_cap = max(tri_cap, int(n_tri.value + n_tri.value // 4 + 1024))
+            blk_cap = max(blk_cap, int(n_blk.value))
+        _check(st)
+        n, m = int(n_tri.value), int(n_blk.value)
+        blocks = np.frombuffer(bufs[2][:m].cpu().numpy().tobytes(), dtype=MESH_BLOCK_DTYPE) if m else np.zeros(0, MESH_BLOCK_DTYPE)
+        return bufs[0][:n], bufs[1][:n], blocks
 
 
 def map_bytes(voxels_per_block: int, block_capacity: int = 0, max_points: int = 0, scratch_blocks: int = 0) -> int:
