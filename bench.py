@@ -42,8 +42,11 @@ FLUSH_BYTES = 256 << 20  # > 129 MB L2
 NCU_TRAFFIC = {
     # k_esdf<1024>, room workload, one scan (dram__bytes_read.sum 2,293,248 + write 512)
     ("esdf", "esdf.cu", "6701305c164ce8c3"): 2293760,
+    # k_mesh_blocks<16>, full mesh of the room map (dram__bytes_read.sum 25,988,096 + write 2,304;
+    # the 17 MB of triangles it writes are still in L2 when it ends)
+    ("mesh_blocks", "mesh.cu", "cbd5b0c8554fc2d5"): 25990400,
 }
-KERNEL_SOURCE = {"esdf": "esdf.cu", "integrate_rays": "integrate.cu", "apply": "integrate.cu", "bin_points": "integrate.cu", "query": "query.cu"}
+KERNEL_SOURCE = {"mesh_blocks": "mesh.cu", "esdf": "esdf.cu", "integrate_rays": "integrate.cu", "apply": "integrate.cu", "bin_points": "integrate.cu", "query": "query.cu"}
 
 
 def _ncu_traffic(kernel: str):
@@ -518,6 +521,7 @@ def run_mesh(args, vbx, torch, dev, s, pts_dev, flush):
             "peak": peak,
             "unit": "GB/s",
             "frac": gbs / peak,
+            "traffic": _ncu_traffic("mesh_blocks"),
             "bytes_per_launch": alg,
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6800 GB/s",
         },

@@ -634,13 +634,13 @@ vbx_status vbx_extract_mesh(vbx_map_t m, int updated_only, int32_t* cells, float
   o.block_cap = (unsigned long long)block_cap;
   if ((e = vbx::launch_mesh(m->d, updated_only == 0, o, m->cfg(stream), &m->hook)) != cudaSuccess)
     return cuda_fail(e, "mesh launch");
-  vbx_status st = read_error(m, s);  // synchronises the stream
-  if (st != VBX_OK) return st;
-  unsigned long long ntri = 0;
-  unsigned nblk = 0;
-  if ((e = cudaMemcpy(&ntri, &m->d.ctr->mesh_tris, sizeof(ntri), cudaMemcpyDeviceToHost)) != cudaSuccess ||
-      (e = cudaMemcpy(&nblk, &m->d.ctr->mesh_blocks, sizeof(nblk), cudaMemcpyDeviceToHost)) != cudaSuccess)
+  vbx::Counters c;  // one copy brings the error word and the sizes
+  if ((e = cudaMemcpyAsync(&c, m->d.ctr, sizeof(c), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess)
     return cuda_fail(e, "read mesh sizes");
+  if (c.error) return read_error(m, s);
+  const unsigned long long ntri = c.mesh_tris;
+  const unsigned nblk = c.mesh_blocks;
   *n_tri_out = (int64_t)ntri;
   *n_blocks_out = (int64_t)nblk;
   if ((int64_t)ntri > tri_cap || (int64_t)nblk > block_cap)

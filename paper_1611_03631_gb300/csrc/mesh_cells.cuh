@@ -17,13 +17,10 @@
 
 namespace vbx {
 
-// Corners at the two ends of edge e.
-__host__ __device__ __forceinline__ int mc_edge_lo(int e) {
-  if (e < 4) return 2 * e;
-  if (e < 8) return ((e - 4) & 1) | (((e - 4) >> 1) << 2);
-  return e - 8;
-}
-__host__ __device__ __forceinline__ int mc_edge_hi(int e) { return mc_edge_lo(e) + (e < 4 ? 1 : e < 8 ? 2 : 4); }
+// Corners at the two ends of edge e (4 bits per edge in a constant: 0,2,4,6 | 0,1,4,5 |
+// 0,1,2,3); the upper one is one step along the edge's axis.
+__host__ __device__ __forceinline__ int mc_edge_lo(int e) { return (int)((0x321054106420ull >> (4 * e)) & 15u); }
+__host__ __device__ __forceinline__ int mc_edge_hi(int e) { return mc_edge_lo(e) + (1 << (e >> 2)); }
 // Axis along which edge e runs.
 __host__ __device__ __forceinline__ int mc_edge_axis(int e) { return e >> 2; }
 
@@ -139,10 +136,13 @@ __host__ __device__ __forceinline__ void mc_vertex(int e, const DF& D, const PF&
   v[2] = ax == 2 ? x : v[2];
 }
 
-// Triangles of one cell with loops L: each loop is emitted against its direction, so that
-// (b - a) x (c - a) points to positive D; a loop of 3 gives one triangle, a loop of k > 3 the
-// k triangles (centroid, vertex i + 1, vertex i), the centroid being the float32 sum of the
-// loop's vertices in loop order divided by k. out(index in cell, a, b, c) receives them.
+// Triangles of one cell with loops L, each vertex evaluated once and handed to
+// out(triangle index in cell, slot 0/1/2 = a/b/c, vertex). Each loop is emitted against its
+// direction, so that (b - a) x (c - a) points to positive D: a loop of 3 edge vertices v0 v1 v2
+// gives the triangle (v0, v2, v1); a loop of k > 3 gives the k triangles
+// (centroid, v[i + 1], v[i]), so v[i] is slot c of triangle i and slot b of triangle i - 1, and
+// the centroid -- the float32 sum of the loop's vertices in loop order, divided by k -- is
+// slot a of all k.
 #pragma nv_exec_check_disable
 template <class DF, class PF, class Sink>
 __host__ __device__ __forceinline__ void mc_emit(const McLoops& L, const DF& D, const PF& P, const Sink& out) {
@@ -153,11 +153,14 @@ __host__ __device__ __forceinline__ void mc_emit(const McLoops& L, const DF& D, 
     const unsigned long long s = L.seq >> (4 * pos);
     pos += k;
     if (k == 3) {
-      float a[3], b[3], c[3];
-      mc_vertex((int)(s & 15u), D, P, a);
-      mc_vertex((int)((s >> 4) & 15u), D, P, b);
-      mc_vertex((int)((s >> 8) & 15u), D, P, c);
-      out(idx++, a, c, b);
+      float w[3];
+      mc_vertex((int)(s & 15u), D, P, w);
+      out(idx, 0, w);
+      mc_vertex((int)((s >> 4) & 15u), D, P, w);
+      out(idx, 2, w);
+      mc_vertex((int)((s >> 8) & 15u), D, P, w);
+      out(idx, 1, w);
+      ++idx;
       continue;
     }
     float cen[3] = {0.0f, 0.0f, 0.0f};
@@ -166,25 +169,13 @@ __host__ __device__ __forceinline__ void mc_emit(const McLoops& L, const DF& D, 
       mc_vertex((int)((s >> (4 * i)) & 15u), D, P, w);
 #pragma unroll
       for (int q = 0; q < 3; ++q) cen[q] = mc_add(cen[q], w[q]);
+      out(idx + i, 2, w);
+      out(idx + (i == 0 ? k - 1 : i - 1), 1, w);
     }
 #pragma unroll
     for (int q = 0; q < 3; ++q) cen[q] = mc_div(cen[q], (float)k);
-    float first[3], prev[3];
-    mc_vertex((int)(s & 15u), D, P, first);
-#pragma unroll
-    for (int q = 0; q < 3; ++q) prev[q] = first[q];
-    for (int i = 0; i < k; ++i) {
-      float nxt[3];
-      if (i + 1 < k) {
-        mc_vertex((int)((s >> (4 * (i + 1))) & 15u), D, P, nxt);
-      } else {
-#pragma unroll
-        for (int q = 0; q < 3; ++q) nxt[q] = first[q];
-      }
-      out(idx++, cen, nxt, prev);
-#pragma unroll
-      for (int q = 0; q < 3; ++q) prev[q] = nxt[q];
-    }
+    for (int i = 0; i < k; ++i) out(idx + i, 0, cen);
+    idx += k;
   }
 }
 

@@ -382,13 +382,11 @@ class Map:
         import torch
 
         bufs = getattr(self, "_mesh_bufs", None)
-        nb = max(self.num_blocks(stream), 1)
         tri_cap = bufs[0].shape[0] if bufs is not None else 1 << 16
-        blk_cap = bufs[2].shape[0] if bufs is not None else 0
+        blk_cap = bufs[2].shape[0] if bufs is not None else 1 << 10
         n_tri, n_blk = ctypes.c_int64(), ctypes.c_int64()
         for _ in range(2):
-            if bufs is None or bufs[0].shape[0] < tri_cap or bufs[2].shape[0] < blk_cap or blk_cap < nb:
-                blk_cap = max(blk_cap, nb)
+            if bufs is None or bufs[0].shape[0] < tri_cap or bufs[2].shape[0] < blk_cap:
                 dev = torch.device("cuda", torch.cuda.current_device())
                 bufs = (
                     torch.empty((tri_cap, 4), dtype=torch.int32, device=dev),
@@ -403,7 +401,7 @@ class Map:
             if st != VBX_ERR_CAPACITY:
                 break
             tri_cap = max(tri_cap, int(n_tri.value + n_tri.value // 4 + 1024))
-            blk_cap = max(blk_cap, int(n_blk.value))
+            blk_cap = max(blk_cap, int(n_blk.value + n_blk.value // 4 + 64))
         _check(st)
         n, m = int(n_tri.value), int(n_blk.value)
         blocks = np.frombuffer(bufs[2][:m].cpu().numpy().tobytes(), dtype=MESH_BLOCK_DTYPE) if m else np.zeros(0, MESH_BLOCK_DTYPE)

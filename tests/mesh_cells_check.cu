@@ -39,16 +39,18 @@ int main() {
     const vbx::McLoops L = vbx::mc_cell_loops(pattern);
     auto D = [&](int c) { return Dc[c]; };
     auto P = [&](int c, int q) { return vbx::mc_mul(vbx::mc_add((float)(g[q] + ((c >> q) & 1)), 0.5f), v); };
+    float tri[12][9];
     int emitted = 0;
-    auto out = [&](int idx, const float* a, const float* b, const float* c) {
-      std::printf("%ld %d", i, idx);
-      for (int q = 0; q < 3; ++q) std::printf(" %08x", to_bits(a[q]));
-      for (int q = 0; q < 3; ++q) std::printf(" %08x", to_bits(b[q]));
-      for (int q = 0; q < 3; ++q) std::printf(" %08x", to_bits(c[q]));
-      std::printf("\n");
-      ++emitted;
+    auto out = [&](int idx, int slot, const float* w) {
+      for (int q = 0; q < 3; ++q) tri[idx][3 * slot + q] = w[q];
+      if (idx + 1 > emitted) emitted = idx + 1;
     };
     vbx::mc_emit(L, D, P, out);
+    for (int t = 0; t < emitted; ++t) {
+      std::printf("%ld %d", i, t);
+      for (int q = 0; q < 9; ++q) std::printf(" %08x", to_bits(tri[t][q]));
+      std::printf("\n");
+    }
     if (emitted != vbx::mc_triangles(L.meta)) {
       std::printf("count mismatch cell %ld: %d emitted, %d in table\n", i, emitted, vbx::mc_triangles(L.meta));
       return 1;
