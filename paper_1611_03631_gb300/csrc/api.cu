@@ -26,6 +26,10 @@ const char* const kKernelNames[kNumKernels] = {"reset_counters", "bin_points",  
 namespace {
 
 thread_local std::string g_last_error;
+
+// Slots of the lower wave's queue ring: every tile once plus 27 pushes in flight per CTA, for the
+// largest grid (32 resident CTAs per SM).
+uint64_t lower_ring_slots(uint64_t tiles, int num_sms) { return tiles + 27ull * 32ull * (uint64_t)(num_sms > 0 ? num_sms : 1); }
 std::atomic<long long> g_total_launches{0};
 
 vbx_status fail(vbx_status s, const char* fmt, ...) {
@@ -352,6 +356,10 @@ vbx_status vbx_create_map(float voxel_size, int voxels_per_block, float truncati
     VBX_ALLOC(ctl.ract1, items, 0);
     VBX_ALLOC(ctl.lact0, items, 0);
     VBX_ALLOC(ctl.lact1, items, 0);
+    const uint64_t ring = lower_ring_slots(items, m->num_sms);
+    ctl.rcap = (unsigned)ring;
+    VBX_ALLOC(ctl.lring, ring, 0);
+    VBX_ALLOC(ctl.ltag, ring, 0);
     if ((e = cudaMemcpy(m->ctl_dev, &ctl, sizeof(ctl), cudaMemcpyHostToDevice)) != cudaSuccess) {
       delete m;
       return cuda_fail(e, "esdf control block");
@@ -441,7 +449,9 @@ vbx_status vbx_update_esdf(vbx_map_t m, void* stream) {
   if (e != cudaSuccess) return cuda_fail(e, "reset esdf counters");
   e = cudaMemsetAsync(m->ctl_dev, 0, offsetof(vbx::EsdfCtl, cap), s);
   if (e != cudaSuccess) return cuda_fail(e, "reset esdf control");
-  e = vbx::launch_esdf(m->d_dev, 1, m->B, m->ctl_dev, m->cfg(stream), &m->hook);
+  // one map: its rounds would hold about one tile per SM, so the lower wave runs as one
+  // asynchronous work queue
+  e = vbx::launch_esdf(m->d_dev, 1, m->B, m->ctl_dev, m->cfg(stream), &m->hook, true);
   if (e != cudaSuccess) return cuda_fail(e, "esdf cooperative launch");
   return VBX_OK;
 }
@@ -756,7 +766,8 @@ vbx_status batch_enqueue(vbx_batch_t b, int k, int flags, cudaStream_t s) {
   if (flags & VBX_STEP_ESDF) {
     if ((e = cudaMemsetAsync(b->ctl_dev, 0, offsetof(vbx::EsdfCtl, cap), s)) != cudaSuccess)
       return cuda_fail(e, "batch esdf reset");
-    if ((e = vbx::launch_esdf(b->maps_dev(), b->count, b->max_B, b->ctl_dev, cfg, &b->hook)) != cudaSuccess)
+    // many maps keep every round full of tiles: the lower wave keeps its rounds
+    if ((e = vbx::launch_esdf(b->maps_dev(), b->count, b->max_B, b->ctl_dev, cfg, &b->hook, false)) != cudaSuccess)
       return cuda_fail(e, "batch esdf");
   }
   if (flags & VBX_STEP_QUERY) {
@@ -896,7 +907,11 @@ vbx_status vbx_batch_create(const vbx_map_t* maps, int count, int64_t max_querie
   };
   vbx::EsdfCtl ctl{};
   ctl.cap = (unsigned)std::min<uint64_t>(cap_sum, UINT32_MAX);
+  const uint64_t ring = lower_ring_slots(cap_sum, b->num_sms);
+  ctl.rcap = (unsigned)std::min<uint64_t>(ring, UINT32_MAX);
   if ((e = dalloc((void**)&b->dev_block, b->block_bytes)) != cudaSuccess ||
+      (e = dalloc((void**)&ctl.lring, ring * sizeof(uint2))) != cudaSuccess ||
+      (e = dalloc((void**)&ctl.ltag, ring * sizeof(unsigned long long))) != cudaSuccess ||
       (e = dalloc((void**)&b->ctl_dev, sizeof(vbx::EsdfCtl))) != cudaSuccess ||
       (e = dalloc((void**)&ctl.ract0, cap_sum * sizeof(uint2))) != cudaSuccess ||
       (e = dalloc((void**)&ctl.ract1, cap_sum * sizeof(uint2))) != cudaSuccess ||
@@ -948,18 +963,25 @@ vbx_status vbx_batch_bind(vbx_batch_t b, int slot, vbx_map_t map) {
     if ((e = cudaMemcpy(&ctl, b->ctl_dev, sizeof(ctl), cudaMemcpyDeviceToHost)) != cudaSuccess)
       return cuda_fail(e, "esdf control");
     if (cap_sum > ctl.cap) {
-      void* lists[4] = {nullptr, nullptr, nullptr, nullptr};
-      for (int i = 0; i < 4; ++i) {
-        if ((e = cudaMalloc(&lists[i], cap_sum * sizeof(uint2))) != cudaSuccess) {
-          for (int j = 0; j < i; ++j) cudaFree(lists[j]);
+      const uint64_t ring = lower_ring_slots(cap_sum, b->num_sms);
+      const size_t bytes[6] = {cap_sum * sizeof(uint2), cap_sum * sizeof(uint2), cap_sum * sizeof(uint2),
+                               cap_sum * sizeof(uint2), ring * sizeof(uint2),    ring * sizeof(unsigned long long)};
+      void* lists[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+      for (int i = 0; i < 6; ++i) {
+        if ((e = cudaMalloc(&lists[i], bytes[i])) != cudaSuccess ||
+            (e = cudaMemset(lists[i], 0, bytes[i])) != cudaSuccess) {
+          for (int j = 0; j <= i; ++j) cudaFree(lists[j]);
           return cuda_fail(e, "esdf lists");
         }
-        b->dev_allocs.push_back(lists[i]);
       }
+      for (int i = 0; i < 6; ++i) b->dev_allocs.push_back(lists[i]);
       ctl.ract0 = (uint2*)lists[0];
       ctl.ract1 = (uint2*)lists[1];
       ctl.lact0 = (uint2*)lists[2];
       ctl.lact1 = (uint2*)lists[3];
+      ctl.lring = (uint2*)lists[4];
+      ctl.ltag = (unsigned long long*)lists[5];
+      ctl.rcap = (unsigned)std::min<uint64_t>(ring, UINT32_MAX);
       ctl.cap = (unsigned)std::min<uint64_t>(cap_sum, UINT32_MAX);
       if ((e = cudaMemcpy(b->ctl_dev, &ctl, sizeof(ctl), cudaMemcpyHostToDevice)) != cudaSuccess)
         return cuda_fail(e, "esdf control");
@@ -1112,6 +1134,14 @@ vbx_status vbx_map_bytes(int B, const vbx_map_options* opt_in, int64_t* out) {
   bytes += scr * (4 + 4) + scr * B3 * (32 + 1);           // scratch blocks: lists, sums, touch flags
   bytes += 4 * (V / 32) * 4;                              // frontier bitmasks
   bytes += tiles * (2 * 4 + 4 * 8);                       // tile stamps, active lists
+  {
+    int dev = 0, sms = 152;  // lower-wave queue ring (this device's SM count, else 152)
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      sms = 152;
+    }
+    bytes += lower_ring_slots(tiles, sms) * (8 + 8);
+  }
   bytes += entries * sizeof(vbx::GroupEntry) + pts * (4 + 16);  // per-scan scratch
   *out = (int64_t)bytes;
   return VBX_OK;

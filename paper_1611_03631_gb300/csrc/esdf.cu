@@ -251,55 +251,153 @@ __device__ __forceinline__ int coords_tile_dir(int x, int y, int z) {
   return (dx + 1) * 9 + (dy + 1) * 3 + (dz + 1);
 }
 
-// Stages tile `item` of map m: its words with the one-voxel halo (one tile row of T words per
-// thread, the S interior words of a row read as 16-byte vectors), and the current frontier bits
-// of its interior (cleared in global memory, appended to the active list).
+// Stages tile `item` of map m: the current frontier bits of its interior (cleared in global
+// memory, appended to the active list), then its words with the one-voxel halo (one tile row of
+// T words per thread, the S interior words of a row read as 16-byte vectors).
 template <int NT, int B, int S>
-__device__ void stage_tile(const DevMap& m, const TileRef& r, uint32_t* cur_bits, const Tile& t) {
+__device__ void stage_tile(const DevMap& m, const TileRef& r, uint32_t* cur_bits, const Tile& t, bool ordered) {
   using G = Geo<B, S>;
   if (threadIdx.x < 27) t.nslot[threadIdx.x] = threadIdx.x == 13 ? r.slot : __ldcg(&m.nbr[(size_t)r.slot * 27 + threadIdx.x]);
   if (threadIdx.x < 8) t.cnt[threadIdx.x] = 0u;
   for (int i = threadIdx.x; i < (G::T3 + 31) / 32; i += NT) t.chg[i] = 0u;
   for (int i = threadIdx.x; i < (2 * G::S3 + 31) / 32; i += NT) t.in[i] = 0u;
   __syncthreads();
-  for (int row = threadIdx.x; row < G::T * G::T; row += NT) {
-    const int y = row % G::T - 1, z = row / G::T - 1;
-    unsigned long long* dst = &t.w[row * G::T];
-    const uint32_t vl = coords_vid<B, S>(t, r, -1, y, z);
-    const uint32_t v0 = coords_vid<B, S>(t, r, 0, y, z);
-    const uint32_t vr = coords_vid<B, S>(t, r, S, y, z);
-    dst[0] = vl == kInvalid ? 0ull : __ldcg(&m.esdf[vl]);
-    if (v0 == kInvalid) {
-#pragma unroll
-      for (int x = 0; x < S; ++x) dst[1 + x] = 0ull;
-    } else {
-      const ulonglong2* src = reinterpret_cast<const ulonglong2*>(&m.esdf[v0]);
-#pragma unroll
-      for (int j = 0; j < S / 2; ++j) {
-        const ulonglong2 v = __ldcg(&src[j]);
-        dst[1 + 2 * j] = v.x;
-        dst[2 + 2 * j] = v.y;
+  auto take_bits = [&]() {
+    // frontier bits: tile row (z, y) = S consecutive bits of the block bitmap, inside one word
+    for (int row = threadIdx.x; row < S * S; row += NT) {
+      const int z = row / S, y = row % S;
+      const uint32_t base = (r.slot << (3 * G::LOGB)) + (uint32_t)((((r.oz + z) << G::LOGB) | (r.oy + y)) << G::LOGB) + r.ox;
+      uint32_t* wp = &cur_bits[base >> 5];
+      const uint32_t mask = ((1u << S) - 1u) << (base & 31);
+      if (!(__ldcg(wp) & mask)) continue;
+      uint32_t chunk = (atomicAnd(wp, ~mask) & mask) >> (base & 31);
+      const unsigned at = atomicAdd(&t.cnt[0], (unsigned)__popc(chunk));
+      unsigned i = at;
+      while (chunk) {
+        const int x = __ffs(chunk) - 1;
+        chunk &= chunk - 1;
+        t.a[i++] = (uint16_t)((((z << G::LOGS) | y) << G::LOGS) | x);
       }
     }
-    dst[S + 1] = vr == kInvalid ? 0ull : __ldcg(&m.esdf[vr]);
-  }
-  // frontier bits: tile row (z, y) = S consecutive bits of the block bitmap, inside one word
-  for (int row = threadIdx.x; row < S * S; row += NT) {
-    const int z = row / S, y = row % S;
-    const uint32_t base = (r.slot << (3 * G::LOGB)) + (uint32_t)((((r.oz + z) << G::LOGB) | (r.oy + y)) << G::LOGB) + r.ox;
-    uint32_t* wp = &cur_bits[base >> 5];
-    const uint32_t mask = ((1u << S) - 1u) << (base & 31);
-    if (!(__ldcg(wp) & mask)) continue;
-    uint32_t chunk = (atomicAnd(wp, ~mask) & mask) >> (base & 31);
-    const unsigned at = atomicAdd(&t.cnt[0], (unsigned)__popc(chunk));
-    unsigned i = at;
-    while (chunk) {
-      const int x = __ffs(chunk) - 1;
-      chunk &= chunk - 1;
-      t.a[i++] = (uint16_t)((((z << G::LOGS) | y) << G::LOGS) | x);
+  };
+  auto load_words = [&]() {
+    for (int row = threadIdx.x; row < G::T * G::T; row += NT) {
+      const int y = row % G::T - 1, z = row / G::T - 1;
+      unsigned long long* dst = &t.w[row * G::T];
+      const uint32_t vl = coords_vid<B, S>(t, r, -1, y, z);
+      const uint32_t v0 = coords_vid<B, S>(t, r, 0, y, z);
+      const uint32_t vr = coords_vid<B, S>(t, r, S, y, z);
+      dst[0] = vl == kInvalid ? 0ull : __ldcg(&m.esdf[vl]);
+      if (v0 == kInvalid) {
+#pragma unroll
+        for (int x = 0; x < S; ++x) dst[1 + x] = 0ull;
+      } else {
+        const ulonglong2* src = reinterpret_cast<const ulonglong2*>(&m.esdf[v0]);
+#pragma unroll
+        for (int j = 0; j < S / 2; ++j) {
+          const ulonglong2 v = __ldcg(&src[j]);
+          dst[1 + 2 * j] = v.x;
+          dst[2 + 2 * j] = v.y;
+        }
+      }
+      dst[S + 1] = vr == kInvalid ? 0ull : __ldcg(&m.esdf[vr]);
     }
+  };
+  if (ordered) {
+    // asynchronous lower wave: the frontier bits are taken before the words are read. A
+    // neighbour writes a voxel's word, fences, then sets its bit, so a bit taken here comes with
+    // a word at least that low.
+    take_bits();
+    __threadfence();
+    __syncthreads();
+    load_words();
+  } else {  // rounds: writers and readers are separated by a grid barrier
+    load_words();
+    take_bits();
   }
   __syncthreads();
+}
+
+// ---- the lower wave's work queue. Tiles are taken one at a time by tickets (qhead); the
+// first n0 tickets are the list that classification and raise built, later ones are tiles
+// pushed while the wave runs, each in ring slot (ticket - n0) mod rcap with a publish tag. A
+// tile is stamped e0 (its map's epoch) while queued and e0 - 1 once taken, so it is queued at
+// most once at a time and is queued again by any write that lands after it was staged.
+constexpr long long kMaxWaitSpins = 1ll << 24;
+
+struct LowerQueue {
+  EsdfCtl* ctl;
+  unsigned n0;  // length of the initial list (lact0)
+  unsigned tag_epoch;  // this launch's call number
+};
+
+__device__ __forceinline__ unsigned long long q_pub_tag(unsigned ep, unsigned h) {
+  return ((unsigned long long)(2u * ep) << 32) | (0x80000000u | (h & 0x7fffffffu));
+}
+__device__ __forceinline__ unsigned long long q_read_tag(unsigned ep, unsigned h) {
+  return ((unsigned long long)(2u * ep + 1u) << 32) | (0x80000000u | (h & 0x7fffffffu));
+}
+
+// Queues tile `item` of map mi unless it is queued already (one thread).
+__device__ void q_push(const LowerQueue& q, unsigned mi, uint32_t item, uint32_t* stamps, unsigned e0) {
+  __threadfence();  // the frontier bits set for this tile are visible before it can be taken
+  if (__ldcg(&stamps[item]) >= e0) return;
+  if (atomicMax(&stamps[item], e0) >= e0) return;
+  EsdfCtl* ctl = q.ctl;
+  const unsigned h = q.n0 + atomicAdd(&ctl->qtail, 1u);
+  const unsigned slot = (h - q.n0) % ctl->rcap;
+  unsigned long long* tag = &ctl->ltag[slot];
+  if (h - q.n0 >= ctl->rcap) {  // the ticket that used this slot before must have been read
+    const unsigned long long want = q_read_tag(q.tag_epoch, h - ctl->rcap);
+    long long spins = 0;
+    while (*(volatile unsigned long long*)tag != want) {
+      if (++spins > kMaxWaitSpins || *(volatile unsigned*)&ctl->error) {
+        atomicOr(&ctl->error, kErrTimeout);
+        return;
+      }
+      __nanosleep(64);
+    }
+  }
+  ctl->lring[slot] = make_uint2(mi, item);
+  __threadfence();
+  atomicExch(tag, q_pub_tag(q.tag_epoch, h));
+  __threadfence();  // the ticket is visible before the pushing tile is counted as finished
+}
+
+// Takes the next ticket (one thread): 1 with the tile in *out, 0 once the queue has drained
+// (every produced ticket finished, so no tile can be queued any more), -1 on error.
+__device__ int q_pop(const LowerQueue& q, uint2* out) {
+  EsdfCtl* ctl = q.ctl;
+  const unsigned h = atomicAdd(&ctl->qhead, 1u);
+  if (h < q.n0) {
+    *out = __ldcg(&ctl->lact0[h]);
+    return 1;
+  }
+  const unsigned slot = (h - q.n0) % ctl->rcap;
+  unsigned long long* tag = &ctl->ltag[slot];
+  const unsigned long long want = q_pub_tag(q.tag_epoch, h);
+  long long spins = 0;
+  for (;;) {
+    if (*(volatile unsigned long long*)tag == want) break;
+    // finished items are read strictly before produced tickets: if every ticket produced so far
+    // had finished when qdone was read, no tile was being processed then, so none can be
+    // queued later (a pushing tile is counted finished only after its tickets are visible)
+    const unsigned done = *(volatile unsigned*)&ctl->qdone;
+    __threadfence();
+    const unsigned made = q.n0 + *(volatile unsigned*)&ctl->qtail;
+    if (done == made && h >= made) return 0;
+    if (*(volatile unsigned*)&ctl->error) return -1;
+    if (++spins > kMaxWaitSpins) {
+      atomicOr(&ctl->error, kErrTimeout);
+      return -1;
+    }
+    __nanosleep(64);
+  }
+  __threadfence();
+  *out = __ldcg(&ctl->lring[slot]);  // L2: the producer's store on another SM
+  __threadfence();
+  atomicExch(tag, q_read_tag(q.tag_epoch, h));
+  return 1;
 }
 
 struct RoundArgs {
@@ -309,6 +407,7 @@ struct RoundArgs {
   uint32_t* nxt_bits;
   uint2* nxt_list;
   unsigned* nxt_cnt;
+  const LowerQueue* q;  // lower wave: where neighbour tiles are queued
 };
 
 // A7 for one staged tile (all threads of the CTA).
@@ -318,7 +417,7 @@ __device__ void raise_tile(const DevMap& m, uint32_t item, uint32_t* cur_bits, c
   using G = Geo<B, S>;
   const Tile t = carve(smem, S);
   const TileRef r = tile_ref<B, S>(item);
-  stage_tile<NT, B, S>(m, r, cur_bits, t);
+  stage_tile<NT, B, S>(m, r, cur_bits, t, false);
   const float dmax = m.dmax;
   unsigned iters = 0;
   for (int it = 0;; ++it) {
@@ -403,7 +502,7 @@ __device__ void lower_tile(const DevMap& m, uint32_t item, uint32_t* cur_bits, c
   using G = Geo<B, S>;
   const Tile t = carve(smem, S);
   const TileRef r = tile_ref<B, S>(item);
-  stage_tile<NT, B, S>(m, r, cur_bits, t);
+  stage_tile<NT, B, S>(m, r, cur_bits, t, ra.q != nullptr);
   const float L1 = m.L1, L2 = m.L2, L3 = m.L3;
   unsigned iters = 0;
   for (int it = 0;; ++it) {
@@ -461,15 +560,33 @@ __device__ void lower_tile(const DevMap& m, uint32_t item, uint32_t* cur_bits, c
     if (!(t.chg[c >> 5] & (1u << (c & 31)))) continue;
     const uint32_t vid = cell_vid<B, S>(t, r, c);
     atomicMin(&m.esdf[vid], t.w[c]);
-    if (!cell_interior<B, S>(c)) {
+    if (ra.q == nullptr && !cell_interior<B, S>(c)) {  // rounds: the bit goes with the value
       set_bit(ra.nxt_bits, vid);
       atomicOr(&t.cnt[3], 1u << cell_tile_dir<B, S>(c));
     }
   }
+  // asynchronous wave: values before frontier bits (a tile that takes a bit must find the word
+  // at least that low), and bits before the pushes of the tiles that own them
+  const bool async = ra.q != nullptr;
+  if (async) {
+    __threadfence();
+    __syncthreads();
+    for (int c = threadIdx.x; c < G::T3; c += NT) {
+      if (!(t.chg[c >> 5] & (1u << (c & 31))) || cell_interior<B, S>(c)) continue;
+      set_bit(ra.nxt_bits, cell_vid<B, S>(t, r, c));
+      atomicOr(&t.cnt[3], 1u << cell_tile_dir<B, S>(c));
+    }
+    __threadfence();
+  }
   __syncthreads();
   if (threadIdx.x < 27 && (t.cnt[3] >> threadIdx.x & 1u)) {
     const uint32_t nit = neighbor_tile_item<B, S>(t, r, threadIdx.x);
-    if (nit != kInvalid) activate(ra.nxt_list, ra.nxt_cnt, m.bstamp_l, nit, ra.ep_next, ra.mi);
+    if (nit != kInvalid) {
+      if (async)
+        q_push(*ra.q, ra.mi, nit, m.bstamp_l, ra.e0);
+      else
+        activate(ra.nxt_list, ra.nxt_cnt, m.bstamp_l, nit, ra.ep_next, ra.mi);
+    }
   }
   __syncthreads();
 }
@@ -516,14 +633,23 @@ __device__ __forceinline__ unsigned upper_index(const unsigned* pfx, int n, unsi
 #define VBX_ESDF_MINB_128 12
 #endif
 template <int NT>
-__global__ void __launch_bounds__(NT, NT == 256 ? VBX_ESDF_MINB_256 : (NT == 128 ? VBX_ESDF_MINB_128 : (NT == 512 ? 2 : 1))) k_esdf(const DevMap* __restrict__ maps, int nmaps, EsdfCtl* ctl) {
+__global__ void __launch_bounds__(NT, NT == 256 ? VBX_ESDF_MINB_256 : (NT == 128 ? VBX_ESDF_MINB_128 : (NT == 512 ? 2 : 1))) k_esdf(const DevMap* __restrict__ maps, int nmaps, EsdfCtl* ctl, int async_lower) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ unsigned pfx[kMaxBatch + 1];
   __shared__ unsigned long long cta_pops;
   __shared__ unsigned sh_item;
+  __shared__ int sh_state;
+  __shared__ uint2 sh_e;
+  __shared__ unsigned long long sh_t[4];  // phase boundaries, taken by thread 0 of each CTA
   const unsigned tid = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned nthreads = gridDim.x * blockDim.x;
-  const unsigned long long t_start = global_ns();
+  if (threadIdx.x == 0) sh_t[0] = global_ns();
+  // the lower queue's ring must hold the initial list's worth plus 27 pushes per CTA in flight
+  if (async_lower && ctl->rcap < ctl->cap + 27u * gridDim.x) {
+    if (tid == 0) atomicOr(&ctl->error, kErrTimeout);
+    return;
+  }
+  if (tid == 0) atomicAdd(&ctl->calls, 1u);  // read by every CTA after the first grid barrier
 
   // ---------------------------------------------------------------- A6: classification
   // exclusive prefix of the maps' dirty counts: warp 0 scans kMaxBatch / 32 counts per lane
@@ -610,7 +736,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? VBX_ESDF_MINB_256 : (NT == 128
     }
   }
   if (!grid_barrier(&ctl->bar, gridDim.x, &ctl->error)) return;
-  const unsigned long long t_classified = global_ns();
+  if (threadIdx.x == 0) sh_t[1] = global_ns();
 
   // ------------------------------------------------------------------------ A7: raise
   unsigned r = 0;
@@ -641,6 +767,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? VBX_ESDF_MINB_256 : (NT == 128
       ra.nxt_bits = (r & 1) ? m.rbits0 : m.rbits1;
       ra.nxt_list = (r & 1) ? ctl->ract0 : ctl->ract1;
       ra.nxt_cnt = &ctl->rcnt[(r + 1) % 3];
+      ra.q = nullptr;
       if (threadIdx.x == 0) cta_pops = 0;
       raise_dispatch<NT>(m, e.y, (r & 1) ? m.rbits1 : m.rbits0, ra, ctl, dsm, &cta_pops);
       if (threadIdx.x == 0) {
@@ -651,52 +778,109 @@ __global__ void __launch_bounds__(NT, NT == 256 ? VBX_ESDF_MINB_256 : (NT == 128
     if (!grid_barrier(&ctl->bar, gridDim.x, &ctl->error)) return;
   }
   const unsigned raise_rounds = r;
-  const unsigned long long t_raised = global_ns();
+  if (threadIdx.x == 0) sh_t[2] = global_ns();
 
   // ------------------------------------------------------------------------ A8: lower
+  // Two schedules reach the same fixpoint (the lower wave is a monotone relaxation: values only
+  // decrease, by global atomicMin, so neither the processing order nor two CTAs working on
+  // neighbouring tiles at once change the result):
+  //  * rounds (batches): all tiles active in a round, then a grid barrier; many maps keep every
+  //    round full of tiles;
+  //  * one asynchronous work queue (single maps, whose rounds hold about one tile per SM): each
+  //    CTA takes a tile, un-stamps it (a write into it from then on queues it again), relaxes it
+  //    to local convergence and queues the neighbour tiles whose voxels it lowered, with no grid
+  //    barrier; the phase ends when every produced ticket has finished.
   unsigned l = 0;
-  for (;; ++l) {
-    const unsigned cnt = __ldcg(&ctl->lcnt[l % 3]);
-    if (cnt == 0 || __ldcg(&ctl->error)) break;
-    if (l >= kMaxRounds) {
-      if (tid == 0) atomicOr(&ctl->error, kErrTimeout);
-      break;
-    }
-    if (tid == 0) {
-      ctl->lcnt[(l + 2) % 3] = 0;
-      ctl->lnext[(l + 2) % 3] = 0;
-    }
-    const uint2* cur = (l & 1) ? ctl->lact1 : ctl->lact0;
+  if (async_lower) {
+    LowerQueue q;
+    q.ctl = ctl;
+    q.n0 = __ldcg(&ctl->lcnt[0]);
+    q.tag_epoch = __ldcg(&ctl->calls);
+    l = q.n0 > 0 ? 1u : 0u;  // reported as one lower "round"
     for (;;) {
-      if (threadIdx.x == 0) sh_item = atomicAdd(&ctl->lnext[l % 3], 1u);
+      if (threadIdx.x == 0) {
+        uint2 e = make_uint2(0u, 0u);
+        const int st = q_pop(q, &e);
+        if (st == 1) {
+          const DevMap& m = maps[e.x];
+          atomicExch(&m.bstamp_l[e.y], __ldcg(&m.ctr->epoch));  // e0 - 1: no longer queued
+          __threadfence();
+        }
+        sh_state = st;
+        sh_e = e;
+      }
       __syncthreads();
-      const unsigned item = sh_item;
+      const int st = sh_state;
+      const uint2 e = sh_e;
+      // the un-stamping is ordered before this CTA's reads of the tile's frontier bits (a
+      // neighbour that sets a bit after those reads then sees the tile as not queued)
+      __threadfence();
       __syncthreads();
-      if (item >= cnt) break;
-      const uint2 e = cur[item];
+      if (st != 1) break;
       const DevMap& m = maps[e.x];
       RoundArgs ra;
       ra.mi = e.x;
       ra.e0 = __ldcg(&m.ctr->epoch) + 1;
-      ra.ep_next = ra.e0 + 1 + l;
-      ra.nxt_bits = (l & 1) ? m.lbits0 : m.lbits1;
-      ra.nxt_list = (l & 1) ? ctl->lact0 : ctl->lact1;
-      ra.nxt_cnt = &ctl->lcnt[(l + 1) % 3];
+      ra.ep_next = ra.e0;
+      ra.nxt_bits = m.lbits0;
+      ra.nxt_list = nullptr;
+      ra.nxt_cnt = nullptr;
+      ra.q = &q;
       if (threadIdx.x == 0) cta_pops = 0;
-      lower_dispatch<NT>(m, e.y, (l & 1) ? m.lbits1 : m.lbits0, ra, ctl, dsm, &cta_pops);
+      lower_dispatch<NT>(m, e.y, m.lbits0, ra, ctl, dsm, &cta_pops);
       if (threadIdx.x == 0) {
         if (cta_pops) atomicAdd(&m.ctr->lower_pops, cta_pops);
         atomicAdd(&m.ctr->esdf_block_visits, 1u);
+        __threadfence();
+        atomicAdd(&ctl->qdone, 1u);
       }
     }
-    if (!grid_barrier(&ctl->bar, gridDim.x, &ctl->error)) return;
+  } else {
+    for (;; ++l) {
+      const unsigned cnt = __ldcg(&ctl->lcnt[l % 3]);
+      if (cnt == 0 || __ldcg(&ctl->error)) break;
+      if (l >= kMaxRounds) {
+        if (tid == 0) atomicOr(&ctl->error, kErrTimeout);
+        break;
+      }
+      if (tid == 0) {
+        ctl->lcnt[(l + 2) % 3] = 0;
+        ctl->lnext[(l + 2) % 3] = 0;
+      }
+      const uint2* cur = (l & 1) ? ctl->lact1 : ctl->lact0;
+      for (;;) {
+        if (threadIdx.x == 0) sh_item = atomicAdd(&ctl->lnext[l % 3], 1u);
+        __syncthreads();
+        const unsigned item = sh_item;
+        __syncthreads();
+        if (item >= cnt) break;
+        const uint2 e = cur[item];
+        const DevMap& m = maps[e.x];
+        RoundArgs ra;
+        ra.mi = e.x;
+        ra.e0 = __ldcg(&m.ctr->epoch) + 1;
+        ra.ep_next = ra.e0 + 1 + l;
+        ra.nxt_bits = (l & 1) ? m.lbits0 : m.lbits1;
+        ra.nxt_list = (l & 1) ? ctl->lact0 : ctl->lact1;
+        ra.nxt_cnt = &ctl->lcnt[(l + 1) % 3];
+        ra.q = nullptr;
+        if (threadIdx.x == 0) cta_pops = 0;
+        lower_dispatch<NT>(m, e.y, (l & 1) ? m.lbits1 : m.lbits0, ra, ctl, dsm, &cta_pops);
+        if (threadIdx.x == 0) {
+          if (cta_pops) atomicAdd(&m.ctr->lower_pops, cta_pops);
+          atomicAdd(&m.ctr->esdf_block_visits, 1u);
+        }
+      }
+      if (!grid_barrier(&ctl->bar, gridDim.x, &ctl->error)) return;
+    }
   }
-  const unsigned long long t_end = global_ns();
+  if (threadIdx.x == 0) sh_t[3] = global_ns();
+  __syncthreads();
   for (unsigned i = tid; i < (unsigned)nmaps; i += nthreads) {
     Counters* c = maps[i].ctr;
-    c->esdf_phase_ns[0] = (unsigned)(t_classified - t_start);
-    c->esdf_phase_ns[1] = (unsigned)(t_raised - t_classified);
-    c->esdf_phase_ns[2] = (unsigned)(t_end - t_raised);
+    c->esdf_phase_ns[0] = (unsigned)(sh_t[1] - sh_t[0]);
+    c->esdf_phase_ns[1] = (unsigned)(sh_t[2] - sh_t[1]);
+    c->esdf_phase_ns[2] = (unsigned)(sh_t[3] - sh_t[2]);
     c->esdf_in = pfx[i + 1] - pfx[i];
     c->raise_rounds = raise_rounds;
     c->lower_rounds = l;
@@ -736,7 +920,7 @@ int esdf_grid(int num_sms, int max_B, int ctas_per_sm, int threads) {
 }
 
 cudaError_t launch_esdf(const DevMap* maps_dev, int nmaps, int max_B, EsdfCtl* ctl, const LaunchCfg& cfg,
-                        LaunchHook* hook) {
+                        LaunchHook* hook, bool async_lower) {
   if (nmaps <= 0 || nmaps > kMaxBatch) return cudaErrorInvalidValue;
   const int threads = cfg.tune.esdf_threads;
   const void* k = esdf_kernel(threads);
@@ -744,7 +928,8 @@ cudaError_t launch_esdf(const DevMap* maps_dev, int nmaps, int max_B, EsdfCtl* c
   const int grid = esdf_grid(cfg.num_sms, max_B, cfg.tune.esdf_ctas_per_sm, threads);
   if (grid <= 0) return cudaErrorCooperativeLaunchTooLarge;
   const size_t smem = esdf_smem_bytes(max_B);
-  void* args[] = {(void*)&maps_dev, (void*)&nmaps, (void*)&ctl};
+  int async = async_lower ? 1 : 0;
+  void* args[] = {(void*)&maps_dev, (void*)&nmaps, (void*)&ctl, (void*)&async};
   hook->begin(kKEsdf, cfg.stream);
   cudaError_t e = cudaLaunchCooperativeKernel(k, dim3(grid), dim3(threads), args, smem, cfg.stream);
   hook->end(kKEsdf, cfg.stream);

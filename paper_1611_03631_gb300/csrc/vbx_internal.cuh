@@ -110,12 +110,23 @@ struct EsdfCtl {
   unsigned int lcnt[3];
   unsigned int rnext[3];  // next unclaimed entry of the round's raise / lower list (CTAs claim
   unsigned int lnext[3];  // tiles one at a time, so a round is not paced by a static split)
+  // lower wave as one asynchronous work queue (no rounds): consumer tickets, tickets produced
+  // beyond the initial list, and items finished
+  unsigned int qhead;
+  unsigned int qtail;
+  unsigned int qdone;
   unsigned int error;
   unsigned int cap;  // capacity of each active list
   uint2* ract0;
   uint2* ract1;
   uint2* lact0;
   uint2* lact1;
+  // lower-wave queue ring (entries past the initial list) and its per-slot publish / read tags;
+  // rcap >= cap + 27 x (largest grid), so a producer never waits on a slot no CTA will read
+  unsigned int rcap;
+  unsigned int calls;  // launches so far (tags carry it, so stale tags never match)
+  uint2* lring;
+  unsigned long long* ltag;
 };
 
 struct DevMap {
@@ -435,7 +446,7 @@ struct DdaSeg {
 
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t) : : "memory");
   return t;
 }
 
