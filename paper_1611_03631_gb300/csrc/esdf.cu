@@ -318,8 +318,9 @@ __device__ void stage_tile(const DevMap& m, const TileRef& r, uint32_t* cur_bits
   __syncthreads();
 }
 
-// ---- the lower wave's work queue. Tiles are taken one at a time by tickets (qhead); the
-// first n0 tickets are the list that classification and raise built, later ones are tiles
+// ---- the work queue of a wave (raise, then lower, for single maps). Tiles are taken one at a
+// time by tickets (qhead); the first n0 tickets are the wave's initial list (built by
+// classification, and for the lower wave also by raise), later ones are tiles
 // pushed while the wave runs, each in ring slot (ticket - n0) mod rcap with a publish tag. A
 // tile is stamped e0 (its map's epoch) while queued and e0 - 1 once taken, so it is queued at
 // most once at a time and is queued again by any write that lands after it was staged.
@@ -327,8 +328,9 @@ constexpr long long kMaxWaitSpins = 1ll << 24;
 
 struct LowerQueue {
   EsdfCtl* ctl;
-  unsigned n0;  // length of the initial list (lact0)
-  unsigned tag_epoch;  // this launch's call number
+  const uint2* init;  // the initial list (raise: ract0, lower: lact0)
+  unsigned n0;        // its length
+  unsigned tag_epoch;  // 2 x this launch's call number + phase (0 raise, 1 lower)
 };
 
 __device__ __forceinline__ unsigned long long q_pub_tag(unsigned ep, unsigned h) {
@@ -370,7 +372,7 @@ __device__ int q_pop(const LowerQueue& q, uint2* out) {
   EsdfCtl* ctl = q.ctl;
   const unsigned h = atomicAdd(&ctl->qhead, 1u);
   if (h < q.n0) {
-    *out = __ldcg(&ctl->lact0[h]);
+    *out = __ldcg(&q.init[h]);
     return 1;
   }
   const unsigned slot = (h - q.n0) % ctl->rcap;
@@ -480,14 +482,23 @@ __device__ void raise_tile(const DevMap& m, uint32_t item, uint32_t* cur_bits, c
     if (!(t.chg[c >> 5] & (1u << (c & 31)))) continue;
     m.esdf[cell_vid<B, S>(t, r, c)] = t.w[c];
   }
-  // activate the tiles that received raise (next round) or lower (seed) frontier bits
+  // activate the tiles that received raise (next round, or the queue) or lower (seed) bits
+  if (ra.q) {  // the raise bits set by any thread precede the pushes' stamp checks
+    __threadfence();
+    __syncthreads();
+  }
   if (threadIdx.x < 27) {
     const int k = threadIdx.x;
     const bool rz = t.cnt[3] >> k & 1u, lz = t.cnt[4] >> k & 1u;
     if (rz || lz) {
       const uint32_t nit = neighbor_tile_item<B, S>(t, r, k);
       if (nit != kInvalid) {
-        if (rz) activate(ra.nxt_list, ra.nxt_cnt, m.bstamp_r, nit, ra.ep_next, ra.mi);
+        if (rz) {
+          if (ra.q)
+            q_push(*ra.q, ra.mi, nit, m.bstamp_r, ra.e0);
+          else
+            activate(ra.nxt_list, ra.nxt_cnt, m.bstamp_r, nit, ra.ep_next, ra.mi);
+        }
         if (lz) activate(ctl->lact0, &ctl->lcnt[0], m.bstamp_l, nit, ra.e0, ra.mi);
       }
     }
@@ -739,43 +750,99 @@ __global__ void __launch_bounds__(NT, NT == 256 ? VBX_ESDF_MINB_256 : (NT == 128
   if (threadIdx.x == 0) sh_t[1] = global_ns();
 
   // ------------------------------------------------------------------------ A7: raise
+  // The raised set is the closure over parent directions from the classified voxels, and
+  // parent directions do not change while the wave runs, so its result does not depend on the
+  // schedule either: rounds for batches, the work queue for single maps (then the queue's
+  // counters are reset between two grid barriers for the lower wave).
   unsigned r = 0;
-  for (;; ++r) {
-    const unsigned cnt = __ldcg(&ctl->rcnt[r % 3]);
-    if (cnt == 0 || __ldcg(&ctl->error)) break;
-    if (r >= kMaxRounds) {
-      if (tid == 0) atomicOr(&ctl->error, kErrTimeout);
-      break;
-    }
-    if (tid == 0) {
-      ctl->rcnt[(r + 2) % 3] = 0;
-      ctl->rnext[(r + 2) % 3] = 0;
-    }
-    const uint2* cur = (r & 1) ? ctl->ract1 : ctl->ract0;
+  if (async_lower) {
+    LowerQueue q;
+    q.ctl = ctl;
+    q.init = ctl->ract0;
+    q.n0 = __ldcg(&ctl->rcnt[0]);
+    q.tag_epoch = 2u * __ldcg(&ctl->calls);
+    r = q.n0 > 0 ? 1u : 0u;  // reported as one raise "round"
     for (;;) {
-      if (threadIdx.x == 0) sh_item = atomicAdd(&ctl->rnext[r % 3], 1u);
+      if (threadIdx.x == 0) {
+        uint2 e = make_uint2(0u, 0u);
+        const int st = q_pop(q, &e);
+        if (st == 1) {
+          const DevMap& m = maps[e.x];
+          atomicExch(&m.bstamp_r[e.y], __ldcg(&m.ctr->epoch));  // e0 - 1: no longer queued
+          __threadfence();
+        }
+        sh_state = st;
+        sh_e = e;
+      }
       __syncthreads();
-      const unsigned item = sh_item;
+      const int st = sh_state;
+      const uint2 e = sh_e;
+      __threadfence();
       __syncthreads();
-      if (item >= cnt) break;
-      const uint2 e = cur[item];
+      if (st != 1) break;
       const DevMap& m = maps[e.x];
       RoundArgs ra;
       ra.mi = e.x;
       ra.e0 = __ldcg(&m.ctr->epoch) + 1;
-      ra.ep_next = ra.e0 + 1 + r;
-      ra.nxt_bits = (r & 1) ? m.rbits0 : m.rbits1;
-      ra.nxt_list = (r & 1) ? ctl->ract0 : ctl->ract1;
-      ra.nxt_cnt = &ctl->rcnt[(r + 1) % 3];
-      ra.q = nullptr;
+      ra.ep_next = ra.e0;
+      ra.nxt_bits = m.rbits0;
+      ra.nxt_list = nullptr;
+      ra.nxt_cnt = nullptr;
+      ra.q = &q;
       if (threadIdx.x == 0) cta_pops = 0;
-      raise_dispatch<NT>(m, e.y, (r & 1) ? m.rbits1 : m.rbits0, ra, ctl, dsm, &cta_pops);
+      raise_dispatch<NT>(m, e.y, m.rbits0, ra, ctl, dsm, &cta_pops);
       if (threadIdx.x == 0) {
         if (cta_pops) atomicAdd(&m.ctr->raise_pops, cta_pops);
         atomicAdd(&m.ctr->esdf_block_visits, 1u);
+        __threadfence();
+        atomicAdd(&ctl->qdone, 1u);
       }
     }
     if (!grid_barrier(&ctl->bar, gridDim.x, &ctl->error)) return;
+    if (tid == 0) {
+      ctl->qhead = 0u;
+      ctl->qtail = 0u;
+      ctl->qdone = 0u;
+    }
+    if (!grid_barrier(&ctl->bar, gridDim.x, &ctl->error)) return;
+  } else {
+    for (;; ++r) {
+      const unsigned cnt = __ldcg(&ctl->rcnt[r % 3]);
+      if (cnt == 0 || __ldcg(&ctl->error)) break;
+      if (r >= kMaxRounds) {
+        if (tid == 0) atomicOr(&ctl->error, kErrTimeout);
+        break;
+      }
+      if (tid == 0) {
+        ctl->rcnt[(r + 2) % 3] = 0;
+        ctl->rnext[(r + 2) % 3] = 0;
+      }
+      const uint2* cur = (r & 1) ? ctl->ract1 : ctl->ract0;
+      for (;;) {
+        if (threadIdx.x == 0) sh_item = atomicAdd(&ctl->rnext[r % 3], 1u);
+        __syncthreads();
+        const unsigned item = sh_item;
+        __syncthreads();
+        if (item >= cnt) break;
+        const uint2 e = cur[item];
+        const DevMap& m = maps[e.x];
+        RoundArgs ra;
+        ra.mi = e.x;
+        ra.e0 = __ldcg(&m.ctr->epoch) + 1;
+        ra.ep_next = ra.e0 + 1 + r;
+        ra.nxt_bits = (r & 1) ? m.rbits0 : m.rbits1;
+        ra.nxt_list = (r & 1) ? ctl->ract0 : ctl->ract1;
+        ra.nxt_cnt = &ctl->rcnt[(r + 1) % 3];
+        ra.q = nullptr;
+        if (threadIdx.x == 0) cta_pops = 0;
+        raise_dispatch<NT>(m, e.y, (r & 1) ? m.rbits1 : m.rbits0, ra, ctl, dsm, &cta_pops);
+        if (threadIdx.x == 0) {
+          if (cta_pops) atomicAdd(&m.ctr->raise_pops, cta_pops);
+          atomicAdd(&m.ctr->esdf_block_visits, 1u);
+        }
+      }
+      if (!grid_barrier(&ctl->bar, gridDim.x, &ctl->error)) return;
+    }
   }
   const unsigned raise_rounds = r;
   if (threadIdx.x == 0) sh_t[2] = global_ns();
@@ -794,8 +861,9 @@ __global__ void __launch_bounds__(NT, NT == 256 ? VBX_ESDF_MINB_256 : (NT == 128
   if (async_lower) {
     LowerQueue q;
     q.ctl = ctl;
+    q.init = ctl->lact0;
     q.n0 = __ldcg(&ctl->lcnt[0]);
-    q.tag_epoch = __ldcg(&ctl->calls);
+    q.tag_epoch = 2u * __ldcg(&ctl->calls) + 1u;
     l = q.n0 > 0 ? 1u : 0u;  // reported as one lower "round"
     for (;;) {
       if (threadIdx.x == 0) {
