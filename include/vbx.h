@@ -273,8 +273,8 @@ vbx_status vbx_batch_step(vbx_batch_t batch, const vbx_scan_in* scans, const vbx
 
 /* Chooses launch shapes (CTAs per SM of the traversal kernel; threads per CTA and CTAs per SM of
  * the ESDF kernel) by timing full steps on the given inputs: one untimed step, then the better of
- * two steps per candidate. The scans ARE integrated into the maps at every step, so call it on
- * warm-up data. Writes a one-line description to report (may be NULL) that ends with
+ * two steps per candidate; a candidate replaces the current best only when it is more than 3 %
+ * faster. The scans ARE integrated into the maps at every step, so call it on warm-up data. Writes a one-line description to report (may be NULL) that ends with
  * "trial_steps=<number of steps it ran>". */
 vbx_status vbx_batch_autotune(vbx_batch_t batch, const vbx_scan_in* scans, const vbx_query_io* queries, int flags,
                               void* stream, char* report, int report_len);

@@ -449,8 +449,7 @@ vbx_status vbx_update_esdf(vbx_map_t m, void* stream) {
   if (e != cudaSuccess) return cuda_fail(e, "reset esdf counters");
   e = cudaMemsetAsync(m->ctl_dev, 0, offsetof(vbx::EsdfCtl, cap), s);
   if (e != cudaSuccess) return cuda_fail(e, "reset esdf control");
-  // one map: its rounds would hold about one tile per SM, so the lower wave runs as one
-  // asynchronous work queue
+  // one map: its rounds would hold about one tile per SM, so the waves run as work queues
   e = vbx::launch_esdf(m->d_dev, 1, m->B, m->ctl_dev, m->cfg(stream), &m->hook, true);
   if (e != cudaSuccess) return cuda_fail(e, "esdf cooperative launch");
   return VBX_OK;
@@ -766,8 +765,8 @@ vbx_status batch_enqueue(vbx_batch_t b, int k, int flags, cudaStream_t s) {
   if (flags & VBX_STEP_ESDF) {
     if ((e = cudaMemsetAsync(b->ctl_dev, 0, offsetof(vbx::EsdfCtl, cap), s)) != cudaSuccess)
       return cuda_fail(e, "batch esdf reset");
-    // many maps keep every round full of tiles: the lower wave keeps its rounds
-    if ((e = vbx::launch_esdf(b->maps_dev(), b->count, b->max_B, b->ctl_dev, cfg, &b->hook, false)) != cudaSuccess)
+    // the kernel keeps rounds when many maps have work (full rounds), queues when few do
+    if ((e = vbx::launch_esdf(b->maps_dev(), b->count, b->max_B, b->ctl_dev, cfg, &b->hook, true)) != cudaSuccess)
       return cuda_fail(e, "batch esdf");
   }
   if (flags & VBX_STEP_QUERY) {
@@ -1029,7 +1028,11 @@ vbx_status vbx_batch_autotune(vbx_batch_t b, const vbx_scan_in* scans, const vbx
       return st;
     }
   }
-  // a candidate's time is the better of two steps
+  // a candidate's time is the better of two steps; a later candidate replaces the best only
+  // when it is clearly faster (the trial steps repeat the same scans, so their ESDF work is
+  // small and differences within a few per cent are noise; the candidates are listed with the
+  // usual winner first)
+  constexpr float kMargin = 0.97f;
   auto time_candidate = [&](float* ms) -> vbx_status {
     float a = 0.0f, c = 0.0f;
     vbx_status s2 = time_step(&a);
@@ -1044,7 +1047,7 @@ vbx_status vbx_batch_autotune(vbx_batch_t b, const vbx_scan_in* scans, const vbx
     b->tune.rays_ctas_per_sm = r;
     float ms = 0.0f;
     if ((st = time_candidate(&ms)) != VBX_OK) break;
-    if (ms < best_ms) {
+    if (ms < best_ms * kMargin) {
       best_ms = ms;
       best = b->tune;
     }
@@ -1060,7 +1063,7 @@ vbx_status vbx_batch_autotune(vbx_batch_t b, const vbx_scan_in* scans, const vbx
       b->tune.esdf_ctas_per_sm = o[1];
       float ms = 0.0f;
       if ((st = time_candidate(&ms)) != VBX_OK) break;
-      if (ms < best_ms) {
+      if (ms < best_ms * kMargin) {
         best_ms = ms;
         best = b->tune;
       }

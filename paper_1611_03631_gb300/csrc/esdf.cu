@@ -325,6 +325,11 @@ __device__ void stage_tile(const DevMap& m, const TileRef& r, uint32_t* cur_bits
 // tile is stamped e0 (its map's epoch) while queued and e0 - 1 once taken, so it is queued at
 // most once at a time and is queued again by any write that lands after it was staged.
 constexpr long long kMaxWaitSpins = 1ll << 24;
+// Largest number of maps with work in one launch for which the waves run as work queues.
+#ifndef VBX_ESDF_QUEUE_MAPS
+#define VBX_ESDF_QUEUE_MAPS 16
+#endif
+constexpr unsigned kMaxQueuedMaps = VBX_ESDF_QUEUE_MAPS;
 
 struct LowerQueue {
   EsdfCtl* ctl;
@@ -644,7 +649,7 @@ __device__ __forceinline__ unsigned upper_index(const unsigned* pfx, int n, unsi
 #define VBX_ESDF_MINB_128 12
 #endif
 template <int NT>
-__global__ void __launch_bounds__(NT, NT == 256 ? VBX_ESDF_MINB_256 : (NT == 128 ? VBX_ESDF_MINB_128 : (NT == 512 ? 2 : 1))) k_esdf(const DevMap* __restrict__ maps, int nmaps, EsdfCtl* ctl, int async_lower) {
+__global__ void __launch_bounds__(NT, NT == 256 ? VBX_ESDF_MINB_256 : (NT == 128 ? VBX_ESDF_MINB_128 : (NT == 512 ? 2 : 1))) k_esdf(const DevMap* __restrict__ maps, int nmaps, EsdfCtl* ctl, int allow_async) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ unsigned pfx[kMaxBatch + 1];
   __shared__ unsigned long long cta_pops;
@@ -652,14 +657,10 @@ __global__ void __launch_bounds__(NT, NT == 256 ? VBX_ESDF_MINB_256 : (NT == 128
   __shared__ int sh_state;
   __shared__ uint2 sh_e;
   __shared__ unsigned long long sh_t[4];  // phase boundaries, taken by thread 0 of each CTA
+  __shared__ unsigned sh_active;          // maps with dirty voxels in this launch
   const unsigned tid = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned nthreads = gridDim.x * blockDim.x;
   if (threadIdx.x == 0) sh_t[0] = global_ns();
-  // the lower queue's ring must hold the initial list's worth plus 27 pushes per CTA in flight
-  if (async_lower && ctl->rcap < ctl->cap + 27u * gridDim.x) {
-    if (tid == 0) atomicOr(&ctl->error, kErrTimeout);
-    return;
-  }
   if (tid == 0) atomicAdd(&ctl->calls, 1u);  // read by every CTA after the first grid barrier
 
   // ---------------------------------------------------------------- A6: classification
@@ -681,6 +682,12 @@ __global__ void __launch_bounds__(NT, NT == 256 ? VBX_ESDF_MINB_256 : (NT == 128
       if ((int)threadIdx.x >= off) incl += up;
     }
     unsigned run = incl - sum;
+    unsigned act = 0;
+#pragma unroll
+    for (int j = 0; j < per; ++j) act += v[j] > 0u ? 1u : 0u;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) act += __shfl_xor_sync(0xffffffffu, act, off);
+    if (threadIdx.x == 0) sh_active = act;
     if (threadIdx.x == 0) pfx[0] = 0u;
 #pragma unroll
     for (int j = 0; j < per; ++j) {
@@ -690,6 +697,15 @@ __global__ void __launch_bounds__(NT, NT == 256 ? VBX_ESDF_MINB_256 : (NT == 128
   }
   __syncthreads();
   const unsigned total = pfx[nmaps];
+  // Schedule of the raise and lower waves (every CTA decides alike, from the same counts): with
+  // few maps at work, rounds would hold a few tiles each and wait for their slowest one, so the
+  // waves run as work queues; with many, rounds are full and cheaper.
+  const bool async_lower = allow_async && sh_active <= kMaxQueuedMaps;
+  // the queue's ring must hold every tile plus 27 pushes per CTA in flight
+  if (async_lower && ctl->rcap < ctl->cap + 27u * gridDim.x) {
+    if (tid == 0) atomicOr(&ctl->error, kErrTimeout);
+    return;
+  }
   for (unsigned i = tid; i < total; i += nthreads) {
     const unsigned mi = upper_index(pfx, nmaps, i);
     const DevMap& m = maps[mi];
@@ -988,7 +1004,7 @@ int esdf_grid(int num_sms, int max_B, int ctas_per_sm, int threads) {
 }
 
 cudaError_t launch_esdf(const DevMap* maps_dev, int nmaps, int max_B, EsdfCtl* ctl, const LaunchCfg& cfg,
-                        LaunchHook* hook, bool async_lower) {
+                        LaunchHook* hook, bool allow_async) {
   if (nmaps <= 0 || nmaps > kMaxBatch) return cudaErrorInvalidValue;
   const int threads = cfg.tune.esdf_threads;
   const void* k = esdf_kernel(threads);
@@ -996,7 +1012,7 @@ cudaError_t launch_esdf(const DevMap* maps_dev, int nmaps, int max_B, EsdfCtl* c
   const int grid = esdf_grid(cfg.num_sms, max_B, cfg.tune.esdf_ctas_per_sm, threads);
   if (grid <= 0) return cudaErrorCooperativeLaunchTooLarge;
   const size_t smem = esdf_smem_bytes(max_B);
-  int async = async_lower ? 1 : 0;
+  int async = allow_async ? 1 : 0;
   void* args[] = {(void*)&maps_dev, (void*)&nmaps, (void*)&ctl, (void*)&async};
   hook->begin(kKEsdf, cfg.stream);
   cudaError_t e = cudaLaunchCooperativeKernel(k, dim3(grid), dim3(threads), args, smem, cfg.stream);

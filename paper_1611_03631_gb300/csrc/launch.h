@@ -116,9 +116,10 @@ cudaError_t launch_reset_map(const DevMap& m, const LaunchCfg& cfg);
 // esdf.cu: one cooperative launch updates the ESDF of nmaps maps (device array of DevMap)
 size_t esdf_smem_bytes(int max_B);
 int esdf_grid(int num_sms, int max_B, int ctas_per_sm, int threads);
-// async_lower: the lower wave as one asynchronous work queue (single maps) instead of rounds
+// allow_async: the raise and lower waves may run as asynchronous work queues instead of rounds
+// (the kernel takes them when few maps of the launch have work)
 cudaError_t launch_esdf(const DevMap* maps_dev, int nmaps, int max_B, EsdfCtl* ctl, const LaunchCfg& cfg,
-                        LaunchHook* hook, bool async_lower);
+                        LaunchHook* hook, bool allow_async);
 
 // mesh.cu: triangles of the TSDF iso-surface, per block
 struct MeshBlockRec {  // same layout as vbx_mesh_block
