@@ -37,27 +37,31 @@ N_QUERIES = 10000
 FLUSH_BYTES = 256 << 20  # > 129 MB L2
 
 # DRAM bytes (read + write) per launch of a kernel from one ncu capture, keyed by the kernel
-# and the SHA-256 prefix of the source file it was captured on: once that source changes the
-# entry no longer matches and the reported traffic is null.
+# and the SHA-256 prefix of the source files it was captured on (KERNEL_SOURCE): once one of
+# them changes the entry no longer matches and the reported traffic is null.
 NCU_TRAFFIC = {
-    # k_esdf<1024>, room workload, one scan (dram__bytes_read.sum 2,307,328 + write 37,120)
-    ("esdf", "esdf.cu", "0c39731ef03fbdc0"): 2344448,
+    # k_esdf<512> x 2 per SM, room workload, one scan (dram__bytes_read.sum 2,320,384 + write 47,616)
+    ("esdf", "esdf.cu", "625fbf7bddd07a65"): 2368000,
     # k_mesh_blocks<16>, full mesh of the room map (dram__bytes_read.sum 25,988,096 + write 2,304;
     # the 17 MB of triangles it writes are still in L2 when it ends)
     ("mesh_blocks", "mesh.cu", "cbd5b0c8554fc2d5"): 25990400,
 }
-KERNEL_SOURCE = {"mesh_blocks": "mesh.cu", "esdf": "esdf.cu", "integrate_rays": "integrate.cu", "apply": "integrate.cu", "bin_points": "integrate.cu", "query": "query.cu"}
+# the files a kernel's code and launch shape come from (the single-map ESDF shape is in launch.h)
+KERNEL_SOURCE = {"mesh_blocks": "mesh.cu", "esdf": ("esdf.cu", "launch.h"), "integrate_rays": "integrate.cu", "apply": "integrate.cu", "bin_points": "integrate.cu", "query": "query.cu"}
 
 
 def _ncu_traffic(kernel: str):
     import hashlib
 
-    src = KERNEL_SOURCE.get(kernel)
-    if src is None:
+    srcs = KERNEL_SOURCE.get(kernel)
+    if srcs is None:
         return None
-    with open(os.path.join(ROOT, "paper_1611_03631_gb300", "csrc", src), "rb") as f:
-        h = hashlib.sha256(f.read()).hexdigest()[:16]
-    return NCU_TRAFFIC.get((kernel, src, h))
+    srcs = (srcs,) if isinstance(srcs, str) else srcs
+    h = hashlib.sha256()
+    for src in srcs:
+        with open(os.path.join(ROOT, "paper_1611_03631_gb300", "csrc", src), "rb") as f:
+            h.update(f.read())
+    return NCU_TRAFFIC.get((kernel, srcs[0], h.hexdigest()[:16]))
 
 
 def _scene(frames: int):

@@ -53,14 +53,14 @@ struct Tuning {
 };
 // Start point of the batch autotuner (the ESDF grid is clamped to the kernel's occupancy).
 constexpr Tuning kDefaultTuning = {16, 16, 16, 8, 256};
-// Calls on one map: its ESDF waves activate few tiles per round (about one per SM), so the
-// round time is the latency of one tile's local relaxation; wide CTAs shorten it, and a small
-// grid shortens each round's grid barrier.
+// Calls on one map: the ESDF waves run as work queues, and a wave advances as fast as a tile's
+// local relaxation (wide CTAs shorten it) while several tiles along its front are in flight
+// (more CTAs); on the room sequence 512 x 2 per SM beat 1024 x 1 and 256 x 4.
 #ifndef VBX_MAP_ESDF_THREADS
-#define VBX_MAP_ESDF_THREADS 1024
+#define VBX_MAP_ESDF_THREADS 512
 #endif
 #ifndef VBX_MAP_ESDF_CTAS
-#define VBX_MAP_ESDF_CTAS 1
+#define VBX_MAP_ESDF_CTAS 2
 #endif
 constexpr Tuning kMapTuning = {16, 16, 16, VBX_MAP_ESDF_CTAS, VBX_MAP_ESDF_THREADS};
 
