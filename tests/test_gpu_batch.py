@@ -104,3 +104,26 @@ def test_batch_slots_without_scans_and_autotune(vbx):
         m.update_esdf()
     for a, b in zip(ref, maps):
         _same(a, b)
+
+
+def test_many_maps_rounds_equal_single_map_queues(vbx):
+    """More than 16 maps at work: the batched ESDF runs in global rounds, while each map alone
+    runs its waves as work queues. Both schedules must reach the same maps, bit for bit."""
+    ss = [
+        scenes.plane_sphere(frames=3, width=32, height=24, fx=25.0, fy=25.0, cx=16.0, cy=12.0, seed=20 + k)
+        for k in range(20)
+    ]
+    alone = _maps(vbx, ss)
+    mixed = _maps(vbx, ss)
+    batch = vbx.MapBatch(mixed)
+    for f in range(3):
+        pts = [torch.from_numpy(s.points[f]).cuda() for s in ss]
+        for m, s, p in zip(alone, ss, pts):
+            m.integrate_scan(p, s.poses[f])
+            m.update_esdf()
+        batch.step(pts, [s.poses[f] for s in ss])
+        batch.sync()
+        for a, b in zip(alone, mixed):
+            _same(a, b)
+    assert max(m.stats()["lower_rounds"] for m in mixed) > 1  # rounds, not the queue
+    assert max(m.stats()["lower_rounds"] for m in alone) == 1  # one queue
