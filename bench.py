@@ -41,7 +41,7 @@ FLUSH_BYTES = 256 << 20  # > 129 MB L2
 # them changes the entry no longer matches and the reported traffic is null.
 NCU_TRAFFIC = {
     # k_esdf<512> x 2 per SM, room workload, one scan (dram__bytes_read.sum 2,320,384 + write 47,616)
-    ("esdf", "esdf.cu", "625fbf7bddd07a65"): 2368000,
+    ("esdf", "esdf.cu", "5f585b9c2a3af0cc"): 2368000,
     # k_mesh_blocks<16>, full mesh of the room map (dram__bytes_read.sum 25,988,096 + write 2,304;
     # the 17 MB of triangles it writes are still in L2 when it ends)
     ("mesh_blocks", "mesh.cu", "cbd5b0c8554fc2d5"): 25990400,

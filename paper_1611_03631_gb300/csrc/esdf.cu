@@ -331,7 +331,7 @@ constexpr long long kMaxWaitSpins = 1ll << 24;
 #endif
 constexpr unsigned kMaxQueuedMaps = VBX_ESDF_QUEUE_MAPS;
 
-struct LowerQueue {
+struct WaveQueue {
   EsdfCtl* ctl;
   const uint2* init;  // the initial list (raise: ract0, lower: lact0)
   unsigned n0;        // its length
@@ -346,7 +346,7 @@ __device__ __forceinline__ unsigned long long q_read_tag(unsigned ep, unsigned h
 }
 
 // Queues tile `item` of map mi unless it is queued already (one thread).
-__device__ void q_push(const LowerQueue& q, unsigned mi, uint32_t item, uint32_t* stamps, unsigned e0) {
+__device__ void q_push(const WaveQueue& q, unsigned mi, uint32_t item, uint32_t* stamps, unsigned e0) {
   __threadfence();  // the frontier bits set for this tile are visible before it can be taken
   if (__ldcg(&stamps[item]) >= e0) return;
   if (atomicMax(&stamps[item], e0) >= e0) return;
@@ -373,7 +373,7 @@ __device__ void q_push(const LowerQueue& q, unsigned mi, uint32_t item, uint32_t
 
 // Takes the next ticket (one thread): 1 with the tile in *out, 0 once the queue has drained
 // (every produced ticket finished, so no tile can be queued any more), -1 on error.
-__device__ int q_pop(const LowerQueue& q, uint2* out) {
+__device__ int q_pop(const WaveQueue& q, uint2* out) {
   EsdfCtl* ctl = q.ctl;
   const unsigned h = atomicAdd(&ctl->qhead, 1u);
   if (h < q.n0) {
@@ -414,7 +414,7 @@ struct RoundArgs {
   uint32_t* nxt_bits;
   uint2* nxt_list;
   unsigned* nxt_cnt;
-  const LowerQueue* q;  // lower wave: where neighbour tiles are queued
+  const WaveQueue* q;  // lower wave: where neighbour tiles are queued
 };
 
 // A7 for one staged tile (all threads of the CTA).
@@ -772,7 +772,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? VBX_ESDF_MINB_256 : (NT == 128
   // counters are reset between two grid barriers for the lower wave).
   unsigned r = 0;
   if (async_lower) {
-    LowerQueue q;
+    WaveQueue q;
     q.ctl = ctl;
     q.init = ctl->ract0;
     q.n0 = __ldcg(&ctl->rcnt[0]);
@@ -875,7 +875,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? VBX_ESDF_MINB_256 : (NT == 128
   //    barrier; the phase ends when every produced ticket has finished.
   unsigned l = 0;
   if (async_lower) {
-    LowerQueue q;
+    WaveQueue q;
     q.ctl = ctl;
     q.init = ctl->lact0;
     q.n0 = __ldcg(&ctl->lcnt[0]);
