@@ -964,7 +964,7 @@ def run_gpu(args):
             "total": (tsdf_upd + esdf_upd) * ws / secs / 1e6,
             "ray_voxel_records": records * ws / secs / 1e6,
         },
-        "esdf_rounds_per_scan": rounds / args.steps,
+        "esdf_rounds_per_scan": rounds / args.steps,  # 2: one work queue per wave (single map)
         "esdf_block_visits_per_scan": visits / args.steps,
         "esdf_local_iters_per_visit": liters / max(visits, 1),
         "esdf_phase_ms_per_scan": {k: v / 1e6 / args.steps for k, v in zip(("classify", "raise", "lower"), phase_ns)},

@@ -135,16 +135,17 @@ typedef struct {
   int64_t blocks;         /* blocks in the map                                              */
   int64_t esdf_in;        /* TSDF voxels consumed by the last vbx_update_esdf               */
   int64_t seeds;          /* of those, in the fixed band                                    */
-  int64_t raise_pops;     /* voxels processed by raise rounds                               */
-  int64_t lower_pops;     /* voxels processed by lower rounds                               */
-  int64_t raise_rounds;
-  int64_t lower_rounds;
+  int64_t raise_pops;     /* voxels processed by the raise wave                             */
+  int64_t lower_pops;     /* voxels processed by the lower wave                             */
+  int64_t raise_rounds;   /* global rounds of the raise wave; 1 when it ran as one work
+                             queue (16 or fewer maps with work in the launch), 0 if empty  */
+  int64_t lower_rounds;   /* the same for the lower wave                                    */
   int64_t launches;       /* kernels launched by this map since creation                    */
   int64_t esdf_block_visits; /* tiles staged in shared memory by the last ESDF update        */
   int64_t esdf_local_iters;  /* local relaxation iterations summed over those stagings       */
   int64_t esdf_classify_ns;  /* device time of the classification phase of the last update  */
-  int64_t esdf_raise_ns;     /* ... of the raise rounds                                       */
-  int64_t esdf_lower_ns;     /* ... of the lower rounds                                       */
+  int64_t esdf_raise_ns;     /* ... of the raise wave                                         */
+  int64_t esdf_lower_ns;     /* ... of the lower wave                                         */
   int64_t touched_blocks;    /* blocks the rays of the last scan entered (scratch blocks it
                                 needed; above scratch_blocks the scan was rejected)          */
 } vbx_stats;
