@@ -68,3 +68,23 @@ def test_product_package_does_not_import_the_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle\b", txt, re.M), f
                 assert "vbx_oracle" not in txt, f
+
+
+def test_map_bytes_without_a_device():
+    """vbx_map_bytes needs no GPU (the queue ring is sized for 152 SMs when no device answers):
+    it grows with the block pool and the point capacity, and shrinks with fewer scratch
+    blocks; invalid block edges are refused."""
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1611_03631_gb300 import vbx
+
+    vbx.load_library()
+    small = vbx.map_bytes(16, 1024, 1 << 16)
+    assert vbx.map_bytes(16, 4096, 1 << 16) > small
+    assert vbx.map_bytes(16, 1024, 1 << 18) > small
+    assert vbx.map_bytes(16, 1024, 1 << 16, scratch_blocks=64) < small
+    # a pool voxel costs at least its TSDF and ESDF words (16 B) plus the queue ring per tile
+    assert small > 1024 * 16 ** 3 * 16 + 1024 * 8 * 16
+    with pytest.raises(vbx.VbxError):
+        vbx.map_bytes(12, 1024, 1 << 16)
