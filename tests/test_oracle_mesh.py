@@ -77,3 +77,61 @@ def test_random_fields_give_watertight_oriented_surfaces(seed):
     # signed volume they bound (divergence theorem) is positive
     vol = np.einsum("ij,ij->i", verts[:, 0].astype(np.float64), np.cross(verts[:, 1], verts[:, 2]).astype(np.float64)).sum() / 6
     assert vol > 0
+
+
+def _one_cell(Dc, v=0.1):
+    """A map holding one cell (corner c = x + 2y + 4z at voxel (x, y, z)), all observed."""
+    D = np.zeros((2, 2, 2))
+    for c in range(8):
+        D[c & 1, (c >> 1) & 1, c >> 2] = Dc[c]
+    return _grid_map(D, v).extract_mesh()
+
+
+def test_single_inside_corner_is_one_triangle_cut_at_the_interpolated_points():
+    """Worked example: corner 0 at D = -0.25, the others at +0.75. Each of its three edges
+    crosses a quarter of the way from corner 0 (t = -0.25 / (-0.25 - 0.75)), so the triangle's
+    vertices are the cell origin plus v/4 along x, y and z; its normal points away from the
+    inside corner, towards positive D."""
+    v = 0.1
+    cells, verts = _one_cell([-0.25] + [0.75] * 7, v)
+    assert cells.shape[0] == 1 and tuple(cells[0]) == (0, 0, 0, 0)
+    o = np.float32(0.5) * np.float32(v)
+    q = o + np.float32(0.25) * np.float32(v)
+    expect = {(q, o, o), (o, q, o), (o, o, q)}
+    got = {tuple(np.round(p, 7)) for p in verts[0].astype(np.float64)}
+    assert got == {tuple(np.round(np.array(e, np.float64), 7)) for e in expect}
+    n = np.cross(verts[0, 1] - verts[0, 0], verts[0, 2] - verts[0, 0])
+    assert n @ np.ones(3) > 0
+
+
+def test_complement_gives_the_same_triangle_reversed():
+    a_cells, a = _one_cell([-0.25] + [0.75] * 7)
+    b_cells, b = _one_cell([0.25] + [-0.75] * 7)
+    assert a.shape[0] == b.shape[0] == 1
+    assert {tuple(p) for p in a[0]} == {tuple(p) for p in b[0]}
+    na = np.cross(a[0, 1] - a[0, 0], a[0, 2] - a[0, 0])
+    nb = np.cross(b[0, 1] - b[0, 0], b[0, 2] - b[0, 0])
+    assert na @ nb < 0
+
+
+def test_diagonal_inside_corners_on_a_face_are_cut_off_separately():
+    """Corners 0 and 3 inside (diagonal on the face z = 0), the rest outside: the ambiguous face
+    is resolved by cutting each inside corner off alone, so the cell holds two separate
+    triangles (six distinct vertices) rather than one band."""
+    Dc = [0.5] * 8
+    Dc[0] = Dc[3] = -0.5
+    cells, verts = _one_cell(Dc)
+    assert cells.shape[0] == 2
+    assert len({tuple(p) for t in verts for p in t}) == 6
+
+
+def test_a_zero_corner_counts_as_outside():
+    """fl32(D) = 0 (either sign) is outside: with corner 0 at -0.5 and corner 1 at exactly 0,
+    the x edge crosses at t = 1, i.e. exactly at corner 1."""
+    v = 0.1
+    for z in (0.0, -0.0):
+        Dc = [-0.5, z, 0.5, 0.5, 0.5, 0.5, 0.5, 0.5]
+        cells, verts = _one_cell(Dc, v)
+        assert cells.shape[0] == 1
+        c1 = np.array([1.5, 0.5, 0.5], np.float32) * np.float32(v)
+        assert any(np.array_equal(p, c1) for p in verts[0])
