@@ -232,6 +232,9 @@ class MapServer:
         flags_map = vbx.STEP_INTEGRATE | vbx.STEP_ESDF | (vbx.STEP_GRAPH if self.use_graph else 0)
         flags_q = vbx.STEP_QUERY | (vbx.STEP_GRAPH if self.use_graph else 0)
         lat_scan, lat_query, batch_sizes = [], [], []
+        # per scan: its kind, the wait from arrival to the start of its step, and that step's wall
+        # time (scan part); they show where the latency tail comes from
+        scan_kind, scan_wait, scan_step = [], [], []
         admitted = 0
         max_active = 0
         e0 = torch.cuda.Event(enable_timing=True)
@@ -273,6 +276,7 @@ class MapServer:
                 p, T, q = self.pool.frame(a.spec, a.next)
                 points[s], poses[s] = p, T
                 queries[s] = (q,) + self.out[s]
+            t_step = time.perf_counter() - t0
             e0.record()
             self.batch.step(points, poses, flags=flags_map)
             e1.record()
@@ -288,6 +292,9 @@ class MapServer:
                 arrival = float(a.arrivals[a.next])
                 lat_query.append(t_done - arrival)
                 lat_scan.append(t_done - q_ms * 1e-3 - arrival)
+                scan_kind.append(a.spec.kind)
+                scan_wait.append(max(t_step - arrival, 0.0))
+                scan_step.append(t_done - q_ms * 1e-3 - t_step)
                 a.next += 1
                 if a.next == a.spec.n_scans:
                     if on_finish is not None:
@@ -301,6 +308,17 @@ class MapServer:
         n = len(lat_scan)
         ls = np.asarray(lat_scan) * 1e3
         lq = np.asarray(lat_query) * 1e3
+        kinds = np.asarray(scan_kind)
+        pct = lambda x: dict(p50=float(np.percentile(x, 50)), p99=float(np.percentile(x, 99))) if len(x) else None
+        by_kind = {
+            k: dict(
+                scans=int((kinds == k).sum()),
+                latency_ms=pct(ls[kinds == k]),
+                wait_ms=pct(np.asarray(scan_wait)[kinds == k] * 1e3),
+                step_ms=pct(np.asarray(scan_step)[kinds == k] * 1e3),
+            )
+            for k in sorted(set(scan_kind))
+        }
         return dict(
             sessions=admitted,
             scans=n,
@@ -312,6 +330,7 @@ class MapServer:
             mean_batch=float(np.mean(batch_sizes)) if batch_sizes else 0.0,
             max_concurrent_sessions=max_active,
             scan_latency_ms=dict(p50=float(np.percentile(ls, 50)), p99=float(np.percentile(ls, 99))),
+            scan_latency_by_kind=by_kind,
             query_latency_ms=dict(p50=float(np.percentile(lq, 50)), p99=float(np.percentile(lq, 99))),
             peak_map_bytes=self.peak,
             budget_bytes=self.budget,
