@@ -234,7 +234,7 @@ class MapServer:
         lat_scan, lat_query, batch_sizes = [], [], []
         # per scan: its kind, the wait from arrival to the start of its step, and that step's wall
         # time (scan part); they show where the latency tail comes from
-        scan_kind, scan_wait, scan_step = [], [], []
+        scan_kind, scan_wait, scan_step, scan_first = [], [], [], []
         admitted = 0
         max_active = 0
         e0 = torch.cuda.Event(enable_timing=True)
@@ -293,6 +293,7 @@ class MapServer:
                 lat_query.append(t_done - arrival)
                 lat_scan.append(t_done - q_ms * 1e-3 - arrival)
                 scan_kind.append(a.spec.kind)
+                scan_first.append(a.next == 0)
                 scan_wait.append(max(t_step - arrival, 0.0))
                 scan_step.append(t_done - q_ms * 1e-3 - t_step)
                 a.next += 1
@@ -319,6 +320,20 @@ class MapServer:
             )
             for k in sorted(set(scan_kind))
         }
+        # a session's first scan starts from an empty map (all blocks new, the ESDF from scratch)
+        first = np.asarray(scan_first, bool)
+        by_kind.update(
+            {
+                f"{k}_first_scan": dict(scans=int(((kinds == k) & first).sum()), latency_ms=pct(ls[(kinds == k) & first]))
+                for k in sorted(set(scan_kind))
+            }
+        )
+        by_kind.update(
+            {
+                f"{k}_later_scans": dict(scans=int(((kinds == k) & ~first).sum()), latency_ms=pct(ls[(kinds == k) & ~first]))
+                for k in sorted(set(scan_kind))
+            }
+        )
         return dict(
             sessions=admitted,
             scans=n,
