@@ -234,7 +234,7 @@ class MapServer:
         lat_scan, lat_query, batch_sizes = [], [], []
         # per scan: its kind, the wait from arrival to the start of its step, and that step's wall
         # time (scan part); they show where the latency tail comes from
-        scan_kind, scan_wait, scan_step, scan_first = [], [], [], []
+        scan_kind, scan_wait, scan_step, scan_first, scan_gpu = [], [], [], [], []
         admitted = 0
         max_active = 0
         e0 = torch.cuda.Event(enable_timing=True)
@@ -294,6 +294,7 @@ class MapServer:
                 lat_scan.append(t_done - q_ms * 1e-3 - arrival)
                 scan_kind.append(a.spec.kind)
                 scan_first.append(a.next == 0)
+                scan_gpu.append(e0.elapsed_time(e1) * 1e-3)  # the step's device time (scan part)
                 scan_wait.append(max(t_step - arrival, 0.0))
                 scan_step.append(t_done - q_ms * 1e-3 - t_step)
                 a.next += 1
@@ -317,6 +318,7 @@ class MapServer:
                 latency_ms=pct(ls[kinds == k]),
                 wait_ms=pct(np.asarray(scan_wait)[kinds == k] * 1e3),
                 step_ms=pct(np.asarray(scan_step)[kinds == k] * 1e3),
+                step_gpu_ms=pct(np.asarray(scan_gpu)[kinds == k] * 1e3),
             )
             for k in sorted(set(scan_kind))
         }
