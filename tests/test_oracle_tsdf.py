@@ -104,6 +104,31 @@ def test_single_ray_constant_weight_two_scans():
         assert vals[(i, 0, 0)][1] == w
 
 
+def test_single_ray_weight_cap_of_eq3():
+    """Eq. (3) with W_max = 2 (w_max option): four scans of the same ray at depths 1.0, 1.1,
+    1.0, 1.1 (unit weights). Voxel row 10 (centre x = 1.05) sees d = 0.0, 0.1, 0.0, 0.1:
+      D1 = 0, W1 = 1;  D2 = 0.05, W2 = 2;  D3 = (2 * 0.05 + 0) / 3, W3 = min(3, 2) = 2;
+      D4 = (2 * D3 + 0.1) / 3 with the cap, against (3 * D3 + 0.1) / 4 = 0.05 without it."""
+    T = _pose_fwd_x()
+    depths = (1.0, 1.1, 1.0, 1.1)
+    m = oracle.OracleMap(0.1, 8, 0.27, 2.0, weighting=0, w_max=2.0)
+    for depth in depths:
+        m.integrate(np.array([[0.0, 0.0, depth]], np.float32), T)
+    vals, _ = _row_values(m)
+    D3 = (2 * 0.05 + 0.0) / 3
+    D, W = vals[(10, 0, 0)]
+    assert W == 2.0
+    assert D == pytest.approx((2 * D3 + 0.1) / 3, abs=2e-6)
+    m2 = oracle.OracleMap(0.1, 8, 0.27, 2.0, weighting=0)
+    for depth in depths:
+        m2.integrate(np.array([[0.0, 0.0, depth]], np.float32), T)
+    vals2, _ = _row_values(m2)
+    D2u, W2u = vals2[(10, 0, 0)]
+    assert W2u == 4.0
+    assert D2u == pytest.approx((3 * D3 + 0.1) / 4, abs=2e-6)
+    assert abs(D - D2u) > 1e-3  # the cap changes D from the fourth scan on
+
+
 def test_single_ray_quadratic_weight_dropoff():
     # Eq. (4) with delta = 0.27, eps = 0.1; the point is at depth z = 1 so 1/z^2 = 1.
     m = oracle.OracleMap(0.1, 8, 0.27, 2.0, weighting=1, eps=0.1)
