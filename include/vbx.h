@@ -38,7 +38,8 @@ typedef enum {
   VBX_ERR_INVALID_ARG = 1,   /* bad size, pointer or parameter; nothing was enqueued */
   VBX_ERR_OUT_OF_MEMORY = 2, /* device allocation failed or the block pool is exhausted */
   VBX_ERR_HASH_FULL = 3,     /* block hash probe limit reached */
-  VBX_ERR_TIMEOUT = 4,       /* a device loop exceeded its round budget or a wait its limit */
+  VBX_ERR_TIMEOUT = 4,       /* a device loop exceeded its round budget or a wait its limit
+                                (grid barriers, the ESDF work queue)                         */
   VBX_ERR_CUDA = 5,          /* a CUDA runtime call failed (message in vbx_last_error) */
   VBX_ERR_CAPACITY = 6       /* an output buffer is too small: the sizes needed are reported
                                 and the map is unchanged                                     */
@@ -111,8 +112,10 @@ vbx_status vbx_integrate_scan_noalloc(vbx_map_t map, const float* points_dev, in
 /* Updates the ESDF incrementally from the TSDF voxels updated since the last call
  * (Sec. V-A, Algorithm 1): fixed band |D| < gamma, raise wavefront, then lower wavefront over
  * 26-connected neighbours with quasi-Euclidean steps v, v*sqrt(2), v*sqrt(3), capped at
- * d_max. Runs as one cooperative persistent kernel on `stream`: each round stages the active
- * blocks with their one-voxel halos in shared memory and relaxes them to local convergence. */
+ * d_max. Runs as one cooperative persistent kernel on `stream`. A CTA stages an active tile
+ * (a block, or an 8^3 octant of a 16^3 block) with its one-voxel halo in shared memory and
+ * relaxes it to local convergence. For one map each wave runs as a work queue of tiles; batches
+ * with more than 16 maps at work run each wave in global rounds. Both give the same ESDF. */
 vbx_status vbx_update_esdf(vbx_map_t map, void* stream);
 
 /* Distance and gradient queries (the planner's interface, Sec. VII; trilinear interpolation
