@@ -156,6 +156,19 @@ def test_filter_drops_invalid_points():
     assert st["points_in"] == 5 and st["points_valid"] == 1
 
 
+def test_filter_bounds_of_reading_r1():
+    """Reading R1 bounds the integer ranges: a point 2^14 voxels or more from the sensor is
+    dropped (v = 1 m: 16,000 m kept, 16,500 m dropped), and under Eq. (4) so is a point whose
+    1/z^2 weight exceeds 1024 (z = 0.03 m dropped, z = 0.032 m kept) or whose depth is not
+    positive."""
+    m = oracle.OracleMap(1.0, 8, 2.0, 5.0)
+    m.integrate(np.array([[0, 0, 16000.0], [0, 0, 16500.0]], np.float32), _pose_fwd_x())
+    assert m.stats()["points_valid"] == 1
+    q = oracle.OracleMap(0.1, 8, 0.3, 2.0, weighting=1, eps=0.1)
+    q.integrate(np.array([[0, 0, 0.03], [0, 0, 0.032], [0, 0, -1.0]], np.float32), _pose_fwd_x())
+    assert q.stats()["points_valid"] == 1
+
+
 # ------------------------------------------------------------------ grouping, Sec. IV-B
 
 
