@@ -289,14 +289,19 @@ bool accept_point(const Params& p, const float ps[3], float* w) {
   return true;
 }
 
-void integrate(Map& m, const float* pts, int64_t n, const float T[16]) {
-  const Params& p = m.p;
-  m.st = Stats{};
-  m.st.points_in = n;
-  const float s[3] = {T[3], T[7], T[11]};
+// A1 + A2 (R1): the rays of one scan. Grouped raycasting (Sec. IV-B) gives one ray per voxel
+// that holds accepted points, at the weighted mean of its points with the summed weight;
+// plain raycasting gives one ray per accepted point. Each ray comes with the voxel key of its
+// group and the group's point count (per point: the point's own key, count 1). Returns the
+// number of accepted points. Both integrate() and the grouping pin entry use this function.
+struct ScanRay {
+  Key3 key;
+  Ray ray;
+  int64_t count;
+};
 
-  // Rays: grouped (one per voxel containing points) or one per point.
-  std::vector<Ray> rays;
+int64_t scan_rays(const Params& p, const float* pts, int64_t n, const float T[16], std::vector<ScanRay>* out) {
+  int64_t valid = 0;
   std::unordered_map<Key3, Group, Key3Hash> groups;
   for (int64_t i = 0; i < n; ++i) {
     float w;
@@ -310,15 +315,17 @@ void integrate(Map& m, const float* pts, int64_t n, const float T[16]) {
       if (!(std::fabs(q[a]) < 1048576.0f)) in_range = false;  // |key| < 2^20
     }
     if (!in_range) continue;
-    m.st.points_valid++;
+    valid++;
+    Key3 key{(int32_t)std::floor(q[0]), (int32_t)std::floor(q[1]), (int32_t)std::floor(q[2])};
     if (!p.grouped) {
-      Ray r;
-      for (int a = 0; a < 3; ++a) r.pbar[a] = pw[a];
-      r.Wg = w;
-      rays.push_back(r);
+      ScanRay r;
+      r.key = key;
+      for (int a = 0; a < 3; ++a) r.ray.pbar[a] = pw[a];
+      r.ray.Wg = w;
+      r.count = 1;
+      out->push_back(r);
       continue;
     }
-    Key3 key{(int32_t)std::floor(q[0]), (int32_t)std::floor(q[1]), (int32_t)std::floor(q[2])};
     int64_t wq = p.weighting == 0 ? 1 : (int64_t)std::llrint((double)w * 1048576.0);
     Group& g = groups[key];
     g.n += 1;
@@ -330,21 +337,36 @@ void integrate(Map& m, const float* pts, int64_t n, const float T[16]) {
       g.swo[a] += (__int128)wq * o;
     }
   }
-  if (p.grouped) {
-    for (auto& kv : groups) {
-      const Key3& key = kv.first;
-      const Group& g = kv.second;
-      Ray r;
-      const int32_t kk[3] = {key.x, key.y, key.z};
-      for (int a = 0; a < 3; ++a) {
-        __int128 mnum = g.swo[a] + (__int128)(g.sw / 2);
-        int64_t mo = (int64_t)(mnum / (__int128)g.sw);
-        r.pbar[a] = ((float)kk[a] + (float)mo * (1.0f / 65536.0f)) * p.v;
-      }
-      r.Wg = p.weighting == 0 ? (float)g.n : (float)g.sw * (1.0f / 1048576.0f);
-      rays.push_back(r);
+  for (auto& kv : groups) {
+    const Key3& key = kv.first;
+    const Group& g = kv.second;
+    ScanRay r;
+    r.key = key;
+    const int32_t kk[3] = {key.x, key.y, key.z};
+    for (int a = 0; a < 3; ++a) {
+      __int128 mnum = g.swo[a] + (__int128)(g.sw / 2);
+      int64_t mo = (int64_t)(mnum / (__int128)g.sw);
+      r.ray.pbar[a] = ((float)kk[a] + (float)mo * (1.0f / 65536.0f)) * p.v;
     }
+    r.ray.Wg = p.weighting == 0 ? (float)g.n : (float)g.sw * (1.0f / 1048576.0f);
+    r.count = g.n;
+    out->push_back(r);
   }
+  return valid;
+}
+
+void integrate(Map& m, const float* pts, int64_t n, const float T[16]) {
+  const Params& p = m.p;
+  m.st = Stats{};
+  m.st.points_in = n;
+  const float s[3] = {T[3], T[7], T[11]};
+
+  // Rays: grouped (one per voxel containing points) or one per point.
+  std::vector<ScanRay> srays;
+  m.st.points_valid = scan_rays(p, pts, n, T, &srays);
+  std::vector<Ray> rays;
+  rays.reserve(srays.size());
+  for (const ScanRay& r : srays) rays.push_back(r.ray);
   m.st.groups = (int64_t)rays.size();
 
   // Raycasting (Sec. IV-B) and per-voxel accumulation (Eq. 3 summed over the scan).
@@ -945,54 +967,22 @@ float orc_record_weight(const orc_params* op, float Wg, float d) {
 }
 
 // Grouping only (Sec. IV-B): returns the number of groups; writes key, pbar, W_g, count
-// sorted by key.
+// sorted by key. The groups come from scan_rays, the function integrate() casts its rays from.
 int64_t orc_group(const orc_params* op, const float* pts, int64_t n, const float* T16, int32_t* keys, float* pbar,
                   float* Wg, int64_t* count, int64_t cap) {
   Params p{op->voxel_size, op->voxels_per_block, op->truncation, op->max_esdf_dist, op->weighting, op->eps,
            op->fixed_band, op->w_max,            op->max_range,  1,                 op->esdf_fp32, op->esdf_mode};
-  std::vector<std::pair<Key3, Group>> gs;
-  {
-    std::unordered_map<Key3, Group, Key3Hash> groups;
-    for (int64_t i = 0; i < n; ++i) {
-      float w;
-      if (!accept_point(p, pts + 3 * i, &w)) continue;
-      float pw[3];
-      transform_point(T16, pts + 3 * i, pw);
-      float q[3];
-      bool in_range = true;
-      for (int a = 0; a < 3; ++a) {
-        q[a] = pw[a] / p.v;
-        if (!(std::fabs(q[a]) < 1048576.0f)) in_range = false;
-      }
-      if (!in_range) continue;
-      Key3 key{(int32_t)std::floor(q[0]), (int32_t)std::floor(q[1]), (int32_t)std::floor(q[2])};
-      int64_t wq = p.weighting == 0 ? 1 : (int64_t)std::llrint((double)w * 1048576.0);
-      Group& g = groups[key];
-      g.n += 1;
-      g.sw += wq;
-      for (int a = 0; a < 3; ++a) {
-        float frac = q[a] - std::floor(q[a]);
-        int64_t o = (int64_t)std::llrint(frac * 65536.0f);
-        if (o > 65535) o = 65535;
-        g.swo[a] += (__int128)wq * o;
-      }
-    }
-    for (auto& kv : groups) gs.push_back(kv);
-  }
-  std::sort(gs.begin(), gs.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+  std::vector<ScanRay> gs;
+  scan_rays(p, pts, n, T16, &gs);
+  std::sort(gs.begin(), gs.end(), [](const ScanRay& a, const ScanRay& b) { return a.key < b.key; });
   int64_t k = std::min<int64_t>(cap, (int64_t)gs.size());
   for (int64_t i = 0; i < k; ++i) {
-    const Key3& key = gs[i].first;
-    const Group& g = gs[i].second;
-    const int32_t kk[3] = {key.x, key.y, key.z};
-    for (int a = 0; a < 3; ++a) {
-      keys[3 * i + a] = kk[a];
-      __int128 mnum = g.swo[a] + (__int128)(g.sw / 2);
-      int64_t mo = (int64_t)(mnum / (__int128)g.sw);
-      pbar[3 * i + a] = ((float)kk[a] + (float)mo * (1.0f / 65536.0f)) * p.v;
-    }
-    Wg[i] = p.weighting == 0 ? (float)g.n : (float)g.sw * (1.0f / 1048576.0f);
-    count[i] = g.n;
+    keys[3 * i] = gs[i].key.x;
+    keys[3 * i + 1] = gs[i].key.y;
+    keys[3 * i + 2] = gs[i].key.z;
+    for (int a = 0; a < 3; ++a) pbar[3 * i + a] = gs[i].ray.pbar[a];
+    Wg[i] = gs[i].ray.Wg;
+    count[i] = gs[i].count;
   }
   return (int64_t)gs.size();
 }

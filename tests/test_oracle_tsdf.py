@@ -387,3 +387,41 @@ def test_tsdf_near_surface_matches_true_sdf(plane_sphere_oracle):
     # and the sign agrees wherever the true surface is more than a voxel away
     far = (W > 0) & (np.abs(sdf) > 2 * v) & (np.abs(sdf) < 2.5 * v)
     assert np.mean(np.sign(D[far]) == np.sign(sdf[far])) > 0.99
+
+
+# ----------------------------------------- grouping through integrate(), worked by hand
+
+GROUP3 = os.path.join(os.path.dirname(__file__), "golden", "grouped_ray_three_points.json")
+
+
+@pytest.mark.parametrize("mode", ["constant", "quadratic"])
+def test_grouped_ray_of_three_points_through_integrate(mode):
+    """Three points in voxel (0,0,4) become one ray at their R1 weighted mean (half-weight
+    rounding term, integer point weights, a round-half-even tie under Eq. 4); the map that
+    integrate() builds carries the hand-worked D and W at two voxels of that ray. The D
+    values move by about 3e-6 m if the mean's rounding term or its weights are wrong."""
+    with open(GROUP3) as f:
+        g = json.load(f)
+    su, c = g["setup"], g[mode]
+    m = oracle.OracleMap(su["voxel_size"], su["voxels_per_block"], su["truncation"], su["max_esdf_dist"],
+                         weighting=c["weighting"], eps=su["eps"])
+    pts = np.array(su["points"], np.float32)
+    m.integrate(pts, np.eye(4, dtype=np.float32))
+    st = m.stats()
+    assert st["points_valid"] == 3 and st["groups"] == 1
+    ex = m.export()
+    idx = {tuple(k): i for i, k in enumerate(ex["keys"])}
+    B = su["voxels_per_block"]
+    for vc in c["voxels"]:
+        x, y, z = vc["voxel"]
+        b = idx[(x // B, y // B, z // B)]
+        l = ((z % B) * B + (y % B)) * B + (x % B)
+        assert ex["W"][b, l] == vc["W"], vc["working"]
+        assert abs(ex["D"][b, l] - vc["D"]) <= 1e-7, vc["working"]
+    # the grouping entry point returns the same group (it casts from the same function)
+    keys, pbar, Wg, cnt = oracle.group(
+        oracle.make_params(su["voxel_size"], B, su["truncation"], su["max_esdf_dist"], weighting=c["weighting"], eps=su["eps"]),
+        pts, np.eye(4, dtype=np.float32),
+    )
+    assert keys.tolist() == [[0, 0, 4]] and cnt.tolist() == [3]
+    assert pbar[0].astype(np.float64).tolist() == c["pbar"] and float(Wg[0]) == c["W_g"]
