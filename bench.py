@@ -1,13 +1,18 @@
 """Benchmark of the per-scan map update (TSDF integration + incremental ESDF + query batch).
 
 One step = one posed scan through the whole hot path: vbx_integrate_scan, vbx_update_esdf and a
-10k-point distance/gradient query batch, on the room workload (10 x 10 x 3 m, 30 frames of
-640x480 RGB-D, v = 0.05 m, 16^3 blocks, delta = 0.1 m, quadratic weight, d_max = 2 m).
-Frames cycle when steps exceed the sequence. Prints one JSON line (rank 0).
+10k-point distance/gradient query batch. The headline workload is the outdoor LiDAR growth
+sequence: 100 scans of a 64 x 2048-ray spinning LiDAR (60 m range) along a 400 m path over a
+200 x 200 m terrain with 300 buildings and 500 trees, v = 0.2 m, 8^3 blocks, delta = 0.6 m,
+d_max = 5 m. Steps advance along the path (warm-up scans first, then the timed ones); a step
+count beyond the 100 scans starts a fresh map at the beginning of the path (outside the timed
+events). The room RGB-D sequence, the batched and served forms, the ESDF methods and the mesh
+layer are further sections of the same JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl vbx|reference]
 
---impl reference times the CPU oracle (single thread) on the same workload instead.
+--impl reference times the CPU oracle (single thread) on a bounded sample of the same
+workload instead.
 """
 from __future__ import annotations
 
@@ -29,10 +34,20 @@ sys.path.insert(0, ROOT)
 
 METRIC = "scans/s & Mvoxel-updates/s (TSDF+ESDF), p50/p99 scan latency, batched vs plain"
 WORKLOAD = (
+    "outdoor LiDAR growth: 200x200 m terrain (8 sinusoids, 3 m), 300 box buildings, 500 trees; 100 scans of a "
+    "64x2048 spinning LiDAR (elevation -25..+15 deg, 60 m range, no-returns dropped, noise 2 cm) along a 400 m "
+    "path; v=0.2 m, 8^3 blocks, delta=0.6 m, constant weight, gamma=v, d_max=5 m, ESDF after every scan, "
+    "10k queries within 2 m of the sensor per scan; frames advance along the path"
+)
+ROOM_WORKLOAD = (
     "room 10x10x3 m, 20 objects, 30 frames 640x480 RGB-D (fx=fy=525), depth noise 0.0012 z^2, "
     "v=0.05 m, 16^3 blocks, delta=0.1 m, quadratic weight eps=v, gamma=v, d_max=2 m, "
     "ESDF after every frame, 10k queries within 2 m of the sensor per scan"
 )
+C3_SCANS = 100
+C3_BLOCKS = 1 << 17  # block pool of the growing LiDAR map (the 100 scans allocate about 46k blocks)
+C3_SCRATCH = 1 << 16  # scratch blocks: the blocks one scan's rays may enter
+REF_SECTORS = 16  # the reference arm integrates one azimuth sector of 2048 / 16 columns per step
 N_QUERIES = 10000
 FLUSH_BYTES = 256 << 20  # > 129 MB L2
 
@@ -101,12 +116,36 @@ def _cached(tag: str, make):
     return obj
 
 
+def _c3_scene(first: int = C3_SCANS):
+    """The outdoor LiDAR growth sequence (100 scans), generated in parallel and cached; with
+    first < 100, only the path's first scans."""
+    from paper_1611_03631_gb300 import scenes
+
+    n = min(first, C3_SCANS)
+    full = f"lidar_c3_{C3_SCANS}_seed3"
+    cache_dir = os.environ.get("VBX_SCENE_CACHE", os.path.join(tempfile.gettempdir(), "vbx_scene_cache"))
+    if n < C3_SCANS and not os.path.exists(os.path.join(cache_dir, full + ".pkl")):
+        return _cached(f"{full}_first{n}", lambda: scenes.lidar_terrain(scans=C3_SCANS, generate=n, workers=_workers()))
+    s = _cached(full, lambda: scenes.lidar_terrain(scans=C3_SCANS, workers=_workers()))
+    if n < C3_SCANS:
+        s.points, s.poses = s.points[:n], s.poses[:n]
+    return s
+
+
+def _frames(n_frames: int, warmup: int, steps: int) -> str:
+    """The frames the timed steps cover (the same string on both arms)."""
+    if warmup + steps <= n_frames:
+        return f"{warmup}..{warmup + steps - 1} of {n_frames}"
+    return f"{steps} steps over {n_frames} frames (fresh map at each restart of the sequence)"
+
+
 def _workers():
     return max(1, min(16, os.cpu_count() or 1))
 
 
 BATCH_MAPS = 64
 BATCH_FRAMES = 4
+BATCH_STEPS = 20  # timed steps of the batched sections (after 3 warm-up steps)
 SERVE_SESSIONS = 256
 SERVE_SLOTS = 128
 SERVE_BUDGET = 120e9
@@ -624,42 +663,36 @@ def _peaks():
 # ------------------------------------------------------------------------------ oracle arm
 
 
-def _oracle_steps(s, qs, frames_idx):
+def cpu_baseline_c3(s, qs, budget_s: float = 15.0):
+    """The oracle, as it stands, on the first scans of the LiDAR sequence (full 131072-ray
+    scans: TSDF, ESDF and 10k queries each), single thread, until budget_s of CPU work is spent
+    (at least one scan). Returns the baseline and the oracle map for the error report."""
     import oracle
 
     m = oracle.OracleMap.from_scene_params(s.params)
-    times = []
-    for i in frames_idx:
+    t_total, n = 0.0, 0
+    while n < len(s.points) and (n == 0 or t_total < budget_s):
         t0 = time.perf_counter()
-        m.integrate(s.points[i], s.poses[i])
+        m.integrate(s.points[n], s.poses[n])
         m.update_esdf()
-        m.query(qs[i])
-        times.append(time.perf_counter() - t0)
-    return times
-
-
-def cpu_baseline(s, qs, budget_s: float = 15.0, max_frames: int = 8):
-    import oracle
-
-    m = oracle.OracleMap.from_scene_params(s.params)
-    t_total = 0.0
-    n = 0
-    for i in range(min(max_frames, len(s.points))):
-        t0 = time.perf_counter()
-        m.integrate(s.points[i], s.poses[i])
-        m.update_esdf()
-        m.query(qs[i])
+        m.query(qs[n])
         t_total += time.perf_counter() - t0
         n += 1
-        if t_total > budget_s:
-            break
     return {
         "value": n / t_total,
         "unit": "scans/s",
         "cores": 1,
         "kind": "oracle",
-        "sample": f"first {n} frames of the room sequence (full 640x480, TSDF+ESDF+10k queries each), single thread",
-    }
+        "sample": f"first {n} scan(s) of the LiDAR sequence (64x2048 rays, TSDF + ESDF + 10k queries each), single thread, "
+        f"{t_total:.1f} s",
+        "scans": n,
+    }, m
+
+
+def _sector(points: np.ndarray, k: int, sectors: int, columns: int = 2048) -> np.ndarray:
+    """The rays of azimuth sector k (of `sectors`) of a 64 x columns LiDAR scan."""
+    w = columns // sectors
+    return np.ascontiguousarray(points.reshape(-1, columns, 3)[:, k * w : (k + 1) * w].reshape(-1, 3))
 
 
 def _oracle_map_worker(args):
@@ -702,16 +735,37 @@ def cpu_baseline_batched(sets, scans_per_map: int = 1):
 
 
 def run_reference(args):
+    """The oracle as it stands on a bounded sample of the headline workload: step k integrates
+    azimuth sector k mod 16 (64 x 128 rays) of scan k of the LiDAR path into one map, updates
+    the ESDF and answers 10k / 16 queries; the rate counts 1/16 scan per step."""
+    import oracle
+
     dist, rank, ws = _dist_init()
     if rank != 0:
         return 0
-    s = _scene(30)
-    qs = _queries(s, 30)
-    order = [(k % 30) for k in range(args.warmup + args.steps)]
-    times = _oracle_steps(s, qs, order)
+    s = _c3_scene(args.warmup + args.steps)
+    qs = _queries(s, len(s.points))
+    m = oracle.OracleMap.from_scene_params(s.params)
+    times = []
+    nq = N_QUERIES // REF_SECTORS
+    for k in range(args.warmup + args.steps):
+        i = k % len(s.points)
+        if k > 0 and i == 0:
+            m = oracle.OracleMap.from_scene_params(s.params)
+        p = _sector(s.points[i], k % REF_SECTORS, REF_SECTORS)
+        t0 = time.perf_counter()
+        m.integrate(p, s.poses[i])
+        m.update_esdf()
+        m.query(qs[i][:nq])
+        times.append(time.perf_counter() - t0)
     timed = times[args.warmup:]
     total = sum(timed)
-    value = args.steps / total
+    value = args.steps / REF_SECTORS / total
+    sample = (
+        f"{args.steps} timed steps after {args.warmup} warm-up steps; step k = azimuth sector k mod {REF_SECTORS} "
+        f"(64x{2048 // REF_SECTORS} rays) of LiDAR scan k, ESDF update and {nq} queries; 1/{REF_SECTORS} scan per step; "
+        "single thread"
+    )
     line = {
         "impl": "reference",
         "metric": METRIC,
@@ -726,16 +780,15 @@ def run_reference(args):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "parallelism": "single CPU thread (oracle)"},
+        "config": {
+            "workload": WORKLOAD,
+            "frames": _frames(C3_SCANS, args.warmup, args.steps),
+            "l2": "flushed between steps (256 MB write, outside the per-step events); the map (GBs) exceeds L2",
+            "parallelism": f"replicas x{ws} (independent maps, no collective)",
+        },
         "p50_ms": 1000.0 * float(np.percentile(timed, 50)),
         "p99_ms": 1000.0 * float(np.percentile(timed, 99)),
-        "cpu_baseline": {
-            "value": value,
-            "unit": "scans/s",
-            "cores": 1,
-            "kind": "oracle",
-            "sample": f"{args.steps} timed frames of the room sequence after {args.warmup} warm-up frames, single thread",
-        },
+        "cpu_baseline": {"value": value, "unit": "scans/s", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "scans/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -745,12 +798,319 @@ def run_reference(args):
 # --------------------------------------------------------------------------------- GPU arm
 
 
+def _schedule(n_frames: int, warmup: int, steps: int):
+    """(frame, fresh map before it) for every warm-up and timed step: frames advance along the
+    sequence; past its end a fresh map starts at its beginning."""
+    return [(k % n_frames, k > 0 and k % n_frames == 0) for k in range(warmup + steps)]
+
+
+def _alg_bytes(st, n_pts: int, B: int):
+    """Algorithmic bytes of one scan per kernel: what the method must move (not what an
+    implementation happens to move). TSDF: 12 B per input point; 16 B per group (mean, weight);
+    16 B per updated voxel ({D, W} read and write), charged to the ray kernel (which produces
+    the per-voxel sums) and to the merge kernel. ESDF: 8 B per consumed TSDF voxel, 16 B per
+    processed voxel (ESDF read and write), and each staged tile with its one-voxel halo,
+    (E+2)^3 x 8 B for tiles of edge E = 8."""
+    tile = (min(B, 8) + 2) ** 3 * 8
+    return {
+        "bin_points": 12 * n_pts,
+        "group_rays": 16 * st["rays"],
+        "integrate_rays": 16 * st["rays"] + 16 * st["updated"],
+        "apply": 16 * st["updated"],
+        "tsdf_total": 12 * n_pts + 16 * st["rays"] + 16 * st["updated"],
+        "esdf": 8 * st["esdf_in"] + 16 * (st["raise_pops"] + st["lower_pops"]) + tile * st["esdf_block_visits"],
+        "query": N_QUERIES * (12 + 16 + 8 * 8),
+    }
+
+
+TSDF_KERNELS = ("bin_points", "group_rays", "link_blocks", "integrate_rays", "apply")
+
+
+def _roofline_entry(kernel, ms, launches, alg, peak, peaks):
+    per = ms / max(launches, 1)
+    b = alg / max(launches, 1)
+    ach = b / (per * 1e-3) / 1e9 if per > 0 else 0.0
+    return {
+        "bound": "hbm",
+        "kernel": kernel,
+        "achieved": ach,
+        "peak": peak,
+        "unit": "GB/s",
+        "frac": ach / peak,
+        "traffic": _ncu_traffic(kernel),
+        "bytes_per_launch": b,
+        "ms_per_launch": per,
+        "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6800 GB/s",
+    }
+
+
+def run_plain(args, vbx, torch, dev, s, qs, map_kw, flush, dist=None, ws=1, local=0, headline=False):
+    """The plain per-scan path on one map: a timed pass (CUDA events around each step, L2
+    flushed between steps outside the events), a per-kernel pass (the library's own events on
+    the launching stream) for the roofline, and an end-to-end pass from pinned host buffers."""
+    F = len(s.points)
+    B = int(s.params["voxels_per_block"])
+    n_max = max(int(p.shape[0]) for p in s.points)
+    pts_dev = [torch.from_numpy(p).to(dev) for p in s.points]
+    q_dev = [torch.from_numpy(q).to(dev) for q in qs]
+    out = (
+        torch.empty(N_QUERIES, dtype=torch.float32, device=dev),
+        torch.empty((N_QUERIES, 3), dtype=torch.float32, device=dev),
+        torch.empty(N_QUERIES, dtype=torch.uint8, device=dev),
+    )
+    stream = torch.cuda.current_stream()
+    sched = _schedule(F, args.warmup, args.steps)
+
+    def new_map():
+        return vbx.Map.from_scene_params(s.params, max_points=n_max, **map_kw)
+
+    def step(m, i):
+        m.integrate_scan(pts_dev[i], s.poses[i])
+        m.update_esdf()
+        m.query(q_dev[i], out=out)
+
+    # ---------------------------------------------------------------- timed pass
+    m = new_map()
+    for i, fresh in sched[: args.warmup]:
+        if fresh:
+            m.reset()
+        step(m, i)
+    m.sync()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local) if headline else None
+    if clocks:
+        clocks.start()
+    launches0 = vbx.total_launches()
+    step_ms = []
+    tot = dict(tsdf=0, esdf=0, records=0, rounds=0, visits=0, liters=0, rays=0, new_blocks=0)
+    phase_ns = [0, 0, 0]
+    for i, fresh in sched[args.warmup :]:
+        if fresh:
+            m.reset()
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(m, i)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        st = m.stats()
+        tot["tsdf"] += st["updated"]
+        tot["esdf"] += st["raise_pops"] + st["lower_pops"]
+        tot["records"] += st["records"]
+        tot["rays"] += st["rays"]
+        tot["new_blocks"] += st["new_blocks"]
+        tot["rounds"] += st["raise_rounds"] + st["lower_rounds"]
+        tot["visits"] += st["esdf_block_visits"]
+        tot["liters"] += st["esdf_local_iters"]
+        phase_ns[0] += st["esdf_classify_ns"]
+        phase_ns[1] += st["esdf_raise_ns"]
+        phase_ns[2] += st["esdf_lower_ns"]
+    torch.cuda.synchronize()
+    gpu_launches = vbx.total_launches() - launches0
+    clk = clocks.stop() if clocks else None
+    final_blocks = m.num_blocks()
+    m.sync()
+    max_ms, value = whole_job_rate(dist, float(sum(step_ms)), args.steps, ws, dev)
+    if dist is not None:
+        dist.barrier()
+    m.close()
+
+    # ------------------------------------------------------- per-kernel timing pass
+    mp = new_map()
+    for i, fresh in sched[: args.warmup]:
+        if fresh:
+            mp.reset()
+        step(mp, i)
+    mp.sync()
+    mp.set_profiling(True)
+    mp.reset_kernel_times()
+    alg = {}
+    kt = {}
+
+    def add_times():
+        for k, v in mp.kernel_times().items():
+            a = kt.setdefault(k, {"ms": 0.0, "launches": 0})
+            a["ms"] += v["ms"]
+            a["launches"] += v["launches"]
+
+    for i, fresh in sched[args.warmup :]:
+        if fresh:  # a fresh map: the reset's own launches stay out of the kernel totals
+            add_times()
+            mp.set_profiling(False)
+            mp.reset()
+            mp.reset_kernel_times()
+            mp.set_profiling(True)
+        flush.zero_()
+        step(mp, i)
+        for k, v in _alg_bytes(mp.stats(), int(pts_dev[i].shape[0]), B).items():
+            alg[k] = alg.get(k, 0) + v
+    add_times()
+    mp.close()
+    peaks = _peaks()
+    peak = float(peaks["hbm_gbs"]) if peaks and "hbm_gbs" in peaks else 6800.0
+    live = {k: v for k, v in kt.items() if v["launches"]}
+    dom = max(live, key=lambda k: live[k]["ms"])
+    kernels = {
+        k: _roofline_entry(k, live[k]["ms"], live[k]["launches"], alg[k], peak, peaks)
+        for k in ("integrate_rays", "apply", "esdf", "bin_points", "group_rays", "query")
+        if k in live and k in alg
+    }
+    tsdf_ms = sum(live[k]["ms"] for k in TSDF_KERNELS if k in live)
+    kernels["tsdf_total"] = _roofline_entry("tsdf_total", tsdf_ms, args.steps, alg["tsdf_total"], peak, peaks)
+    kernels["tsdf_total"]["kernels"] = list(TSDF_KERNELS)
+    roofline = dict(kernels[dom]) if dom in kernels else _roofline_entry(dom, live[dom]["ms"], live[dom]["launches"], 0, peak, peaks)
+    roofline["kernels"] = kernels
+    roofline["kernels_ms_per_step"] = {k: v["ms"] / args.steps for k, v in live.items()}
+
+    # ------------------------------------------------------------------- e2e pass
+    me = new_map()
+    pin_pts = [torch.from_numpy(p).pin_memory() for p in s.points]
+    pin_q = [torch.from_numpy(q).pin_memory() for q in qs]
+    h_out = (
+        torch.empty(N_QUERIES, dtype=torch.float32).pin_memory(),
+        torch.empty((N_QUERIES, 3), dtype=torch.float32).pin_memory(),
+        torch.empty(N_QUERIES, dtype=torch.uint8).pin_memory(),
+    )
+    d_pts = torch.empty((n_max, 3), dtype=torch.float32, device=dev)
+    d_q = torch.empty((N_QUERIES, 3), dtype=torch.float32, device=dev)
+
+    def e2e_step(i):
+        n = pin_pts[i].shape[0]
+        d_pts[:n].copy_(pin_pts[i], non_blocking=True)
+        d_q.copy_(pin_q[i], non_blocking=True)
+        me.integrate_scan(d_pts[:n], s.poses[i])
+        me.update_esdf()
+        me.query(d_q, out=out)
+        for h, d in zip(h_out, out):
+            h.copy_(d, non_blocking=True)
+
+    for i, fresh in sched[: args.warmup]:
+        if fresh:
+            me.reset()
+        e2e_step(i)
+    torch.cuda.synchronize()
+    e2e_ms = []
+    for i, fresh in sched[args.warmup :]:
+        if fresh:
+            me.reset()
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        e2e_step(i)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    me.close()
+    timed = [i for i, _ in sched[args.warmup :]]
+    h2d = int(np.mean([pin_pts[i].numel() * 4 for i in timed])) + N_QUERIES * 12
+    d2h = N_QUERIES * (4 + 12 + 1)
+    _, e2e_value = whole_job_rate(dist, float(sum(e2e_ms)), args.steps, ws, dev)
+    secs = max_ms / 1000.0
+    return {
+        "value": value,
+        "unit": "scans/s",
+        "ms_per_step": max_ms / args.steps,
+        "p50_ms": float(np.percentile(step_ms, 50)),
+        "p99_ms": float(np.percentile(step_ms, 99)),
+        "frames": _frames(F, args.warmup, args.steps),
+        "mvox_updates_per_s": {
+            "tsdf": tot["tsdf"] * ws / secs / 1e6,
+            "esdf": tot["esdf"] * ws / secs / 1e6,
+            "total": (tot["tsdf"] + tot["esdf"]) * ws / secs / 1e6,
+            "ray_voxel_records": tot["records"] * ws / secs / 1e6,
+        },
+        "per_scan": {
+            "rays": tot["rays"] / args.steps,
+            "records": tot["records"] / args.steps,
+            "tsdf_updates": tot["tsdf"] / args.steps,
+            "esdf_pops": tot["esdf"] / args.steps,
+            "new_blocks": tot["new_blocks"] / args.steps,
+            "esdf_tile_visits": tot["visits"] / args.steps,
+        },
+        "blocks_at_end": int(final_blocks),
+        "esdf_rounds_per_scan": tot["rounds"] / args.steps,
+        "esdf_local_iters_per_visit": tot["liters"] / max(tot["visits"], 1),
+        "esdf_phase_ms_per_scan": {k: v / 1e6 / args.steps for k, v in zip(("classify", "raise", "lower"), phase_ns)},
+        "roofline": roofline,
+        "e2e": {"value": e2e_value, "unit": "scans/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(gpu_launches),
+        "clocks": clk,
+    }
+
+
+def max_err_first_scans(vbx, torch, dev, s, qs, n_scans: int, map_kw, oracle_map=None):
+    """Per-result maximum error of the GPU path (float32) against the float64-accumulated
+    oracle after the first n_scans scans (the scans the CPU leg runs): TSDF D and W on the
+    observed voxels, ESDF d (guard-band rule: seeds whose float64 TSDF value lies within 1e-5 m
+    of the band edge or of zero may differ; their d_max neighbourhood is left out), and the
+    query distance and gradient where both sides report a known value."""
+    import oracle
+
+    g = vbx.Map.from_scene_params(s.params, max_points=max(int(p.shape[0]) for p in s.points), **map_kw)
+    o = oracle_map
+    if o is None:
+        o = oracle.OracleMap.from_scene_params(s.params)
+        for i in range(n_scans):
+            o.integrate(s.points[i], s.poses[i])
+            o.update_esdf()
+    for i in range(n_scans):
+        g.integrate_scan(torch.from_numpy(s.points[i]).to(dev), s.poses[i])
+        g.update_esdf()
+    qd, qg, qs_ = g.query(torch.from_numpy(qs[n_scans - 1]).to(dev))
+    g.sync()
+    gex, oex = g.export(), o.export()
+    g.close()
+    same_blocks = bool(np.array_equal(gex["keys"], oex["keys"]))
+    res = {"scans": n_scans, "blocks_bit_exact": same_blocks}
+    if not same_blocks:
+        return res
+    gobs, oobs = gex["W"] > 0, oex["W"] > 0
+    res["observed_bit_exact"] = bool(np.array_equal(gobs, oobs))
+    obs = gobs & oobs
+    res["tsdf_D_m"] = float(np.max(np.abs(gex["D"][obs].astype(np.float64) - oex["D"][obs]), initial=0.0))
+    res["tsdf_W_rel"] = float(np.max(np.abs(gex["W"][obs].astype(np.float64) - oex["W"][obs]) / oex["W"][obs], initial=0.0))
+    p = s.params
+    gamma = np.float32(p["fixed_band"])
+    Do = oex["D"].astype(np.float32)
+    eobs = (oex["flags"] & 1) > 0
+    ambiguous = (np.abs(np.abs(Do) - gamma) < 1e-5) | (np.abs(Do) < 1e-5)
+    gfix, ofix = (gex["flags"] & 2) > 0, (oex["flags"] & 2) > 0
+    diff = ((gfix != ofix) | (np.sign(gex["D"]) != np.sign(Do))) & eobs
+    res["seed_differences_outside_guard_band"] = int(np.sum(diff & ~ambiguous))
+    res["seed_differences_in_guard_band"] = int(np.sum(diff & ambiguous))
+    mask = eobs & ((gex["flags"] & 1) > 0)
+    if np.any(diff):
+        B = int(p["voxels_per_block"])
+        l = np.arange(B ** 3)
+        loc = np.stack([l % B, (l // B) % B, l // (B * B)], -1)
+        vc = gex["keys"][:, None, :] * B + loc[None]
+        r = int(math.ceil(p["max_esdf_dist"] / p["voxel_size"])) + 1
+        for c in vc[diff]:
+            mask &= ~(np.max(np.abs(vc - c), axis=-1) <= r)
+    res["esdf_d_m"] = float(np.max(np.abs(gex["d"][mask].astype(np.float64) - oex["d"][mask]), initial=0.0))
+    od, og, ost = o.query(qs[n_scans - 1])
+    gst = qs_.cpu().numpy()
+    res["query_status_mismatches"] = int(np.sum(gst != ost))
+    known = (gst == 0) & (ost == 0)
+    res["query_known"] = int(known.sum())
+    res["query_d_m"] = float(np.max(np.abs(qd.cpu().numpy()[known].astype(np.float64) - od[known]), initial=0.0))
+    res["query_grad"] = float(np.max(np.abs(qg.cpu().numpy()[known].astype(np.float64) - og[known]), initial=0.0))
+    res["note"] = "GPU float32 throughout; oracle float64-accumulated TSDF and ESDF"
+    return res
+
+
 def run_gpu(args):
     import torch
 
     dist, rank, ws = _dist_init()
     local = int(os.environ.get("LOCAL_RANK", "0"))
     # scene generation uses spawned worker processes: do it before the first CUDA call
+    c3 = _c3_scene()
     if not args.no_batched and not args.only_batched_plane_sphere:
         _batch_sets()
     if not args.no_served and not (args.only_batched or args.only_batched_plane_sphere):
@@ -761,155 +1121,30 @@ def run_gpu(args):
     __graft_entry__.build()
     from paper_1611_03631_gb300 import vbx
 
+    dev = torch.device("cuda", local)
     if args.only_batched:
-        dev = torch.device("cuda", local)
         print(json.dumps({"batched": run_batched(args, vbx, torch, dev)}), flush=True)
         return 0
     if args.only_batched_plane_sphere:
-        dev = torch.device("cuda", local)
         print(json.dumps({"batched_plane_sphere": run_batched_plane_sphere(args, vbx, torch, dev, n_maps=args.batch_maps)}), flush=True)
         return 0
 
-    F = 30
-    s = _scene(F)
-    qs = _queries(s, F)
-    dev = torch.device("cuda", local)
-    pts_dev = [torch.from_numpy(p).to(dev) for p in s.points]
-    q_dev = [torch.from_numpy(q).to(dev) for q in qs]
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    dist_o = torch.empty(N_QUERIES, dtype=torch.float32, device=dev)
-    grad_o = torch.empty((N_QUERIES, 3), dtype=torch.float32, device=dev)
-    stat_o = torch.empty(N_QUERIES, dtype=torch.uint8, device=dev)
-    out = (dist_o, grad_o, stat_o)
-    stream = torch.cuda.current_stream()
-    order = [(k % F) for k in range(args.warmup + args.steps)]
+    c3_qs = _queries(c3, len(c3.points))
+    c3_kw = dict(block_capacity=C3_BLOCKS, scratch_blocks=C3_SCRATCH)
+    head = run_plain(args, vbx, torch, dev, c3, c3_qs, c3_kw, flush, dist=dist, ws=ws, local=local, headline=True)
+    if args.only_headline:
+        args.no_batched = args.no_served = args.no_room = True
+        args.esdf_methods = args.mesh = False
 
-    def new_map():
-        return vbx.Map.from_scene_params(s.params, max_points=640 * 480)
-
-    def step(m, i):
-        m.integrate_scan(pts_dev[i], s.poses[i])
-        m.update_esdf()
-        m.query(q_dev[i], out=out)
-
-    # ---------------------------------------------------------------- timed pass
-    m = new_map()
-    for i in order[: args.warmup]:
-        step(m, i)
-    m.sync()
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks = Clocks(local)
-    clocks.start()
-    launches0 = vbx.total_launches()
-    step_ms, tsdf_upd, esdf_upd, records, rounds, visits, liters = [], 0, 0, 0, 0, 0, 0
-    phase_ns = [0, 0, 0]
-    for i in order[args.warmup:]:
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step(m, i)
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        st = m.stats()
-        tsdf_upd += st["updated"]
-        esdf_upd += st["raise_pops"] + st["lower_pops"]
-        records += st["records"]
-        rounds += st["raise_rounds"] + st["lower_rounds"]
-        visits += st["esdf_block_visits"]
-        liters += st["esdf_local_iters"]
-        phase_ns[0] += st["esdf_classify_ns"]
-        phase_ns[1] += st["esdf_raise_ns"]
-        phase_ns[2] += st["esdf_lower_ns"]
-    torch.cuda.synchronize()
-    gpu_launches = vbx.total_launches() - launches0 - 0
-    clk = clocks.stop()
-    max_ms, value = whole_job_rate(dist, float(sum(step_ms)), args.steps, ws, dev)
-    if dist is not None:
-        dist.barrier()
-    m.close()
-
-    # ------------------------------------------------------- per-kernel timing pass
-    mp = new_map()
-    for i in order[: args.warmup]:
-        step(mp, i)
-    mp.sync()
-    mp.set_profiling(True)
-    mp.reset_kernel_times()
-    per_kernel_units = {"esdf": 0, "integrate_rays": 0, "apply": 0, "bin_points": 0, "query": 0}
-    alg_bytes = {k: 0 for k in per_kernel_units}
-    for i in order[args.warmup:]:
-        flush.zero_()
-        step(mp, i)
-        st = mp.stats()
-        n_pts = int(pts_dev[i].shape[0])
-        # algorithmic bytes per launch (see the design notes): minimal traffic the method needs
-        alg_bytes["bin_points"] += 12 * n_pts
-        alg_bytes["integrate_rays"] += 16 * st["rays"] + 16 * st["updated"]
-        alg_bytes["apply"] += 16 * st["updated"]
-        alg_bytes["esdf"] += 8 * st["esdf_in"] + 16 * (st["raise_pops"] + st["lower_pops"])
-        alg_bytes["query"] += N_QUERIES * (12 + 16 + 8 * 8)
-    kt = mp.kernel_times()
-    mp.close()
-    dom = max((k for k in kt if kt[k]["launches"] > 0), key=lambda k: kt[k]["ms"])
-    peaks = _peaks()
-    peak = float(peaks["hbm_gbs"]) if peaks and "hbm_gbs" in peaks else 6800.0
-    dom_ms_per_launch = kt[dom]["ms"] / max(kt[dom]["launches"], 1)
-    dom_bytes_per_launch = alg_bytes.get(dom, 0) / max(kt[dom]["launches"], 1)
-    achieved = dom_bytes_per_launch / (dom_ms_per_launch * 1e-3) / 1e9 if dom_ms_per_launch > 0 else 0.0
-    roofline = {
-        "bound": "hbm",
-        "kernel": dom,
-        "achieved": achieved,
-        "peak": peak,
-        "unit": "GB/s",
-        "frac": achieved / peak,
-        "traffic": _ncu_traffic(dom),
-        "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6800 GB/s",
-        "kernels_ms_per_step": {k: v["ms"] / args.steps for k, v in kt.items() if v["launches"]},
-    }
-
-    # ------------------------------------------------------------------- e2e pass
-    me = new_map()
-    pin_pts = [torch.from_numpy(p).pin_memory() for p in s.points]
-    pin_q = [torch.from_numpy(q).pin_memory() for q in qs]
-    h_dist = torch.empty(N_QUERIES, dtype=torch.float32).pin_memory()
-    h_grad = torch.empty((N_QUERIES, 3), dtype=torch.float32).pin_memory()
-    h_stat = torch.empty(N_QUERIES, dtype=torch.uint8).pin_memory()
-    d_pts = torch.empty((640 * 480, 3), dtype=torch.float32, device=dev)
-    d_q = torch.empty((N_QUERIES, 3), dtype=torch.float32, device=dev)
-
-    def e2e_step(i):
-        n = pin_pts[i].shape[0]
-        d_pts[:n].copy_(pin_pts[i], non_blocking=True)
-        d_q.copy_(pin_q[i], non_blocking=True)
-        me.integrate_scan(d_pts[:n], s.poses[i])
-        me.update_esdf()
-        me.query(d_q, out=out)
-        h_dist.copy_(dist_o, non_blocking=True)
-        h_grad.copy_(grad_o, non_blocking=True)
-        h_stat.copy_(stat_o, non_blocking=True)
-
-    for i in order[: args.warmup]:
-        e2e_step(i)
-    torch.cuda.synchronize()
-    e2e_ms = []
-    for i in order[args.warmup:]:
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        e2e_step(i)
-        e1.record(stream)
-        e1.synchronize()
-        e2e_ms.append(e0.elapsed_time(e1))
-    me.close()
-    h2d = int(np.mean([pin_pts[i].numel() * 4 for i in order[args.warmup:]])) + N_QUERIES * 12
-    d2h = N_QUERIES * (4 + 12 + 1)
-    e2e_total, e2e_value = whole_job_rate(dist, float(sum(e2e_ms)), args.steps, ws, dev)
+    room = s_room = None
+    if not args.no_room:
+        s_room = _scene(30)
+        room_qs = _queries(s_room, 30)
+        room_args = argparse.Namespace(**vars(args))
+        room_args.steps, room_args.warmup = 30, 3
+        room = run_plain(room_args, vbx, torch, dev, s_room, room_qs, {}, flush)
+        room["workload"] = ROOM_WORKLOAD + "; 30 timed steps cycling the sequence after 3 warm-up frames"
 
     esdf_cmp = None
     if args.esdf_methods and rank == 0:
@@ -922,30 +1157,36 @@ def run_gpu(args):
             "delta=4v, constant weight, d_max=2 m; errors over observed free voxels with true distance in (0, 1.5] m"
         )
     mesh = None
-    if args.mesh and rank == 0:
-        mesh = run_mesh(args, vbx, torch, dev, s, pts_dev, flush)
+    if args.mesh and rank == 0 and s_room is not None:
+        pts_room = [torch.from_numpy(p).to(dev) for p in s_room.points]
+        mesh = run_mesh(args, vbx, torch, dev, s_room, pts_room, flush)
     batched = batched_c1 = served = None
     if not args.no_batched:
-        batched = run_batched(args, vbx, torch, dev)
+        bargs = argparse.Namespace(**vars(args))
+        bargs.steps, bargs.warmup = BATCH_STEPS, 3
+        batched = run_batched(bargs, vbx, torch, dev)
         if not args.no_cpu_baseline and rank == 0:
             batched["cpu_baseline"] = cpu_baseline_batched(_batch_sets(args.batch_maps))
-        batched_c1 = run_batched_plane_sphere(args, vbx, torch, dev)
+        batched_c1 = run_batched_plane_sphere(bargs, vbx, torch, dev)
         # a smaller batch: lower step latency at a lower throughput
-        batched_c1["with_32_maps"] = run_batched_plane_sphere(args, vbx, torch, dev, n_maps=32)
+        batched_c1["with_32_maps"] = run_batched_plane_sphere(bargs, vbx, torch, dev, n_maps=32)
     if not args.no_served:
         served = run_served(args, vbx, torch)
     if rank != 0:
         return 0
-    cpu = None if args.no_cpu_baseline else cpu_baseline(s, qs)
-    secs = max_ms / 1000.0
+    cpu = max_err = None
+    if not args.no_cpu_baseline:
+        cpu, omap = cpu_baseline_c3(c3, c3_qs)
+        max_err = max_err_first_scans(vbx, torch, dev, c3, c3_qs, cpu["scans"], c3_kw, oracle_map=omap)
+        del cpu["scans"]
     line = {
         "metric": METRIC,
-        "value": value,
+        "value": head["value"],
         "unit": "scans/s",
         "n_gpus": ws,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": max_ms / args.steps,
+        "ms_per_step": head["ms_per_step"],
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
@@ -953,32 +1194,27 @@ def run_gpu(args):
         "data": "synthetic",
         "config": {
             "workload": WORKLOAD,
-            "l2": "flushed between steps (256 MB write, outside the per-step events)",
+            "frames": _frames(C3_SCANS, args.warmup, args.steps),
+            "l2": "flushed between steps (256 MB write, outside the per-step events); the map (GBs) exceeds L2",
             "parallelism": f"replicas x{ws} (independent maps, no collective)",
         },
-        "p50_ms": float(np.percentile(step_ms, 50)),
-        "p99_ms": float(np.percentile(step_ms, 99)),
-        "mvox_updates_per_s": {
-            "tsdf": tsdf_upd * ws / secs / 1e6,
-            "esdf": esdf_upd * ws / secs / 1e6,
-            "total": (tsdf_upd + esdf_upd) * ws / secs / 1e6,
-            "ray_voxel_records": records * ws / secs / 1e6,
-        },
-        "esdf_rounds_per_scan": rounds / args.steps,  # 2: one work queue per wave (single map)
-        "esdf_block_visits_per_scan": visits / args.steps,
-        "esdf_local_iters_per_visit": liters / max(visits, 1),
-        "esdf_phase_ms_per_scan": {k: v / 1e6 / args.steps for k, v in zip(("classify", "raise", "lower"), phase_ns)},
-        "roofline": roofline,
+    }
+    for k in ("p50_ms", "p99_ms", "mvox_updates_per_s", "per_scan", "blocks_at_end", "esdf_rounds_per_scan",
+              "esdf_local_iters_per_visit", "esdf_phase_ms_per_scan", "roofline"):
+        line[k] = head[k]
+    line.update({
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_value, "unit": "scans/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": int(gpu_launches),
-        "clocks": clk,
+        "max_err": max_err,
+        "e2e": head["e2e"],
+        "gpu_launches": head["gpu_launches"],
+        "clocks": head["clocks"],
+        "room": room,
         "batched": batched,
         "batched_plane_sphere": batched_c1,
         "esdf_methods": esdf_cmp,
         "mesh": mesh,
         "served": served,
-    }
+    })
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -988,12 +1224,14 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=C3_SCANS - 3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="vbx", choices=["vbx", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-map batched section")
     ap.add_argument("--no-served", action="store_true", help="skip the served-sessions section")
+    ap.add_argument("--no-room", action="store_true", help="skip the room RGB-D section")
+    ap.add_argument("--only-headline", action="store_true", help="the LiDAR headline (and its CPU leg) alone")
     ap.add_argument(
         "--esdf-methods", action=argparse.BooleanOptionalAction, default=True,
         help="the ESDF-method comparison on the simulated benchmark scene (occupancy, half band, one-voxel band)",

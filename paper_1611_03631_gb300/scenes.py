@@ -398,6 +398,57 @@ class _Terrain:
         return t_hit
 
 
+def _lidar_scan(args):
+    """Scan k of a LiDAR world (run in a worker process when scans are generated in parallel).
+    The range noise of scan k comes from its own generator, seeded by (seed, k), so the scans
+    do not depend on how many workers generate them or in which order."""
+    w, k = args
+    ter, pxy, dirs = w["terrain"], w["pxy"], w["dirs"]
+    beams, columns, max_range = w["beams"], w["columns"], w["max_range"]
+    buildings, trees, b_center, t_center = w["buildings"], w["trees"], w["b_center"], w["t_center"]
+    azim = np.arange(columns) * (2 * math.pi / columns)
+    xy = pxy[k]
+    pos = np.array([xy[0], xy[1], float(ter.h(xy[0], xy[1])) + w["sensor_height"]])
+    tang = pxy[k + 1] - pxy[k]
+    yaw = math.atan2(tang[1], tang[0])
+    R = _yaw_lidar(yaw)
+    uw = dirs @ R.T
+    o = np.broadcast_to(pos, uw.shape).copy()
+    t = ter.hit(o, uw, max_range)
+    col_az = yaw + azim  # world azimuth of each column
+
+    def _cols(center, rb):
+        dvec = center - xy
+        D = float(np.hypot(dvec[0], dvec[1]))
+        if D <= rb:
+            return np.arange(columns)
+        phi = math.atan2(dvec[1], dvec[0])
+        hw = math.asin(min(1.0, rb / D)) + 2.0 * (2 * math.pi / columns)
+        diff = np.angle(np.exp(1j * (col_az - phi)))
+        return np.nonzero(np.abs(diff) <= hw)[0]
+
+    def _rays(cols):
+        return (np.arange(beams)[:, None] * columns + cols[None, :]).reshape(-1)
+
+    for i in np.nonzero(np.linalg.norm(b_center - xy, axis=1) < max_range + 15.0)[0] if len(b_center) else []:
+        lo, hi = buildings[i]
+        rb = 0.5 * float(np.hypot(hi[0] - lo[0], hi[1] - lo[1]))
+        ri = _rays(_cols(b_center[i], rb))
+        if ri.size:
+            t[ri] = np.minimum(t[ri], _hit_box_outside(o[ri], uw[ri], lo, hi))
+    for i in np.nonzero(np.linalg.norm(t_center - xy, axis=1) < max_range + 1.0)[0] if len(t_center) else []:
+        c, r, z0, z1 = trees[i]
+        ri = _rays(_cols(c, r))
+        if ri.size:
+            t[ri] = np.minimum(t[ri], _hit_cylinder_z(o[ri], uw[ri], c, r, z0, z1))
+    t = np.where(t <= max_range, t, np.inf)
+    t = t + np.random.default_rng([w["seed"], 7, k]).normal(0.0, w["noise"], size=t.shape)
+    with np.errstate(invalid="ignore"):
+        p = dirs * t[:, None]
+    p[~np.isfinite(t)] = np.nan
+    return p.astype(np.float32), _pose(R, pos)
+
+
 def lidar_terrain(
     scans: int = 100,
     beams: int = 64,
@@ -411,8 +462,13 @@ def lidar_terrain(
     seed: int = 3,
     voxel_size: float = 0.2,
     sensor_height: float = 2.0,
+    workers: int = 0,
+    generate: Optional[int] = None,
 ) -> ScanSet:
-    """Spinning LiDAR over a heightfield with box buildings and cylinder trees."""
+    """Spinning LiDAR over a heightfield with box buildings and cylinder trees. The scans are
+    generated in `workers` spawned processes when workers > 1 (same result as one process).
+    `generate` limits the output to the first scans of the `scans`-scan path (the same scans
+    the full sequence starts with)."""
     rng = np.random.default_rng(seed)
     ter = _Terrain(rng)
     half = extent / 2.0
@@ -445,55 +501,34 @@ def lidar_terrain(
             continue
         base = float(ter.h(c[0], c[1])) - 0.5
         trees.append((c, r, base, base + 0.5 + h))
-    b_center = np.array([0.5 * (b[0][:2] + b[1][:2]) for b in buildings]) if buildings else np.zeros((0, 2))
-    t_center = np.array([t[0] for t in trees]) if trees else np.zeros((0, 2))
     elev = np.deg2rad(np.linspace(-25.0, 15.0, beams))
     azim = np.arange(columns) * (2 * math.pi / columns)
     E, A = np.meshgrid(elev, azim, indexing="ij")
-    dirs = np.stack([np.cos(E) * np.cos(A), np.cos(E) * np.sin(A), np.sin(E)], -1).reshape(-1, 3)
-    pts, poses = [], []
-    for k in range(scans):
-        xy = pxy[k]
-        pos = np.array([xy[0], xy[1], float(ter.h(xy[0], xy[1])) + sensor_height])
-        tang = pxy[k + 1] - pxy[k]
-        yaw = math.atan2(tang[1], tang[0])
-        R = _yaw_lidar(yaw)
-        uw = dirs @ R.T
-        o = np.broadcast_to(pos, uw.shape).copy()
-        t = ter.hit(o, uw, max_range)
-        col_az = yaw + azim  # world azimuth of each column
+    world = dict(
+        terrain=ter,
+        pxy=pxy,
+        dirs=np.stack([np.cos(E) * np.cos(A), np.cos(E) * np.sin(A), np.sin(E)], -1).reshape(-1, 3),
+        beams=beams,
+        columns=columns,
+        max_range=max_range,
+        noise=noise,
+        seed=seed,
+        sensor_height=sensor_height,
+        buildings=buildings,
+        trees=trees,
+        b_center=np.array([0.5 * (b[0][:2] + b[1][:2]) for b in buildings]) if buildings else np.zeros((0, 2)),
+        t_center=np.array([t[0] for t in trees]) if trees else np.zeros((0, 2)),
+    )
+    jobs = [(world, k) for k in range(scans if generate is None else min(scans, generate))]
+    if workers and workers > 1 and len(jobs) > 1:
+        import multiprocessing as mp
 
-        def _cols(center, rb):
-            dvec = center - xy
-            D = float(np.hypot(dvec[0], dvec[1]))
-            if D <= rb:
-                return np.arange(columns)
-            phi = math.atan2(dvec[1], dvec[0])
-            hw = math.asin(min(1.0, rb / D)) + 2.0 * (2 * math.pi / columns)
-            diff = np.angle(np.exp(1j * (col_az - phi)))
-            return np.nonzero(np.abs(diff) <= hw)[0]
-
-        def _rays(cols):
-            return (np.arange(beams)[:, None] * columns + cols[None, :]).reshape(-1)
-
-        for i in np.nonzero(np.linalg.norm(b_center - xy, axis=1) < max_range + 15.0)[0]:
-            lo, hi = buildings[i]
-            rb = 0.5 * float(np.hypot(hi[0] - lo[0], hi[1] - lo[1]))
-            ri = _rays(_cols(b_center[i], rb))
-            if ri.size:
-                t[ri] = np.minimum(t[ri], _hit_box_outside(o[ri], uw[ri], lo, hi))
-        for i in np.nonzero(np.linalg.norm(t_center - xy, axis=1) < max_range + 1.0)[0]:
-            c, r, z0, z1 = trees[i]
-            ri = _rays(_cols(c, r))
-            if ri.size:
-                t[ri] = np.minimum(t[ri], _hit_cylinder_z(o[ri], uw[ri], c, r, z0, z1))
-        t = np.where(t <= max_range, t, np.inf)
-        t = t + rng.normal(0.0, noise, size=t.shape)
-        with np.errstate(invalid="ignore"):
-            p = dirs * t[:, None]
-        p[~np.isfinite(t)] = np.nan
-        pts.append(p.astype(np.float32))
-        poses.append(_pose(R, pos))
+        with mp.get_context("spawn").Pool(min(workers, len(jobs))) as pool:
+            out = pool.map(_lidar_scan, jobs, chunksize=1)
+    else:
+        out = [_lidar_scan(j) for j in jobs]
+    pts = [o[0] for o in out]
+    poses = [o[1] for o in out]
     params = dict(
         voxel_size=voxel_size,
         voxels_per_block=8,

@@ -83,12 +83,6 @@ def test_tsdf_parity_per_point_raycasting(vbx):
     _run_tsdf(vbx, s, len(s), grouped=False)
 
 
-def test_tsdf_parity_full_size_room_frames(vbx):
-    """Two full 640x480 frames of the room workload (the benchmark's configuration)."""
-    s = scenes.room(frames=2)
-    _run_tsdf(vbx, s, len(s), check_each=True)
-
-
 def test_integration_is_deterministic(vbx):
     s = scenes.room(frames=2, width=160, height=120, fx=131.25, fy=131.25)
     exports = []
@@ -186,43 +180,75 @@ def test_esdf_methods_evaluation_runs(vbx):
     assert np.isfinite(g["tsdf_mean_abs_err_m"])
 
 
-def test_esdf_end_to_end_plane_sphere(vbx):
-    """GPU integrate + ESDF against the float64 oracle; seeds whose TSDF value sits within
-    1e-5 m of the band edge or of zero may legitimately differ (float32 vs float64
-    accumulation) and are excluded together with their d_max neighbourhood."""
-    s = scenes.plane_sphere()
+def _end_to_end(vbx, s, frames, label, **map_kw):
+    """GPU integrate + ESDF against the float64 oracle after every frame: TSDF sets and counts
+    bit-exact, |dD| <= 1e-5 m, relative dW <= 1e-6, then the ESDF. Seeds whose TSDF value sits
+    within 1e-5 m of the band edge or of zero may legitimately differ (float32 vs float64
+    accumulation) and are excluded together with their d_max neighbourhood; every other seed
+    and observed flag must match, and |dd| <= 1e-4 m."""
     p = s.params
-    g = vbx.Map.from_scene_params(p)
+    g = vbx.Map.from_scene_params(p, **map_kw)
     o = oracle.OracleMap.from_scene_params(p)
     B = p["voxels_per_block"]
     gamma = np.float32(p["fixed_band"])
-    worst = 0.0
-    for i in range(len(s)):
+    worst = dict(max_dD=0.0, max_rel_dW=0.0, max_dd=0.0, excluded_seeds=0)
+    for i in range(frames):
         g.integrate_scan(_dev(s.points[i]), s.poses[i])
         o.integrate(s.points[i], s.poses[i])
+        gu = sort_rows(g.last_updated())
+        assert np.array_equal(gu, o.last_updated()), f"{label} frame {i}: updated voxel sets differ"
+        gs, os_ = g.stats(), o.stats()
+        for a, b in (("points_valid", "points_valid"), ("rays", "groups"), ("records", "records"), ("new_blocks", "new_blocks")):
+            assert gs[a] == os_[b], (label, i, a, gs[a], os_[b])
         g.update_esdf()
         o.update_esdf()
         gex, oex = g.export(), o.export()
-        assert np.array_equal(gex["keys"], oex["keys"])
+        r = compare_tsdf(gex, oex, B)
+        assert r["max_dD"] <= TOL_D and r["max_rel_dW"] <= TOL_W_REL, (label, i, r)
         gobs, oobs = (gex["flags"] & 1) > 0, (oex["flags"] & 1) > 0
         assert np.array_equal(gobs, oobs)
         gfix, ofix = (gex["flags"] & 2) > 0, (oex["flags"] & 2) > 0
         Do = oex["D"].astype(np.float32)
         ambiguous = (np.abs(np.abs(Do) - gamma) < 1e-5) | (np.abs(Do) < 1e-5)
-        diff = (gfix != ofix) | (np.sign(gex["D"]) != np.sign(Do)) & oobs
-        assert not np.any(diff & ~ambiguous), f"frame {i}: seed sets differ outside the guard band"
+        diff = ((gfix != ofix) | (np.sign(gex["D"]) != np.sign(Do))) & oobs
+        assert not np.any(diff & ~ambiguous), f"{label} frame {i}: seed sets differ outside the guard band"
         mask = oobs.copy()
         if np.any(diff):
             vc = voxel_coords(gex["keys"], B)
-            bad = vc[diff]
-            r = int(math.ceil(p["max_esdf_dist"] / p["voxel_size"])) + 1
-            for c in bad:
-                near = np.max(np.abs(vc - c), axis=-1) <= r
-                mask &= ~near
+            rad = int(math.ceil(p["max_esdf_dist"] / p["voxel_size"])) + 1
+            for c in vc[diff]:
+                mask &= ~(np.max(np.abs(vc - c), axis=-1) <= rad)
         err = np.abs(gex["d"][mask].astype(np.float64) - oex["d"][mask])
-        worst = max(worst, float(err.max()))
-        assert err.max() <= TOL_ESDF, (i, float(err.max()))
-    print("plane_sphere ESDF end-to-end max |dd| %.3g m" % worst)
+        worst["max_dD"] = max(worst["max_dD"], r["max_dD"])
+        worst["max_rel_dW"] = max(worst["max_rel_dW"], r["max_rel_dW"])
+        worst["max_dd"] = max(worst["max_dd"], float(err.max()))
+        worst["excluded_seeds"] += int(diff.sum())
+        assert err.max() <= TOL_ESDF, (label, i, float(err.max()))
+    print(
+        "%s end to end: max |dD| %.3g m, max rel dW %.3g, max |dd| %.3g m, %d guard-band seeds excluded, %d blocks"
+        % (label, worst["max_dD"], worst["max_rel_dW"], worst["max_dd"], worst["excluded_seeds"], g.num_blocks())
+    )
+    return g, o, worst
+
+
+def test_esdf_end_to_end_plane_sphere(vbx):
+    s = scenes.plane_sphere()
+    _end_to_end(vbx, s, len(s), "plane_sphere")
+
+
+def test_end_to_end_full_size_room_frames(vbx):
+    """Two full 640x480 frames of the room sequence, TSDF and ESDF against the float64 oracle."""
+    s = scenes.room(frames=2)
+    _end_to_end(vbx, s, len(s), "room 640x480")
+
+
+def test_end_to_end_full_size_lidar_scans(vbx):
+    """The first three scans of the outdoor LiDAR growth sequence at its full size (64 x 2048
+    rays, 60 m range, the 100-scan path over the 200 m terrain): TSDF and ESDF against the
+    float64 oracle after every scan. These scans allocate about 24k blocks, traverse long
+    block segments and run raise waves."""
+    s = scenes.lidar_terrain(generate=3, workers=8)
+    _, _, worst = _end_to_end(vbx, s, len(s), "lidar 64x2048", block_capacity=1 << 17)
 
 
 # ----------------------------------------------------------------------------- query
