@@ -37,6 +37,7 @@ class orc_params(ctypes.Structure):
         ("grouped", ctypes.c_int),
         ("esdf_fp32", ctypes.c_int),
         ("esdf_mode", ctypes.c_int),
+        ("euclidean", ctypes.c_int),
     ]
 
 
@@ -97,6 +98,7 @@ def _load():
     lib.orc_group.argtypes = [P(orc_params), vp, i64, vp, vp, vp, vp, vp, i64]
     lib.orc_extract_mesh.restype = i64
     lib.orc_extract_mesh.argtypes = [vp, vp, vp, i64]
+    lib.orc_export_sites.argtypes = [vp, vp, vp]
     _lib = lib
     return lib
 
@@ -118,6 +120,7 @@ def make_params(
     grouped: int = 1,
     esdf_fp32: int = 0,
     esdf_mode: int = 0,
+    euclidean: int = 0,
 ) -> orc_params:
     return orc_params(
         voxel_size,
@@ -132,6 +135,7 @@ def make_params(
         grouped,
         esdf_fp32,
         esdf_mode,
+        euclidean,
     )
 
 
@@ -216,6 +220,16 @@ class OracleMap:
             parent=parent.reshape(nb, B3),
             flags=flags.reshape(nb, B3),
         )
+
+    def export_sites(self):
+        """Euclidean variant: (offsets, has_site) in the block order of export(); offsets are
+        site - voxel as (nb, B^3, 3) int32, has_site (nb, B^3) bool."""
+        nb = self.num_blocks()
+        B3 = self.B ** 3
+        off = np.zeros(nb * B3 * 3, dtype=np.int32)
+        has = np.zeros(nb * B3, dtype=np.uint8)
+        self._lib.orc_export_sites(self._h, _ptr(off), _ptr(has))
+        return off.reshape(nb, B3, 3), has.reshape(nb, B3).astype(bool)
 
     def last_updated(self) -> np.ndarray:
         n = int(self._lib.orc_num_last_updated(self._h))

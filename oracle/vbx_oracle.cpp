@@ -65,6 +65,10 @@
 //      iff fl32(D) < 0, float32 edge interpolation, ambiguous faces resolved by cutting off
 //      each inside corner, loops longer than 3 fanned around their centroid, normals towards
 //      positive D; triangles keyed by (cell min corner, index in cell). See mesh_cell.
+//   R13 full Euclidean variant (Sec. V-A says only that the parent then holds the full offset):
+//      a voxel keeps the offset to its site (a fixed voxel); a site offers |d_s| + v * ||n - s||;
+//      a fixed voxel whose value changes, or that leaves the band, is raised, and a voxel is its
+//      child iff it is measured to it. See update_esdf_euclidean.
 
 #include <algorithm>
 #include <cmath>
@@ -116,6 +120,9 @@ struct EsdfVoxel {
   int parent = kNoParent;
   bool observed = false;
   bool fixed = false;
+  // Euclidean variant (R13): the fixed voxel ("site") this voxel's distance is measured to
+  bool has_site = false;
+  int32_t site[3] = {0, 0, 0};
 };
 
 struct Block {
@@ -136,6 +143,7 @@ struct Params {
   int grouped;
   int esdf_fp32;  // 1: ESDF values computed in float32 (bit-exact mode), 0: float64
   int esdf_mode;  // 0: fixed band |D| < gamma (Sec. V-A); 1: occupancy (R11, Sec. VI-B)
+  int euclidean;  // 1: full Euclidean distance through stored sites (Sec. V-A, R13)
 };
 
 // 26-neighbourhood; index k = (dx+1)*9 + (dy+1)*3 + (dz+1); 13 is the voxel itself, and the
@@ -157,6 +165,9 @@ struct Map {
   std::vector<Key3> last_updated;  // voxels updated by the last scan
   std::vector<Key3> dirty;         // voxels updated since the last ESDF update
   std::unordered_map<Key3, char, Key3Hash> dirty_set;
+  // Euclidean variant: the voxels that took each site (entries of voxels that later took another
+  // site are stale and skipped where the list is read)
+  std::unordered_map<Key3, std::vector<Key3>, Key3Hash> site_takers;
   Stats st;
 
   int B3() const { return p.B * p.B * p.B; }
@@ -456,7 +467,13 @@ double seed_value(const Params& p, double D) {
   return D;
 }
 
+void update_esdf_euclidean(Map& m, int fifo);
+
 void update_esdf(Map& m, int fifo) {
+  if (m.p.euclidean) {
+    update_esdf_euclidean(m, fifo);
+    return;
+  }
   const Params& p = m.p;
   const double dmax = p.esdf_fp32 ? (double)p.dmax : (double)p.dmax;
   std::deque<Key3> raise;
@@ -568,6 +585,161 @@ void update_esdf(Map& m, int fifo) {
       if (cand < std::fabs(en->d)) {
         en->d = sv * cand;
         en->parent = 26 - k;  // direction from n back to c
+        m.st.lower_improve++;
+        push_lower(n, en->d);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Sec. V-A, full Euclidean variant: a voxel keeps the full offset to its site, the fixed voxel
+// its distance is measured to, instead of the direction of the neighbour that lowered it. Reading
+// R13 (the paper states only that the parent then holds the full offset):
+//  * the distance a site s offers voxel n is |d_s| + v * ||n - s|| (float32 in the bit-exact
+//    mode: |d_s| + fl(v * sqrt(fl(dx^2 + dy^2 + dz^2))), each operation rounded once);
+//  * classification follows Algorithm 1 (R6), except that a fixed voxel whose value changes at
+//    all is raised (voxels measured to it would otherwise keep a value computed from its old
+//    value);
+//  * raise: a voxel is a child of a raised site iff it is measured to that site (found here
+//    through the list of voxels that took the site, each re-checked); children are reset to
+//    +-d_max without a site, and the observed neighbours of every reset voxel and raised site
+//    join the lower wave (this also reaches voxels whose chain of neighbours back to the site
+//    was broken by later improvements along it);
+//  * lower: the popped voxel offers its site (itself if fixed) to its observed, non-fixed,
+//    same-sign neighbours; a neighbour takes it iff the offered distance is smaller than its own.
+
+double euclid_offer(const Params& p, double dsite, const int32_t s[3], const Key3& n) {
+  const int64_t dx = (int64_t)n.x - s[0], dy = (int64_t)n.y - s[1], dz = (int64_t)n.z - s[2];
+  const int64_t q = dx * dx + dy * dy + dz * dz;
+  if (p.esdf_fp32) {
+    const float len = p.v * std::sqrt((float)q);
+    return (double)(std::fabs((float)dsite) + len);
+  }
+  return std::fabs(dsite) + (double)p.v * std::sqrt((double)q);
+}
+
+void update_esdf_euclidean(Map& m, int fifo) {
+  const Params& p = m.p;
+  const double dmax = (double)p.dmax;
+  std::vector<Key3> raised;  // sites whose value changed or that left the band
+  std::priority_queue<LowerItem, std::vector<LowerItem>, std::greater<LowerItem>> lower_pq;
+  std::deque<Key3> lower_fifo;
+  uint64_t seq = 0;
+  auto push_lower = [&](const Key3& c, double d) {
+    if (fifo)
+      lower_fifo.push_back(c);
+    else
+      lower_pq.push(LowerItem{std::fabs(d), seq++, c});
+  };
+  auto push_observed_neighbours = [&](const Key3& c) {
+    for (int k = 0; k < 27; ++k) {
+      if (k == 13) continue;
+      Nbr o = nbr(k);
+      Key3 n{c.x + o.dx, c.y + o.dy, c.z + o.dz};
+      EsdfVoxel* en = m.esdf_at(n);
+      if (en && en->observed) push_lower(n, en->d);
+    }
+  };
+  m.st.esdf_updated_in = (int64_t)m.dirty.size();
+  m.st.seeds = m.st.raise_pops = m.st.lower_pops = m.st.lower_improve = 0;
+
+  // Classification (first loop of Algorithm 1, R6 and R13).
+  std::vector<Key3> work = m.dirty;
+  std::sort(work.begin(), work.end());
+  for (const Key3& c : work) {
+    TsdfVoxel* t = m.tsdf_at(c);
+    EsdfVoxel* e = m.esdf_at(c);
+    if (!t || !e || !(t->W > 0.0)) continue;
+    float Df = (float)t->D;
+    const bool occ = p.esdf_mode == 1;
+    double sT = occ ? 1.0 : (Df >= 0.0f ? 1.0 : -1.0);
+    bool fixed_now = occ ? Df < 0.0f : std::fabs(Df) < p.gamma;
+    if (fixed_now) {
+      m.st.seeds++;
+      double val = occ ? 0.0 : seed_value(p, t->D);
+      if (e->observed && e->fixed && e->d != val) raised.push_back(c);
+      e->observed = true;
+      e->fixed = true;
+      e->d = val;
+      e->has_site = false;
+      push_lower(c, val);
+    } else if (e->fixed) {  // leaves the band: its dependants are raised
+      e->fixed = false;
+      e->d = sT * dmax;
+      e->has_site = false;
+      raised.push_back(c);
+    } else if (!e->observed) {  // new voxel: its observed neighbours offer their sites
+      e->observed = true;
+      e->d = sT * dmax;
+      e->has_site = false;
+      push_observed_neighbours(c);
+    } else if (sgn(e->d) != sT) {  // sign flip of a non-fixed voxel (nothing is measured to it)
+      e->d = sT * dmax;
+      e->has_site = false;
+      push_observed_neighbours(c);
+    }
+  }
+  m.dirty.clear();
+  m.dirty_set.clear();
+
+  // Raise (R13): reset every voxel measured to a raised site.
+  for (const Key3& r : raised) {
+    m.st.raise_pops++;
+    push_observed_neighbours(r);
+    auto it = m.site_takers.find(r);
+    if (it == m.site_takers.end()) continue;
+    for (const Key3& n : it->second) {
+      EsdfVoxel* en = m.esdf_at(n);
+      if (!en || !en->observed || en->fixed || !en->has_site) continue;
+      if (en->site[0] != r.x || en->site[1] != r.y || en->site[2] != r.z) continue;
+      en->d = sgn(en->d) * dmax;
+      en->has_site = false;
+      m.st.raise_pops++;
+      push_observed_neighbours(n);
+    }
+    m.site_takers.erase(it);
+  }
+
+  // Lower (R8 with R13): sites travel through observed, non-fixed, same-sign neighbours.
+  while (fifo ? !lower_fifo.empty() : !lower_pq.empty()) {
+    Key3 c;
+    if (fifo) {
+      c = lower_fifo.front();
+      lower_fifo.pop_front();
+    } else {
+      c = lower_pq.top().c;
+      lower_pq.pop();
+    }
+    EsdfVoxel* e = m.esdf_at(c);
+    if (!e || !e->observed) continue;
+    int32_t s[3];
+    double dsite;
+    if (e->fixed) {
+      s[0] = c.x;
+      s[1] = c.y;
+      s[2] = c.z;
+      dsite = e->d;
+    } else if (e->has_site) {
+      std::memcpy(s, e->site, sizeof(s));
+      dsite = m.esdf_at(Key3{s[0], s[1], s[2]})->d;
+    } else {
+      continue;  // at d_max without a site: nothing to offer
+    }
+    m.st.lower_pops++;
+    double sv = sgn(e->d);
+    for (int k = 0; k < 27; ++k) {
+      if (k == 13) continue;
+      Nbr o = nbr(k);
+      Key3 n{c.x + o.dx, c.y + o.dy, c.z + o.dz};
+      EsdfVoxel* en = m.esdf_at(n);
+      if (!en || !en->observed || en->fixed || sgn(en->d) != sv) continue;
+      double cand = euclid_offer(p, dsite, s, n);
+      if (cand < std::fabs(en->d)) {
+        en->d = sv * cand;
+        en->has_site = true;
+        std::memcpy(en->site, s, sizeof(s));
+        m.site_takers[Key3{s[0], s[1], s[2]}].push_back(n);
         m.st.lower_improve++;
         push_lower(n, en->d);
       }
@@ -838,13 +1010,14 @@ struct orc_params {
   int grouped;
   int esdf_fp32;
   int esdf_mode;
+  int euclidean;
 };
 
 void* orc_create(const orc_params* op) {
   Map* m = new Map();
   m->p = Params{op->voxel_size, op->voxels_per_block, op->truncation, op->max_esdf_dist, op->weighting,
                 op->eps,        op->fixed_band,       op->w_max,      op->max_range,     op->grouped,
-                op->esdf_fp32,  op->esdf_mode};
+                op->esdf_fp32,  op->esdf_mode,        op->euclidean};
   return m;
 }
 
@@ -897,6 +1070,28 @@ void orc_last_updated(void* h, int32_t* out) {
     out[3 * i + 0] = m.last_updated[i].x;
     out[3 * i + 1] = m.last_updated[i].y;
     out[3 * i + 2] = m.last_updated[i].z;
+  }
+}
+
+// Sites of the Euclidean variant in the block order of orc_export: offsets (site - voxel) as
+// nb x B^3 x 3 int32 and a has-site flag per voxel.
+void orc_export_sites(void* h, int32_t* offsets, uint8_t* has_site) {
+  Map& m = *(Map*)h;
+  std::vector<Key3> ks;
+  for (auto& kv : m.blocks) ks.push_back(kv.first);
+  std::sort(ks.begin(), ks.end());
+  const int B = m.p.B, B3 = m.B3();
+  for (size_t b = 0; b < ks.size(); ++b) {
+    const Block& blk = m.blocks.at(ks[b]);
+    for (int l = 0; l < B3; ++l) {
+      const int x = ks[b].x * B + l % B, y = ks[b].y * B + (l / B) % B, z = ks[b].z * B + l / (B * B);
+      const EsdfVoxel& e = blk.esdf[l];
+      has_site[b * B3 + l] = e.has_site ? 1 : 0;
+      int32_t* o = offsets + 3 * (b * B3 + l);
+      o[0] = e.has_site ? e.site[0] - x : 0;
+      o[1] = e.has_site ? e.site[1] - y : 0;
+      o[2] = e.has_site ? e.site[2] - z : 0;
+    }
   }
 }
 
@@ -962,7 +1157,7 @@ float orc_projective_distance(const float* pbar, const float* s, const int32_t* 
 
 float orc_record_weight(const orc_params* op, float Wg, float d) {
   Params p{op->voxel_size, op->voxels_per_block, op->truncation, op->max_esdf_dist, op->weighting, op->eps,
-           op->fixed_band, op->w_max,            op->max_range,  op->grouped,       op->esdf_fp32, op->esdf_mode};
+           op->fixed_band, op->w_max,            op->max_range,  op->grouped,       op->esdf_fp32, op->esdf_mode, op->euclidean};
   return record_weight(p, Wg, d);
 }
 
@@ -971,7 +1166,7 @@ float orc_record_weight(const orc_params* op, float Wg, float d) {
 int64_t orc_group(const orc_params* op, const float* pts, int64_t n, const float* T16, int32_t* keys, float* pbar,
                   float* Wg, int64_t* count, int64_t cap) {
   Params p{op->voxel_size, op->voxels_per_block, op->truncation, op->max_esdf_dist, op->weighting, op->eps,
-           op->fixed_band, op->w_max,            op->max_range,  1,                 op->esdf_fp32, op->esdf_mode};
+           op->fixed_band, op->w_max,            op->max_range,  1,                 op->esdf_fp32, op->esdf_mode, op->euclidean};
   std::vector<ScanRay> gs;
   scan_rays(p, pts, n, T16, &gs);
   std::sort(gs.begin(), gs.end(), [](const ScanRay& a, const ScanRay& b) { return a.key < b.key; });
