@@ -398,7 +398,7 @@ def _serve_c1_sets():
     return {"plane_sphere": [scenes.plane_sphere(seed=60 + i) for i in range(4)]}
 
 
-def _serve_once(serve, sets, arrivals: float, capacity, slots: int = SERVE_SLOTS, sessions: int = SERVE_SESSIONS):
+def _serve_once(serve, sets, arrivals: float, capacity, slots: int = SERVE_SLOTS, sessions: int = SERVE_SESSIONS, profile: bool = False):
     pool = serve.ScanPool(sets, n_queries=N_QUERIES)
     scratch = serve.scratch_for_pool(pool, capacity)
     srv = serve.MapServer(
@@ -412,7 +412,7 @@ def _serve_once(serve, sets, arrivals: float, capacity, slots: int = SERVE_SLOTS
         sessions_per_s=arrivals,
         scans_per_session=16,
     )
-    res = srv.run(specs)
+    res = srv.run(specs, profile_steps=profile)
     srv.close()
     res["scratch_blocks"] = scratch
     res["map_bytes"] = {k: srv.map_bytes(k) for k in sets}
@@ -434,6 +434,10 @@ def run_served(args, vbx, torch):
         f"{SERVE_SESSIONS} robot sessions arriving as a Poisson process ({SERVE_ARRIVALS:.0f}/s), half room RGB-D 640x480 "
         f"(v=0.05 m), half LiDAR 64x2048 terrain (v=0.2 m), " + common
     )
+    # where the slow steps' device time goes: the same stream once more, one step at a time with
+    # direct (non-graph) launches and per-kernel device times
+    prof = _serve_once(serve, _serve_sets(), SERVE_ARRIVALS, SERVE_CAPACITY, profile=True)
+    res["slow_step_attribution"] = prof["slow_step_kernels"]
     sat = _serve_once(serve, _serve_sets(), SERVE_SATURATED_ARRIVALS, SERVE_CAPACITY)
     sat["workload"] = f"as above, sessions arriving at {SERVE_SATURATED_ARRIVALS:.0f}/s (more scans offered than the GPU serves)"
     res["saturated"] = sat

@@ -266,12 +266,17 @@ enum { VBX_STEP_INTEGRATE = 1, VBX_STEP_ESDF = 2, VBX_STEP_QUERY = 4, VBX_STEP_G
  * scan the map has integrated alone); batches never grow a map's scratch. */
 vbx_status vbx_batch_create(const vbx_map_t* maps, int count, int64_t max_queries, vbx_batch_t* out);
 
-/* Rebinds slot `slot` to `map` (same device, not bound to another slot); synchronises. */
+/* Rebinds slot `slot` to `map` (same device, not bound to another slot). Steps already issued keep
+ * the map they were issued with; the next step takes the new one. The call synchronises the
+ * device only when the map needs larger ESDF work lists or a larger block edge than the batch has
+ * held so far (it reallocates them), so binding maps of the kinds already bound never stalls
+ * steps in flight. */
 vbx_status vbx_batch_bind(vbx_batch_t batch, int slot, vbx_map_t map);
 
 /* One batched step on `stream`: scans[count] (VBX_STEP_INTEGRATE), ESDF update of every slot
  * (VBX_STEP_ESDF), queries[count] (VBX_STEP_QUERY, may be NULL otherwise). Host arrays are copied
- * before the call returns. Double-buffered: the call waits for the step issued two calls earlier. */
+ * before the call returns. The staged descriptors form a ring of 4: the call waits for the step
+ * issued four calls earlier, so up to 4 steps may be in flight on the stream. */
 vbx_status vbx_batch_step(vbx_batch_t batch, const vbx_scan_in* scans, const vbx_query_io* queries, int flags,
                           void* stream);
 

@@ -704,15 +704,19 @@ struct vbx_batch_s {
   // device descriptor block: DevMap[count] | ScanDesc[count] | QueryDesc[count]
   unsigned char* dev_block = nullptr;
   size_t block_bytes = 0;
-  unsigned char* staging[2] = {nullptr, nullptr};  // pinned host copies, double-buffered
-  cudaEvent_t staged[2] = {nullptr, nullptr};
+  // pinned host copies of the descriptors, a ring of kStages: a step waits only for the step
+  // issued kStages calls earlier, so a caller can keep several steps in flight
+  static constexpr int kStages = 4;
+  unsigned char* staging[kStages] = {};
+  cudaEvent_t staged[kStages] = {};
   uint64_t steps = 0;
   vbx::EsdfCtl* ctl_dev = nullptr;
   std::vector<void*> dev_allocs;
   vbx::Tuning tune = vbx::kDefaultTuning;
   cudaStream_t cap_stream = nullptr;
-  cudaGraphExec_t graphs[2][8] = {};
-  long long graph_kernels[2][8] = {};  // kernels captured into each graph
+  cudaGraphExec_t graphs[kStages][8] = {};
+  long long graph_kernels[kStages][8] = {};  // kernels captured into each graph
+  uint64_t ctl_cap = 0;  // tiles the ESDF active lists hold (host copy of ctl.cap)
   MapHook hook;
 
   vbx::DevMap* maps_dev() const { return reinterpret_cast<vbx::DevMap*>(dev_block); }
@@ -740,7 +744,7 @@ struct vbx_batch_s {
   ~vbx_batch_s() {
     cudaDeviceSynchronize();
     drop_graphs();
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < kStages; ++k) {
       if (staging[k]) cudaFreeHost(staging[k]);
       if (staged[k]) cudaEventDestroy(staged[k]);
     }
@@ -794,7 +798,7 @@ vbx_status batch_stage(vbx_batch_t b, const vbx_scan_in* scans, const vbx_query_
         return fail(VBX_ERR_INVALID_ARG, "slot %d: query buffers must not be NULL", i);
     }
   }
-  const int k = (int)(b->steps & 1);
+  const int k = (int)(b->steps % vbx_batch_s::kStages);
   cudaError_t e = cudaEventSynchronize(b->staged[k]);
   if (e != cudaSuccess) return cuda_fail(e, "batch staging wait");
   unsigned char* st = b->staging[k];
@@ -920,7 +924,8 @@ vbx_status vbx_batch_create(const vbx_map_t* maps, int count, int64_t max_querie
     delete b;
     return cuda_fail(e, "batch buffers");
   }
-  for (int k = 0; k < 2; ++k) {
+  b->ctl_cap = ctl.cap;
+  for (int k = 0; k < vbx_batch_s::kStages; ++k) {
     if ((e = cudaMallocHost((void**)&b->staging[k], b->block_bytes)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&b->staged[k], cudaEventDisableTiming)) != cudaSuccess) {
       delete b;
@@ -945,46 +950,53 @@ vbx_status vbx_batch_bind(vbx_batch_t b, int slot, vbx_map_t map) {
   if (map->device != b->device) return fail(VBX_ERR_INVALID_ARG, "map lives on another device");
   for (int j = 0; j < b->count; ++j)
     if (j != slot && b->maps[j] == map) return fail(VBX_ERR_INVALID_ARG, "map already bound to slot %d", j);
+  // the ESDF active lists were sized for the bound maps' pools
+  uint64_t cap_sum = 0;
+  for (int j = 0; j < b->count; ++j) {
+    const vbx_map_t mj = j == slot ? map : b->maps[j];
+    cap_sum += (uint64_t)mj->d.cap_blocks << mj->d.tile_shift;
+  }
+  const bool grow_lists = cap_sum > b->ctl_cap;
+  const bool new_shape = map->B > b->max_B;  // the ESDF launch's shared-memory tile must fit the largest block
+  if (!grow_lists && !new_shape) {
+    // steps read the slot's map from the descriptors they stage, so in-flight steps keep the
+    // map they were issued with and the next step takes the new one: no synchronisation
+    b->maps[slot] = map;
+    return VBX_OK;
+  }
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(e, "bind sync");
-  if (map->B > b->max_B) {  // the ESDF launch's shared-memory tile must fit the largest block
+  if (new_shape) {
     b->max_B = map->B;
     b->drop_graphs();
   }
-  if (((uint64_t)map->d.cap_blocks << map->d.tile_shift) > ((uint64_t)b->maps[slot]->d.cap_blocks << b->maps[slot]->d.tile_shift)) {
-    // the active lists were sized for the old maps' pools
-    uint64_t cap_sum = 0;
-    for (int j = 0; j < b->count; ++j) {
-      const vbx_map_t mj = j == slot ? map : b->maps[j];
-      cap_sum += (uint64_t)mj->d.cap_blocks << mj->d.tile_shift;
-    }
+  if (grow_lists) {
     vbx::EsdfCtl ctl{};
     if ((e = cudaMemcpy(&ctl, b->ctl_dev, sizeof(ctl), cudaMemcpyDeviceToHost)) != cudaSuccess)
       return cuda_fail(e, "esdf control");
-    if (cap_sum > ctl.cap) {
-      const uint64_t ring = lower_ring_slots(cap_sum, b->num_sms);
-      const size_t bytes[6] = {cap_sum * sizeof(uint2), cap_sum * sizeof(uint2), cap_sum * sizeof(uint2),
-                               cap_sum * sizeof(uint2), ring * sizeof(uint2),    ring * sizeof(unsigned long long)};
-      void* lists[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-      for (int i = 0; i < 6; ++i) {
-        if ((e = cudaMalloc(&lists[i], bytes[i])) != cudaSuccess ||
-            (e = cudaMemset(lists[i], 0, bytes[i])) != cudaSuccess) {
-          for (int j = 0; j <= i; ++j) cudaFree(lists[j]);
-          return cuda_fail(e, "esdf lists");
-        }
+    const uint64_t ring = lower_ring_slots(cap_sum, b->num_sms);
+    const size_t bytes[6] = {cap_sum * sizeof(uint2), cap_sum * sizeof(uint2), cap_sum * sizeof(uint2),
+                             cap_sum * sizeof(uint2), ring * sizeof(uint2),    ring * sizeof(unsigned long long)};
+    void* lists[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    for (int i = 0; i < 6; ++i) {
+      if ((e = cudaMalloc(&lists[i], bytes[i])) != cudaSuccess ||
+          (e = cudaMemset(lists[i], 0, bytes[i])) != cudaSuccess) {
+        for (int j = 0; j <= i; ++j) cudaFree(lists[j]);
+        return cuda_fail(e, "esdf lists");
       }
-      for (int i = 0; i < 6; ++i) b->dev_allocs.push_back(lists[i]);
-      ctl.ract0 = (uint2*)lists[0];
-      ctl.ract1 = (uint2*)lists[1];
-      ctl.lact0 = (uint2*)lists[2];
-      ctl.lact1 = (uint2*)lists[3];
-      ctl.lring = (uint2*)lists[4];
-      ctl.ltag = (unsigned long long*)lists[5];
-      ctl.rcap = (unsigned)std::min<uint64_t>(ring, UINT32_MAX);
-      ctl.cap = (unsigned)std::min<uint64_t>(cap_sum, UINT32_MAX);
-      if ((e = cudaMemcpy(b->ctl_dev, &ctl, sizeof(ctl), cudaMemcpyHostToDevice)) != cudaSuccess)
-        return cuda_fail(e, "esdf control");
     }
+    for (int i = 0; i < 6; ++i) b->dev_allocs.push_back(lists[i]);
+    ctl.ract0 = (uint2*)lists[0];
+    ctl.ract1 = (uint2*)lists[1];
+    ctl.lact0 = (uint2*)lists[2];
+    ctl.lact1 = (uint2*)lists[3];
+    ctl.lring = (uint2*)lists[4];
+    ctl.ltag = (unsigned long long*)lists[5];
+    ctl.rcap = (unsigned)std::min<uint64_t>(ring, UINT32_MAX);
+    ctl.cap = (unsigned)std::min<uint64_t>(cap_sum, UINT32_MAX);
+    if ((e = cudaMemcpy(b->ctl_dev, &ctl, sizeof(ctl), cudaMemcpyHostToDevice)) != cudaSuccess)
+      return cuda_fail(e, "esdf control");
+    b->ctl_cap = ctl.cap;
   }
   b->maps[slot] = map;
   return VBX_OK;

@@ -222,30 +222,87 @@ class MapServer:
         seed: int = 7,
         on_finish: Optional[Callable[[SessionSpec, vbx.Map, tuple], None]] = None,
         time_limit: float = 600.0,
+        max_in_flight: int = 2,
+        profile_steps: bool = False,
     ) -> Dict[str, object]:
+        """Serves `sessions` to completion. Steps are issued without waiting for the previous
+        ones: up to `max_in_flight` server steps (each a map step and a query step, on one
+        stream, so a session's consecutive scans stay in order) are on the GPU while the host
+        admits sessions and forms the next batch. A step's completion is seen by polling its
+        events; a scan's latency runs from its arrival to the host time at which the end of its
+        step's map part was first seen, a query's to the end of the query part.
+        profile_steps: a diagnostic pass instead, with direct (non-graph) launches and per-kernel
+        device times of every step (one step at a time)."""
         import torch
 
+        if profile_steps:
+            max_in_flight = 1
         rng = np.random.default_rng(seed)
         waiting = collections.deque(sorted(sessions, key=lambda s: s.start))
         active: Dict[int, _Active] = {}
         free_slots = list(range(self.slots))[::-1]
-        flags_map = vbx.STEP_INTEGRATE | vbx.STEP_ESDF | (vbx.STEP_GRAPH if self.use_graph else 0)
-        flags_q = vbx.STEP_QUERY | (vbx.STEP_GRAPH if self.use_graph else 0)
+        graph = 0 if (profile_steps or not self.use_graph) else vbx.STEP_GRAPH
+        flags_map = vbx.STEP_INTEGRATE | vbx.STEP_ESDF | graph
+        flags_q = vbx.STEP_QUERY | graph
         lat_scan, lat_query, batch_sizes = [], [], []
-        # per scan: its kind, the wait from arrival to the start of its step, and that step's wall
-        # time (scan part); they show where the latency tail comes from
+        # per scan: its kind, the wait from arrival to the issue of its step, and the time from
+        # that issue to the end of the step's map part; they show where the latency tail comes from
         scan_kind, scan_wait, scan_step, scan_first, scan_gpu = [], [], [], [], []
+        step_kernels = []  # profile_steps: per step, {kernel: ms} and its map-part device time
+        if profile_steps:
+            self.batch.set_profiling(True)
+            prev_kt = self.batch.kernel_times()
         admitted = 0
         max_active = 0
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e2 = torch.cuda.Event(enable_timing=True)
+        in_flight = collections.deque()
+        pool_events = []
+
+        def event():
+            return pool_events.pop() if pool_events else torch.cuda.Event(enable_timing=True)
+
         gpu_ms = 0.0
+        overlap_issues = 0  # steps issued while an earlier one was still on the GPU
         t0 = time.perf_counter()
-        while waiting or active:
+
+        def retire(block: bool):
+            nonlocal gpu_ms
+            while in_flight:
+                now = time.perf_counter() - t0
+                for f in in_flight:
+                    if f["t_scan"] is None and f["e1"].query():
+                        f["t_scan"] = now
+                f = in_flight[0]
+                if block:
+                    if f["t_scan"] is None:
+                        f["e1"].synchronize()
+                        f["t_scan"] = time.perf_counter() - t0
+                    f["e2"].synchronize()
+                    now = time.perf_counter() - t0
+                elif not f["e2"].query():
+                    return
+                if f["t_scan"] is None:
+                    f["t_scan"] = now
+                in_flight.popleft()
+                t_done = now
+                gpu_ms += f["e0"].elapsed_time(f["e2"])
+                f["map_ms"] = f["e0"].elapsed_time(f["e1"])
+                scan_gpu_s = f["map_ms"] * 1e-3
+                for arrival, kind, first in f["scans"]:
+                    lat_query.append(t_done - arrival)
+                    lat_scan.append(f["t_scan"] - arrival)
+                    scan_kind.append(kind)
+                    scan_first.append(first)
+                    scan_gpu.append(scan_gpu_s)
+                    scan_wait.append(max(f["t_issue"] - arrival, 0.0))
+                    scan_step.append(f["t_scan"] - f["t_issue"])
+                pool_events.extend((f["e0"], f["e1"], f["e2"]))
+                block = False
+
+        while waiting or active or in_flight:
             now = time.perf_counter() - t0
             if now > time_limit:
                 raise RuntimeError("serving run exceeded its time limit")
+            retire(False)
             # admission: arrival order, a free slot and room in the memory budget
             while waiting and waiting[0].start <= now and free_slots:
                 spec = waiting[0]
@@ -261,50 +318,57 @@ class MapServer:
                 admitted += 1
             max_active = max(max_active, len(active))
             ready = [s for s, a in active.items() if a.arrivals[a.next] <= now]
-            if not ready:
-                nxt = [a.arrivals[a.next] for a in active.values()]
-                if waiting and free_slots:
-                    nxt.append(waiting[0].start)
-                wait = (min(nxt) - now) if nxt else 0.001
-                time.sleep(min(max(wait, 0.0), 0.002))
+            if not ready or len(in_flight) >= max_in_flight:
+                if not ready and not in_flight:
+                    nxt = [a.arrivals[a.next] for a in active.values()]
+                    if waiting and free_slots:
+                        nxt.append(waiting[0].start)
+                    wait = (min(nxt) - now) if nxt else 0.001
+                    time.sleep(min(max(wait, 0.0), 0.002))
+                elif len(in_flight) >= max_in_flight:
+                    retire(True)
+                else:
+                    time.sleep(5e-5)
                 continue
             points = [None] * self.slots
             poses = [None] * self.slots
             queries = [None] * self.slots
+            scans = []
             for s in ready:
                 a = active[s]
                 p, T, q = self.pool.frame(a.spec, a.next)
                 points[s], poses[s] = p, T
                 queries[s] = (q,) + self.out[s]
-            t_step = time.perf_counter() - t0
-            e0.record()
+                scans.append((float(a.arrivals[a.next]), a.spec.kind, a.next == 0))
+            if in_flight:
+                overlap_issues += 1
+            f = dict(e0=event(), e1=event(), e2=event(), scans=scans, t_scan=None, t_issue=time.perf_counter() - t0)
+            f["e0"].record()
             self.batch.step(points, poses, flags=flags_map)
-            e1.record()
+            f["e1"].record()
             self.batch.step(queries=queries, flags=flags_q)
-            e2.record()
-            e2.synchronize()
-            t_done = time.perf_counter() - t0
-            q_ms = e1.elapsed_time(e2)
-            gpu_ms += e0.elapsed_time(e2)
+            f["e2"].record()
+            in_flight.append(f)
             batch_sizes.append(len(ready))
+            if profile_steps:
+                retire(True)
+                kt = self.batch.kernel_times()
+                step_kernels.append((f["map_ms"], {k: v["ms"] - prev_kt.get(k, {"ms": 0.0})["ms"] for k, v in kt.items()}))
+                prev_kt = kt
             for s in ready:
                 a = active[s]
-                arrival = float(a.arrivals[a.next])
-                lat_query.append(t_done - arrival)
-                lat_scan.append(t_done - q_ms * 1e-3 - arrival)
-                scan_kind.append(a.spec.kind)
-                scan_first.append(a.next == 0)
-                scan_gpu.append(e0.elapsed_time(e1) * 1e-3)  # the step's device time (scan part)
-                scan_wait.append(max(t_step - arrival, 0.0))
-                scan_step.append(t_done - q_ms * 1e-3 - t_step)
                 a.next += 1
                 if a.next == a.spec.n_scans:
+                    # the session's last scan is issued; work enqueued from here on (the callback's
+                    # copies, a reset for the next session) runs after it on the same stream
                     if on_finish is not None:
                         on_finish(a.spec, a.m, tuple(t.clone() for t in self.out[s]))
                     self.batch.bind(s, self.idle[s])
                     self.free[a.spec.kind].append(a.m)
                     del active[s]
                     free_slots.append(s)
+        if profile_steps:
+            self.batch.set_profiling(False)
         self.batch.sync()
         wall = time.perf_counter() - t0
         n = len(lat_scan)
@@ -351,4 +415,31 @@ class MapServer:
             query_latency_ms=dict(p50=float(np.percentile(lq, 50)), p99=float(np.percentile(lq, 99))),
             peak_map_bytes=self.peak,
             budget_bytes=self.budget,
+            steps_issued_while_gpu_busy=overlap_issues,
+            max_in_flight=max_in_flight,
+            slow_step_kernels=_slow_step_kernels(step_kernels) if profile_steps else None,
         )
+
+
+def _slow_step_kernels(step_kernels, q: float = 99.0):
+    """Mean per-kernel device time of the steps whose map part is at or above the q-th
+    percentile of map-part device time, beside the same for the median half of the steps."""
+    if not step_kernels:
+        return None
+    t = np.asarray([x[0] for x in step_kernels])
+    hi = t >= np.percentile(t, q)
+    mid = (t >= np.percentile(t, 25)) & (t <= np.percentile(t, 75))
+
+    def mean(mask):
+        ks = sorted({k for x in step_kernels for k in x[1]})
+        n = max(int(mask.sum()), 1)
+        return {k: sum(x[1].get(k, 0.0) for x, m in zip(step_kernels, mask) if m) / n for k in ks}
+
+    return dict(
+        steps=len(step_kernels),
+        slow_steps=int(hi.sum()),
+        slow_step_map_ms=float(t[hi].mean()),
+        median_step_map_ms=float(np.median(t)),
+        slow_step_kernel_ms=mean(hi),
+        median_steps_kernel_ms=mean(mid),
+    )
