@@ -55,6 +55,10 @@ FLUSH_BYTES = 256 << 20  # > 129 MB L2
 # and the SHA-256 prefix of the source files it was captured on (KERNEL_SOURCE): once one of
 # them changes the entry no longer matches and the reported traffic is null.
 NCU_TRAFFIC = {
+    # k_integrate_rays, LiDAR growth scan 3 (dram__bytes_read.sum 62,646,528 + write 27,521,792)
+    ("integrate_rays", "integrate.cu", "8cc3dfdaee1ac4cf"): 90168320,
+    # k_apply, LiDAR growth scan 3 (dram__bytes_read.sum 94,035,712 + write 39,201,792)
+    ("apply", "integrate.cu", "8cc3dfdaee1ac4cf"): 133237504,
     # k_esdf<512> x 2 per SM, room workload, one scan (dram__bytes_read.sum 2,320,384 + write 47,616)
     ("esdf", "esdf.cu", "5f585b9c2a3af0cc"): 2368000,
     # k_mesh_blocks<16>, full mesh of the room map (dram__bytes_read.sum 25,988,096 + write 2,304;
