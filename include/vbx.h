@@ -67,6 +67,16 @@ typedef struct {
                              occupancy ESDF compared in Sec. VI-B: observed voxels with D < 0
                              are occupied at distance 0 and every other observed voxel holds
                              its unsigned distance to them                                   */
+  int euclidean;          /* 0: quasi-Euclidean distances (26-neighbour steps v, v*sqrt(2),
+                             v*sqrt(3), the parent is a neighbour direction); 1: full Euclidean
+                             distances, each voxel keeping the offset to its site, the fixed
+                             voxel it is measured to (Sec. V-A, Sec. VI-B). Requires
+                             max_esdf_dist / voxel_size <= 126. Such maps are updated one at a
+                             time (vbx_update_esdf), not in batches. The result depends on the
+                             processing order: every voxel's distance is exactly what its site
+                             offers it, |d_site| + v * |offset|, the site is an observed fixed
+                             voxel of its sign, and no observed same-sign neighbour's site
+                             offers it less                                                  */
 } vbx_map_options;
 
 /* Fills *opt with the defaults above (weighting 0, grouped 1). */
@@ -164,11 +174,18 @@ vbx_status vbx_num_blocks(vbx_map_t map, int64_t* n_out, void* stream);
  *   keys:   cap x 3 int32 block coordinates
  *   tsdf:   cap x B^3 x 2 float32 (D, W) per voxel
  *   esdf_d: cap x B^3 float32 ESDF distance per voxel
- *   parent: cap x B^3 uint8, direction to the parent voxel (k = (dx+1)*9+(dy+1)*3+(dz+1), 255 none)
- *   flags:  cap x B^3 uint8, bit0 observed, bit1 fixed
+ *   parent: cap x B^3 uint8, direction to the parent voxel (k = (dx+1)*9+(dy+1)*3+(dz+1), 255 none);
+ *           Euclidean maps: the low byte of the word (use vbx_export_sites)
+ *   flags:  cap x B^3 uint8, bit0 observed, bit1 fixed, bit2 holds a site (Euclidean maps)
  * Synchronises `stream`. */
 vbx_status vbx_export_blocks(vbx_map_t map, int32_t* keys, float* tsdf, float* esdf_d, uint8_t* parent,
                              uint8_t* flags, int64_t cap, void* stream);
+
+/* Euclidean maps (options.euclidean = 1): the site of every voxel, in the block order of
+ * vbx_export_blocks. offsets: cap x B^3 x 3 int8 (site - voxel, in voxels), has_site: cap x B^3
+ * (1: the voxel holds a site; fixed voxels are their own sites and report 0). Host buffers,
+ * either may be NULL. Synchronising; VBX_ERR_INVALID_ARG for a quasi-Euclidean map. */
+vbx_status vbx_export_sites(vbx_map_t map, int8_t* offsets, uint8_t* has_site, int64_t cap, void* stream);
 
 /* Voxel coordinates (cap x 3 int32, host) of the voxels updated by the last
  * vbx_integrate_scan or vbx_import_tsdf, in unspecified order; *n_out = their number

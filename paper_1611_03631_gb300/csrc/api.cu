@@ -259,6 +259,9 @@ vbx_status vbx_create_map(float voxel_size, int voxels_per_block, float truncati
   if (opt_in) opt = *opt_in;
   if (opt.weighting != 0 && opt.weighting != 1) return fail(VBX_ERR_INVALID_ARG, "weighting must be 0 or 1");
   if (opt.esdf_mode != 0 && opt.esdf_mode != 1) return fail(VBX_ERR_INVALID_ARG, "esdf_mode must be 0 or 1");
+  if (opt.euclidean != 0 && opt.euclidean != 1) return fail(VBX_ERR_INVALID_ARG, "euclidean must be 0 or 1");
+  if (opt.euclidean && !(max_esdf_dist <= 126.0f * voxel_size))
+    return fail(VBX_ERR_INVALID_ARG, "euclidean maps need max_esdf_dist <= 126 * voxel_size (site offsets are 8-bit)");
   const float eps = opt.eps > 0.0f ? opt.eps : voxel_size;
   if (opt.weighting == 1 && !(eps < truncation)) return fail(VBX_ERR_INVALID_ARG, "eps must be below truncation");
   const int B = voxels_per_block;
@@ -306,6 +309,7 @@ vbx_status vbx_create_map(float voxel_size, int voxels_per_block, float truncati
   d.tile_shift = (B == 16 && VBX_TILE_EDGE == 8) ? 3 : 0;  // ESDF tiles of 8^3 voxels
   d.weighting = opt.weighting;
   d.esdf_mode = opt.esdf_mode;
+  d.euclid = opt.euclidean;
   d.grouped = opt.grouped ? 1 : 0;
   d.cap_blocks = (uint32_t)cap;
   const uint32_t H = next_pow2((uint64_t)cap * 2);
@@ -449,8 +453,10 @@ vbx_status vbx_update_esdf(vbx_map_t m, void* stream) {
   if (e != cudaSuccess) return cuda_fail(e, "reset esdf counters");
   e = cudaMemsetAsync(m->ctl_dev, 0, offsetof(vbx::EsdfCtl, cap), s);
   if (e != cudaSuccess) return cuda_fail(e, "reset esdf control");
-  // one map: its rounds would hold about one tile per SM, so the waves run as work queues
-  e = vbx::launch_esdf(m->d_dev, 1, m->B, m->ctl_dev, m->cfg(stream), &m->hook, true);
+  if (m->opt.euclidean)
+    e = vbx::launch_esdf_euclid(m->d_dev, m->B, m->ctl_dev, m->cfg(stream), &m->hook);
+  else  // one map: its rounds would hold about one tile per SM, so the waves run as work queues
+    e = vbx::launch_esdf(m->d_dev, 1, m->B, m->ctl_dev, m->cfg(stream), &m->hook, true);
   if (e != cudaSuccess) return cuda_fail(e, "esdf cooperative launch");
   return VBX_OK;
 }
@@ -547,6 +553,31 @@ vbx_status vbx_export_blocks(vbx_map_t m, int32_t* keys, float* tsdf, float* esd
       if (esdf_d) esdf_d[i] = dv;
       if (parent) parent[i] = (uint8_t)(w[i] & 0xff);
       if (flags) flags[i] = (uint8_t)((w[i] >> 8) & 0xff);
+    }
+  }
+  return read_error(m, (cudaStream_t)stream);
+}
+
+vbx_status vbx_export_sites(vbx_map_t m, int8_t* offsets, uint8_t* has_site, int64_t cap, void* stream) {
+  if (!m) return fail(VBX_ERR_INVALID_ARG, "map is NULL");
+  if (!m->opt.euclidean) return fail(VBX_ERR_INVALID_ARG, "the map is not a Euclidean map");
+  int64_t nb = 0;
+  vbx_status st = vbx_num_blocks(m, &nb, stream);
+  if (st != VBX_OK) return st;
+  if (cap < nb) return fail(VBX_ERR_INVALID_ARG, "cap %lld below the number of blocks %lld", (long long)cap, (long long)nb);
+  const size_t V = (size_t)nb * m->B * m->B * m->B;
+  if (V && (offsets || has_site)) {
+    std::vector<unsigned long long> w(V);
+    cudaError_t e = cudaMemcpy(w.data(), m->d.esdf, V * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "copy esdf");
+    for (size_t i = 0; i < V; ++i) {
+      const bool has = ((w[i] >> 8) & vbx::kHasSite) != 0;
+      if (has_site) has_site[i] = has ? 1 : 0;
+      if (offsets) {
+        offsets[3 * i] = has ? (int8_t)(w[i] & 0xff) : 0;
+        offsets[3 * i + 1] = has ? (int8_t)((w[i] >> 16) & 0xff) : 0;
+        offsets[3 * i + 2] = has ? (int8_t)((w[i] >> 24) & 0xff) : 0;
+      }
     }
   }
   return read_error(m, (cudaStream_t)stream);
@@ -885,6 +916,7 @@ vbx_status vbx_batch_create(const vbx_map_t* maps, int count, int64_t max_querie
   for (int i = 0; i < count; ++i) {
     if (!maps[i]) return fail(VBX_ERR_INVALID_ARG, "slot %d: map is NULL", i);
     if (maps[i]->device != device) return fail(VBX_ERR_INVALID_ARG, "slot %d: map lives on another device", i);
+    if (maps[i]->opt.euclidean) return fail(VBX_ERR_INVALID_ARG, "slot %d: Euclidean maps are updated one at a time", i);
     for (int j = 0; j < i; ++j)
       if (maps[j] == maps[i]) return fail(VBX_ERR_INVALID_ARG, "a map is bound to two slots");
   }
@@ -948,6 +980,7 @@ vbx_status vbx_batch_bind(vbx_batch_t b, int slot, vbx_map_t map) {
   if (!b || !map) return fail(VBX_ERR_INVALID_ARG, "batch or map is NULL");
   if (slot < 0 || slot >= b->count) return fail(VBX_ERR_INVALID_ARG, "slot out of range");
   if (map->device != b->device) return fail(VBX_ERR_INVALID_ARG, "map lives on another device");
+  if (map->opt.euclidean) return fail(VBX_ERR_INVALID_ARG, "Euclidean maps are updated one at a time");
   for (int j = 0; j < b->count; ++j)
     if (j != slot && b->maps[j] == map) return fail(VBX_ERR_INVALID_ARG, "map already bound to slot %d", j);
   // the ESDF active lists were sized for the bound maps' pools

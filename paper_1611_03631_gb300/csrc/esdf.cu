@@ -38,7 +38,7 @@ constexpr int kMaxLocalIters = 1 << 15;
 // halo (tile edge T = S + 2).
 struct Tile {
   unsigned long long* w;  // T^3 ESDF words, halo included
-  uint16_t* a;            // active interior voxels (tile-local index), current
+  uint16_t* a;            // active interior voxels (tile cell index), current
   uint16_t* b;            // active interior voxels, next
   uint32_t* in;           // 2 x S^3 bits: already queued for the next local iteration (by parity)
   uint32_t* chg;          // T^3 bits: word changed in this tile-round
@@ -47,6 +47,9 @@ struct Tile {
                           // (j+2)%3), [3] neighbour tiles to activate in the next-round list,
                           // [4] neighbour tiles whose lower frontier was seeded (bit k = direction
                           // k of the neighbour tile relative to this one)
+  uint32_t* lseed;        // T^3 bits: cells the raise re-seeds into the lower wave
+  int* doff;              // [27] tile cell offset of direction k
+  unsigned char* dcls;    // [27] 1, 2 or 3: axes direction k moves along (step v, v*sqrt2, v*sqrt3)
 };
 
 #ifndef VBX_TILE_EDGE
@@ -59,7 +62,7 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(
 __host__ __device__ inline size_t tile_bytes(int S) {
   const size_t T = S + 2, T3 = T * T * T, S3 = (size_t)S * S * S;
   return align16(T3 * 8) + align16(S3 * 2) * 2 + align16(S3 / 4 < 16 ? 16 : S3 / 4) + align16((T3 + 31) / 32 * 4) +
-         align16(27 * 4) + 32;
+         align16(27 * 4) + 32 + align16(27 * 4) + 32 + align16((T3 + 31) / 32 * 4);
 }
 
 __device__ inline Tile carve(unsigned char* base, int S) {
@@ -79,6 +82,12 @@ __device__ inline Tile carve(unsigned char* base, int S) {
   t.nslot = reinterpret_cast<uint32_t*>(base + off);
   off += align16(27 * 4);
   t.cnt = reinterpret_cast<unsigned*>(base + off);
+  off += 32;
+  t.doff = reinterpret_cast<int*>(base + off);
+  off += align16(27 * 4);
+  t.dcls = base + off;
+  off += 32;
+  t.lseed = reinterpret_cast<uint32_t*>(base + off);
   return t;
 }
 
@@ -257,9 +266,17 @@ __device__ __forceinline__ int coords_tile_dir(int x, int y, int z) {
 template <int NT, int B, int S>
 __device__ void stage_tile(const DevMap& m, const TileRef& r, uint32_t* cur_bits, const Tile& t, bool ordered) {
   using G = Geo<B, S>;
-  if (threadIdx.x < 27) t.nslot[threadIdx.x] = threadIdx.x == 13 ? r.slot : __ldcg(&m.nbr[(size_t)r.slot * 27 + threadIdx.x]);
+  if (threadIdx.x < 27) {
+    const int k = threadIdx.x;
+    t.nslot[k] = k == 13 ? r.slot : __ldcg(&m.nbr[(size_t)r.slot * 27 + k]);
+    t.doff[k] = G::off(k);
+    t.dcls[k] = (unsigned char)((k / 9 != 1) + ((k / 3) % 3 != 1) + (k % 3 != 1));
+  }
   if (threadIdx.x < 8) t.cnt[threadIdx.x] = 0u;
-  for (int i = threadIdx.x; i < (G::T3 + 31) / 32; i += NT) t.chg[i] = 0u;
+  for (int i = threadIdx.x; i < (G::T3 + 31) / 32; i += NT) {
+    t.chg[i] = 0u;
+    t.lseed[i] = 0u;
+  }
   for (int i = threadIdx.x; i < (2 * G::S3 + 31) / 32; i += NT) t.in[i] = 0u;
   __syncthreads();
   auto take_bits = [&]() {
@@ -276,7 +293,7 @@ __device__ void stage_tile(const DevMap& m, const TileRef& r, uint32_t* cur_bits
       while (chunk) {
         const int x = __ffs(chunk) - 1;
         chunk &= chunk - 1;
-        t.a[i++] = (uint16_t)((((z << G::LOGS) | y) << G::LOGS) | x);
+        t.a[i++] = (uint16_t)G::cell_of_local((((z << G::LOGS) | y) << G::LOGS) | x);
       }
     }
   };
@@ -447,7 +464,7 @@ __device__ void raise_tile(const DevMap& m, uint32_t item, uint32_t* cur_bits, c
       t.in[((it + 1) & 1) * (G::S3 / 32 > 0 ? G::S3 / 32 : 1) + j] = 0u;
     // reset the raised voxels first, so that no child test below sees a stale parent
     for (unsigned i = threadIdx.x; i < na; i += NT) {
-      const int c = G::cell_of_local(cur[i]);
+      const int c = cur[i];
       const unsigned long long w = t.w[c];
       const unsigned fl = ew_flags(w);
       if (!(fl & kFixed)) {
@@ -460,8 +477,8 @@ __device__ void raise_tile(const DevMap& m, uint32_t item, uint32_t* cur_bits, c
       const unsigned i = p / 26u;
       const int kk = (int)(p - i * 26u);
       const int k = kk < 13 ? kk : kk + 1;
-      const int c = G::cell_of_local(cur[i]);
-      const int nc = c + G::off(k);
+      const int c = cur[i];
+      const int nc = c + t.doff[k];
       const unsigned long long nw = t.w[nc];
       const unsigned nfl = ew_flags(nw);
       if (!(nfl & kObserved)) continue;
@@ -469,24 +486,28 @@ __device__ void raise_tile(const DevMap& m, uint32_t item, uint32_t* cur_bits, c
         if (cell_interior<B, S>(nc)) {
           const int nl = interior_local<B, S>(nc);
           const uint32_t bit = 1u << (nl & 31);
-          if (!(atomicOr(&inb[nl >> 5], bit) & bit)) smem_append(nxt, ncnt, (uint16_t)nl);
+          if (!(atomicOr(&inb[nl >> 5], bit) & bit)) smem_append(nxt, ncnt, (uint16_t)nc);
         } else {
           set_bit(ra.nxt_bits, cell_vid<B, S>(t, r, nc));
           atomicOr(&t.cnt[3], 1u << cell_tile_dir<B, S>(nc));
         }
-      } else {  // any other observed neighbour re-seeds the lower wave
-        set_bit(m.lbits0, cell_vid<B, S>(t, r, nc));
-        atomicOr(&t.cnt[4], 1u << cell_tile_dir<B, S>(nc));
+      } else {  // any other observed neighbour re-seeds the lower wave (marked once per cell below)
+        atomicOr(&t.lseed[nc >> 5], 1u << (nc & 31));
       }
     }
     __syncthreads();
   }
   if (threadIdx.x == 0) atomicAdd(&m.ctr->esdf_local_iters, iters);
-  // write back the raised voxels (raise rounds never lower words, plain stores suffice)
+  // write back the raised voxels (raise rounds never lower words, plain stores suffice), and
+  // the lower-wave seeds
   for (int c = threadIdx.x; c < G::T3; c += NT) {
-    if (!(t.chg[c >> 5] & (1u << (c & 31)))) continue;
-    m.esdf[cell_vid<B, S>(t, r, c)] = t.w[c];
+    if (t.chg[c >> 5] & (1u << (c & 31))) m.esdf[cell_vid<B, S>(t, r, c)] = t.w[c];
+    if (t.lseed[c >> 5] & (1u << (c & 31))) {
+      set_bit(m.lbits0, cell_vid<B, S>(t, r, c));
+      atomicOr(&t.cnt[4], 1u << cell_tile_dir<B, S>(c));
+    }
   }
+  __syncthreads();
   // activate the tiles that received raise (next round, or the queue) or lower (seed) bits
   if (ra.q) {  // the raise bits set by any thread precede the pushes' stamp checks
     __threadfence();
@@ -543,18 +564,18 @@ __device__ void lower_tile(const DevMap& m, uint32_t item, uint32_t* cur_bits, c
       const unsigned i = p / 26u;
       const int kk = (int)(p - i * 26u);
       const int k = kk < 13 ? kk : kk + 1;
-      const int c = G::cell_of_local(cur[i]);
+      const int c = cur[i];
       const unsigned long long w = t.w[c];
       if (!(ew_flags(w) & kObserved)) continue;
       const float dv = ew_d(w);
       const bool neg = dv < 0.0f;
-      const int nc = c + G::off(k);
+      const int nc = c + t.doff[k];
       const unsigned long long nw = t.w[nc];
       const unsigned nfl = ew_flags(nw);
       if ((nfl & (kObserved | kFixed)) != kObserved) continue;
       const float dn = ew_d(nw);
       if ((dn < 0.0f) != neg) continue;
-      const int n1 = (k / 9 != 1) + ((k / 3) % 3 != 1) + (k % 3 != 1);
+      const int n1 = t.dcls[k];
       const float cand = __fadd_rn(fabsf(dv), n1 == 1 ? L1 : (n1 == 2 ? L2 : L3));
       if (!(cand < fabsf(dn))) continue;
       const unsigned long long old = atomicMin(&t.w[nc], ew_pack(neg ? -cand : cand, nfl, (unsigned)(26 - k)));
@@ -563,7 +584,7 @@ __device__ void lower_tile(const DevMap& m, uint32_t item, uint32_t* cur_bits, c
       if (cell_interior<B, S>(nc)) {
         const int nl = interior_local<B, S>(nc);
         const uint32_t bit = 1u << (nl & 31);
-        if (!(atomicOr(&inb[nl >> 5], bit) & bit)) smem_append(nxt, ncnt, (uint16_t)nl);
+        if (!(atomicOr(&inb[nl >> 5], bit) & bit)) smem_append(nxt, ncnt, (uint16_t)nc);
       }
     }
     __syncthreads();
@@ -974,6 +995,312 @@ __global__ void __launch_bounds__(NT, NT == 256 ? VBX_ESDF_MINB_256 : (NT == 128
   }
 }
 
+// ------------------------------------------------------------------------------------------
+// Full Euclidean variant (Sec. V-A: the parent holds the full offset to the site instead of a
+// neighbour direction), one map per launch. Reading R13:
+//  * a site s (a fixed voxel) offers voxel n the distance |d_s| + v ||n - s||, each float32
+//    operation rounded once: fl(|d_s| + fl(v * sqrt(fl(q)))), q the squared offset in voxels;
+//  * classification follows the first loop of Algorithm 1, except that a fixed voxel whose
+//    value changes at all, or that leaves the band, is raised (voxels measured to it would
+//    otherwise keep a distance computed from its old value);
+//  * raise: a voxel is a child of a raised site iff it is measured to it; every voxel of the
+//    map is checked once (a lookup of its site's raised flag), children are reset to +-d_max
+//    without a site, and their observed neighbours join the lower wave;
+//  * lower: the tile work queue of the quasi-Euclidean wave, where a voxel offers its site
+//    (itself if fixed) to its observed, non-fixed, same-sign neighbours.
+// Nearest-site propagation through neighbours depends on the processing order, so the result
+// is one of several correct ones: every voxel's distance is exactly the offer of its stored
+// site, which is a fixed voxel of its sign, and no neighbour's site offers it less.
+
+__device__ __forceinline__ float site_offer(float v, float ds, int ox, int oy, int oz) {
+  const int q = ox * ox + oy * oy + oz * oz;
+  return __fadd_rn(ds, __fmul_rn(v, __fsqrt_rn((float)q)));
+}
+
+// Voxel id of global voxel coordinates (kInvalid if the block is not allocated).
+__device__ __forceinline__ uint32_t voxel_at(const DevMap& m, int x, int y, int z) {
+  const uint32_t slot = block_lookup(m, x >> m.blog, y >> m.blog, z >> m.blog);
+  if (slot == kInvalid || slot >= m.cap_blocks) return kInvalid;
+  const int B = m.B;
+  return (slot << m.b3log) | (uint32_t)((((z & (B - 1)) << m.blog | (y & (B - 1))) << m.blog) | (x & (B - 1)));
+}
+
+__device__ __forceinline__ int3 voxel_coords(const DevMap& m, uint32_t vid) {
+  const int3 bc = m.bcoord[vid >> m.b3log];
+  const uint32_t l = vid & ((1u << m.b3log) - 1u);
+  const int B = m.B;
+  return make_int3(bc.x * B + (int)(l & (B - 1)), bc.y * B + (int)((l >> m.blog) & (B - 1)), bc.z * B + (int)(l >> (2 * m.blog)));
+}
+
+// Puts the observed 26-neighbours of vid on the lower frontier (they offer their sites to it).
+__device__ void mark_observed_neighbours(const DevMap& m, uint32_t vid, EsdfCtl* ctl, unsigned e0) {
+  uint32_t last = kInvalid;
+  for (int k = 0; k < 27; ++k) {
+    if (k == 13) continue;
+    const uint32_t n = neighbor_vid(m, vid, k);
+    if (n == kInvalid) continue;
+    if (ew_flags(__ldcg(&m.esdf[n])) & kObserved) {
+      set_bit(m.lbits0, n);
+      const uint32_t nb = tile_item_of(m, n);
+      if (nb != last) activate(ctl->lact0, &ctl->lcnt[0], m.bstamp_l, nb, e0, 0u);
+      last = nb;
+    }
+  }
+}
+
+// Shared memory of a Euclidean lower tile: the tile of the quasi-Euclidean wave, then per active
+// voxel of the current local iteration its site's |d| and offset.
+__host__ __device__ inline size_t euclid_tile_bytes(int S) { return tile_bytes(S) + align16((size_t)S * S * S * 8); }
+
+// A8 with R13 for one staged tile (all threads of the CTA); the work-queue schedule only.
+template <int NT, int B, int S>
+__device__ void lower_tile_euclid(const DevMap& m, uint32_t item, const RoundArgs& ra, EsdfCtl* ctl, unsigned char* smem,
+                                  unsigned long long* pops) {
+  using G = Geo<B, S>;
+  const Tile t = carve(smem, S);
+  float* sds = reinterpret_cast<float*>(smem + tile_bytes(S));  // site |d| per active voxel (< 0: none)
+  int* soff = reinterpret_cast<int*>(sds + G::S3);              // packed site offset per active voxel
+  const TileRef r = tile_ref<B, S>(item);
+  stage_tile<NT, B, S>(m, r, m.lbits0, t, true);
+  const int3 bc = m.bcoord[r.slot];
+  const int gx = bc.x * B + r.ox, gy = bc.y * B + r.oy, gz = bc.z * B + r.oz;  // global origin of the tile
+  const float v = m.v;
+  for (int it = 0;; ++it) {
+    const unsigned na = t.cnt[it % 3];
+    if (na == 0) break;
+    if (it > kMaxLocalIters) {
+      if (threadIdx.x == 0) atomicOr(&ctl->error, kErrTimeout);
+      break;
+    }
+    const uint16_t* cur = (it & 1) ? t.b : t.a;
+    uint16_t* nxt = (it & 1) ? t.a : t.b;
+    unsigned* ncnt = &t.cnt[(it + 1) % 3];
+    uint32_t* inb = t.in + (it & 1) * (G::S3 / 32 > 0 ? G::S3 / 32 : 1);
+    if (threadIdx.x == 0) {
+      *pops += na;
+      t.cnt[(it + 2) % 3] = 0u;
+    }
+    for (int j = threadIdx.x; j < (G::S3 + 31) / 32; j += NT) t.in[((it + 1) & 1) * (G::S3 / 32 > 0 ? G::S3 / 32 : 1) + j] = 0u;
+    // the site each active voxel offers: itself if fixed, else its stored site (a fixed voxel,
+    // whose value does not change during the wave)
+    for (unsigned i = threadIdx.x; i < na; i += NT) {
+      const int c = cur[i];
+      const unsigned long long w = t.w[c];
+      const unsigned fl = ew_flags(w);
+      float ds = -1.0f;
+      int3 o = make_int3(0, 0, 0);
+      if (fl & kFixed) {
+        ds = fabsf(ew_d(w));
+      } else if ((fl & (kObserved | kHasSite)) == (kObserved | kHasSite)) {
+        o = ew_site(w);
+        int x, y, z;
+        G::xyz(c, &x, &y, &z);
+        const uint32_t sv = voxel_at(m, gx + x + o.x, gy + y + o.y, gz + z + o.z);
+        if (sv != kInvalid) {
+          const unsigned long long sw = __ldcg(&m.esdf[sv]);
+          if (ew_flags(sw) & kFixed) ds = fabsf(ew_d(sw));
+        }
+      }
+      sds[i] = ds;
+      soff[i] = (o.x & 0xff) | ((o.y & 0xff) << 8) | ((o.z & 0xff) << 16);
+    }
+    __syncthreads();
+    for (unsigned p = threadIdx.x; p < na * 26u; p += NT) {
+      const unsigned i = p / 26u;
+      const float ds = sds[i];
+      if (!(ds >= 0.0f)) continue;
+      const int kk = (int)(p - i * 26u);
+      const int k = kk < 13 ? kk : kk + 1;
+      const int c = cur[i];
+      const unsigned long long w = t.w[c];
+      const bool neg = ew_d(w) < 0.0f;
+      const int nc = c + t.doff[k];
+      const unsigned long long nw = t.w[nc];
+      const unsigned nfl = ew_flags(nw);
+      if ((nfl & (kObserved | kFixed)) != kObserved) continue;
+      const float dn = ew_d(nw);
+      if ((dn < 0.0f) != neg) continue;
+      const int so = soff[i];
+      // offset from the neighbour to the site: the voxel's offset minus the step to the neighbour
+      const int ox = (int)(signed char)(so & 0xff) - (k / 9 - 1);
+      const int oy = (int)(signed char)((so >> 8) & 0xff) - ((k / 3) % 3 - 1);
+      const int oz = (int)(signed char)((so >> 16) & 0xff) - (k % 3 - 1);
+      const float cand = site_offer(v, ds, ox, oy, oz);
+      if (!(cand < fabsf(dn))) continue;
+      const unsigned long long old = atomicMin(&t.w[nc], ew_pack_site(neg ? -cand : cand, nfl | kHasSite, ox, oy, oz));
+      if (!(fabsf(ew_d(old)) > cand)) continue;
+      atomicOr(&t.chg[nc >> 5], 1u << (nc & 31));
+      if (cell_interior<B, S>(nc)) {
+        const int nl = interior_local<B, S>(nc);
+        const uint32_t bit = 1u << (nl & 31);
+        if (!(atomicOr(&inb[nl >> 5], bit) & bit)) smem_append(nxt, ncnt, (uint16_t)nc);
+      }
+    }
+    __syncthreads();
+  }
+  // write back (global atomicMin), then frontier bits of lowered halo voxels, then the pushes
+  for (int c = threadIdx.x; c < G::T3; c += NT) {
+    if (!(t.chg[c >> 5] & (1u << (c & 31)))) continue;
+    atomicMin(&m.esdf[cell_vid<B, S>(t, r, c)], t.w[c]);
+  }
+  __threadfence();
+  __syncthreads();
+  for (int c = threadIdx.x; c < G::T3; c += NT) {
+    if (!(t.chg[c >> 5] & (1u << (c & 31))) || cell_interior<B, S>(c)) continue;
+    set_bit(m.lbits0, cell_vid<B, S>(t, r, c));
+    atomicOr(&t.cnt[3], 1u << cell_tile_dir<B, S>(c));
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x < 27 && (t.cnt[3] >> threadIdx.x & 1u)) {
+    const uint32_t nit = neighbor_tile_item<B, S>(t, r, threadIdx.x);
+    if (nit != kInvalid) q_push(*ra.q, 0u, nit, m.bstamp_l, ra.e0);
+  }
+  __syncthreads();
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT, 1) k_esdf_euclid(const DevMap* __restrict__ maps, EsdfCtl* ctl) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ unsigned long long cta_pops;
+  __shared__ int sh_state;
+  __shared__ uint2 sh_e;
+  __shared__ unsigned long long sh_t[4];
+  const DevMap& m = maps[0];
+  const unsigned tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned nthreads = gridDim.x * blockDim.x;
+  if (threadIdx.x == 0) sh_t[0] = global_ns();
+  if (tid == 0) atomicAdd(&ctl->calls, 1u);
+  if (ctl->rcap < ctl->cap + 27u * gridDim.x) {
+    if (tid == 0) atomicOr(&ctl->error, kErrTimeout);
+    return;
+  }
+  const unsigned ndirty = __ldcg(&m.ctr->ndirty);
+  const unsigned e0 = __ldcg(&m.ctr->epoch) + 1;
+  const float dmax = m.dmax;
+  // ---- classification (first loop of Algorithm 1, R6 and R13)
+  for (unsigned i = tid; i < ndirty; i += nthreads) {
+    const uint32_t vid = m.dirty[i];
+    m.vflags[vid] = (uint8_t)(m.vflags[vid] & ~kQueuedForEsdf);
+    const float2 tv = m.tsdf[vid];
+    if (!(tv.y > 0.0f)) continue;
+    const float Df = tv.x == 0.0f ? 0.0f : tv.x;  // sign(0) = +1
+    const bool occ = m.esdf_mode == 1;
+    const bool neg = !occ && Df < 0.0f;
+    const bool fixed_now = occ ? Df < 0.0f : fabsf(Df) < m.gamma;
+    const float seedv = occ ? 0.0f : Df;
+    const float sdmax = neg ? -dmax : dmax;
+    const unsigned long long w = __ldcg(&m.esdf[vid]);
+    const unsigned fl = ew_flags(w);
+    const bool obs = (fl & kObserved) != 0;
+    const float de = ew_d(w);
+    if (fixed_now) {
+      atomicAdd(&m.ctr->seeds, 1u);
+      if (obs && (fl & kFixed) && __float_as_uint(de) != __float_as_uint(seedv)) {
+        m.vflags[vid] = (uint8_t)(m.vflags[vid] | kSiteRaised);
+        atomicAdd(&ctl->rcnt[0], 1u);
+      }
+      m.esdf[vid] = ew_pack_site(seedv, kObserved | kFixed, 0, 0, 0);
+      set_bit(m.lbits0, vid);
+      activate(ctl->lact0, &ctl->lcnt[0], m.bstamp_l, tile_item_of(m, vid), e0, 0u);
+    } else if (fl & kFixed) {  // leaves the band: raised, and its neighbours offer their sites
+      m.vflags[vid] = (uint8_t)(m.vflags[vid] | kSiteRaised);
+      atomicAdd(&ctl->rcnt[0], 1u);
+      m.esdf[vid] = ew_pack_site(sdmax, kObserved, 0, 0, 0);
+      mark_observed_neighbours(m, vid, ctl, e0);
+    } else if (!obs || (de < 0.0f) != neg) {  // new voxel, or sign flip (nothing is measured to it)
+      m.esdf[vid] = ew_pack_site(sdmax, kObserved, 0, 0, 0);
+      mark_observed_neighbours(m, vid, ctl, e0);
+    }
+  }
+  if (!grid_barrier(&ctl->bar, gridDim.x, &ctl->error)) return;
+  if (threadIdx.x == 0) sh_t[1] = global_ns();
+  // ---- raise (R13): every voxel measured to a raised site is reset
+  const bool any_raised = __ldcg(&ctl->rcnt[0]) > 0u;
+  if (any_raised) {
+    const uint32_t V = min(__ldcg(&m.ctr->blocks), m.cap_blocks) << m.b3log;
+    unsigned long long nraised = 0;
+    for (uint32_t vid = tid; vid < V; vid += nthreads) {
+      const unsigned long long w = __ldcg(&m.esdf[vid]);
+      const unsigned fl = ew_flags(w);
+      if ((fl & (kObserved | kFixed | kHasSite)) != (kObserved | kHasSite)) continue;
+      const int3 c = voxel_coords(m, vid);
+      const int3 o = ew_site(w);
+      const uint32_t sv = voxel_at(m, c.x + o.x, c.y + o.y, c.z + o.z);
+      if (sv != kInvalid && !(__ldcg(&m.vflags[sv]) & kSiteRaised) && (ew_flags(__ldcg(&m.esdf[sv])) & kFixed)) continue;
+      m.esdf[vid] = ew_pack_site(ew_d(w) < 0.0f ? -dmax : dmax, kObserved, 0, 0, 0);
+      ++nraised;
+      mark_observed_neighbours(m, vid, ctl, e0);
+    }
+    if (nraised) atomicAdd(&m.ctr->raise_pops, nraised);
+    if (!grid_barrier(&ctl->bar, gridDim.x, &ctl->error)) return;
+    for (unsigned i = tid; i < ndirty; i += nthreads) {
+      const uint32_t vid = m.dirty[i];
+      m.vflags[vid] = (uint8_t)(m.vflags[vid] & ~kSiteRaised);
+    }
+  }
+  if (!grid_barrier(&ctl->bar, gridDim.x, &ctl->error)) return;
+  if (threadIdx.x == 0) sh_t[2] = global_ns();
+  // ---- lower: the tile work queue with site offers
+  WaveQueue q;
+  q.ctl = ctl;
+  q.init = ctl->lact0;
+  q.n0 = __ldcg(&ctl->lcnt[0]);
+  q.tag_epoch = 2u * __ldcg(&ctl->calls) + 1u;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      uint2 e = make_uint2(0u, 0u);
+      const int st = q_pop(q, &e);
+      if (st == 1) {
+        atomicExch(&m.bstamp_l[e.y], __ldcg(&m.ctr->epoch));  // e0 - 1: no longer queued
+        __threadfence();
+      }
+      sh_state = st;
+      sh_e = e;
+    }
+    __syncthreads();
+    const int st = sh_state;
+    const uint2 e = sh_e;
+    __threadfence();
+    __syncthreads();
+    if (st != 1) break;
+    RoundArgs ra;
+    ra.mi = 0;
+    ra.e0 = e0;
+    ra.ep_next = e0;
+    ra.nxt_bits = m.lbits0;
+    ra.nxt_list = nullptr;
+    ra.nxt_cnt = nullptr;
+    ra.q = &q;
+    if (threadIdx.x == 0) cta_pops = 0;
+    switch (m.B) {
+      case 4: lower_tile_euclid<NT, 4, 4>(m, e.y, ra, ctl, dsm, &cta_pops); break;
+      case 8: lower_tile_euclid<NT, 8, 8>(m, e.y, ra, ctl, dsm, &cta_pops); break;
+      default: lower_tile_euclid<NT, 16, kTileEdge>(m, e.y, ra, ctl, dsm, &cta_pops); break;
+    }
+    if (threadIdx.x == 0) {
+      if (cta_pops) atomicAdd(&m.ctr->lower_pops, cta_pops);
+      atomicAdd(&m.ctr->esdf_block_visits, 1u);
+      __threadfence();
+      atomicAdd(&ctl->qdone, 1u);
+    }
+  }
+  if (threadIdx.x == 0) sh_t[3] = global_ns();
+  __syncthreads();
+  if (tid == 0) {
+    Counters* c = m.ctr;
+    c->esdf_phase_ns[0] = (unsigned)(sh_t[1] - sh_t[0]);
+    c->esdf_phase_ns[1] = (unsigned)(sh_t[2] - sh_t[1]);
+    c->esdf_phase_ns[2] = (unsigned)(sh_t[3] - sh_t[2]);
+    c->esdf_in = ndirty;
+    c->raise_rounds = any_raised ? 1u : 0u;
+    c->lower_rounds = q.n0 > 0 ? 1u : 0u;
+    c->epoch = c->epoch + 4;
+    c->ndirty = 0;
+    if (__ldcg(&ctl->error) & kErrTimeout) atomicOr(&c->error, kErrTimeout);
+  }
+}
+
 }  // namespace
 
 size_t esdf_smem_bytes(int max_B) { return tile_bytes(max_B < kTileEdge ? max_B : kTileEdge); }
@@ -1016,6 +1343,21 @@ cudaError_t launch_esdf(const DevMap* maps_dev, int nmaps, int max_B, EsdfCtl* c
   void* args[] = {(void*)&maps_dev, (void*)&nmaps, (void*)&ctl, (void*)&async};
   hook->begin(kKEsdf, cfg.stream);
   cudaError_t e = cudaLaunchCooperativeKernel(k, dim3(grid), dim3(threads), args, smem, cfg.stream);
+  hook->end(kKEsdf, cfg.stream);
+  return e;
+}
+
+// Euclidean variant of one map (R13): cooperative launch of 512-thread CTAs.
+cudaError_t launch_esdf_euclid(const DevMap* map_dev, int B, EsdfCtl* ctl, const LaunchCfg& cfg, LaunchHook* hook) {
+  const void* k = (const void*)k_esdf_euclid<512>;
+  const size_t smem = euclid_tile_bytes(B < kTileEdge ? B : kTileEdge);
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return cudaErrorInvalidValue;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, 512, smem) != cudaSuccess || nb < 1) return cudaErrorCooperativeLaunchTooLarge;
+  nb = nb > 2 ? 2 : nb;
+  void* args[] = {(void*)&map_dev, (void*)&ctl};
+  hook->begin(kKEsdf, cfg.stream);
+  cudaError_t e = cudaLaunchCooperativeKernel(k, dim3(nb * cfg.num_sms), dim3(512), args, smem, cfg.stream);
   hook->end(kKEsdf, cfg.stream);
   return e;
 }

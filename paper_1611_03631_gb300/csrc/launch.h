@@ -118,6 +118,8 @@ size_t esdf_smem_bytes(int max_B);
 int esdf_grid(int num_sms, int max_B, int ctas_per_sm, int threads);
 // allow_async: the raise and lower waves may run as asynchronous work queues instead of rounds
 // (the kernel takes them when few maps of the launch have work)
+// Full Euclidean ESDF update of one map (the map's device descriptor, block edge B).
+cudaError_t launch_esdf_euclid(const DevMap* map_dev, int B, EsdfCtl* ctl, const LaunchCfg& cfg, LaunchHook* hook);
 cudaError_t launch_esdf(const DevMap* maps_dev, int nmaps, int max_B, EsdfCtl* ctl, const LaunchCfg& cfg,
                         LaunchHook* hook, bool allow_async);
 

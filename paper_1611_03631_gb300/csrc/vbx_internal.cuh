@@ -52,8 +52,10 @@ constexpr unsigned kErrScratchFull = 16u;
 // ESDF voxel word: bits 63..32 float d, bits 15..8 flags, bits 7..0 parent direction
 constexpr unsigned kObserved = 1u;
 constexpr unsigned kFixed = 2u;
+constexpr unsigned kHasSite = 4u;  // Euclidean variant: the word holds the offset to its site
 constexpr unsigned kNoParent = 255u;
 constexpr uint8_t kQueuedForEsdf = 1u;
+constexpr uint8_t kSiteRaised = 2u;  // Euclidean variant: a site raised by this ESDF update
 
 struct __align__(16) GroupEntry {
   unsigned long long key;       // packed voxel key, kEmptyKey when free
@@ -135,6 +137,7 @@ struct DevMap {
   float max_range2;  // <= 0: no range limit
   float range_lim2;  // (16384 v)^2: points farther than 2^14 voxels are dropped
   float L1, L2, L3;  // quasi-Euclidean step lengths v, v*sqrt(2), v*sqrt(3)
+  int euclid;        // 1: full Euclidean ESDF (the word holds the offset to the site)
   int B, blog, b3log;
   int tile_shift;  // log2 of the ESDF tiles per block: 3 for B = 16 (8^3 octants), else 0
   int weighting, grouped;
@@ -260,6 +263,16 @@ __device__ __forceinline__ unsigned long long ew_pack(float d, unsigned flags, u
 __device__ __forceinline__ float ew_d(unsigned long long w) { return __uint_as_float((uint32_t)(w >> 32)); }
 __device__ __forceinline__ unsigned ew_flags(unsigned long long w) { return (unsigned)(w >> 8) & 0xffu; }
 __device__ __forceinline__ unsigned ew_parent(unsigned long long w) { return (unsigned)w & 0xffu; }
+// Euclidean variant: {d | oz (i8) | oy (i8) | flags | ox (i8)}, the offset from the voxel to its
+// site in voxels (|offset| <= d_max / v < 127)
+__device__ __forceinline__ unsigned long long ew_pack_site(float d, unsigned flags, int ox, int oy, int oz) {
+  return ((unsigned long long)__float_as_uint(d) << 32) | ((unsigned long long)((unsigned)oz & 0xffu) << 24) |
+         ((unsigned long long)((unsigned)oy & 0xffu) << 16) | ((unsigned long long)(flags & 0xffu) << 8) |
+         (unsigned long long)((unsigned)ox & 0xffu);
+}
+__device__ __forceinline__ int3 ew_site(unsigned long long w) {
+  return make_int3((int)(signed char)(w & 0xffu), (int)(signed char)((w >> 16) & 0xffu), (int)(signed char)((w >> 24) & 0xffu));
+}
 
 // Voxel id of the 26-neighbour in direction k (kInvalid if its block does not exist).
 __device__ __forceinline__ uint32_t neighbor_vid(const DevMap& m, uint32_t vid, int k) {

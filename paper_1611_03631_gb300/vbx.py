@@ -51,6 +51,7 @@ class vbx_map_options(ctypes.Structure):
         ("max_points", ctypes.c_int64),
         ("scratch_blocks", ctypes.c_int64),
         ("esdf_mode", ctypes.c_int),
+        ("euclidean", ctypes.c_int),
     ]
 
 
@@ -98,6 +99,11 @@ class vbx_query_io(ctypes.Structure):
 
 STEP_INTEGRATE, STEP_ESDF, STEP_QUERY, STEP_GRAPH = 1, 2, 4, 8
 
+# numpy records with the layouts of vbx_scan_in and vbx_query_io
+SCAN_IN_DTYPE = np.dtype([("points_dev", "<u8"), ("n", "<i8"), ("T", "<f4", (16,))])
+QUERY_IO_DTYPE = np.dtype([("q_dev", "<u8"), ("n", "<i8"), ("dist_dev", "<u8"), ("grad_dev", "<u8"), ("status_dev", "<u8")])
+assert SCAN_IN_DTYPE.itemsize == ctypes.sizeof(vbx_scan_in) and QUERY_IO_DTYPE.itemsize == ctypes.sizeof(vbx_query_io)
+
 _lib = None
 
 # exported symbols and their (restype, argtypes)
@@ -119,6 +125,7 @@ _SIGS = {
     "vbx_num_blocks": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), _vp]),
     "vbx_export_blocks": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _i64, _vp]),
     "vbx_export_updated": (ctypes.c_int, [_vp, _vp, _i64, ctypes.POINTER(_i64), _vp]),
+    "vbx_export_sites": (ctypes.c_int, [_vp, _vp, _vp, _i64, _vp]),
     "vbx_import_tsdf": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i64, _vp]),
     "vbx_set_profiling": (ctypes.c_int, [_vp, ctypes.c_int]),
     "vbx_get_kernel_times": (
@@ -216,6 +223,7 @@ class Map:
         max_points: int = 0,
         scratch_blocks: int = 0,
         esdf_mode: int = 0,
+        euclidean: bool = False,
     ):
         import torch
 
@@ -234,6 +242,7 @@ class Map:
         o.max_points = int(max_points)
         o.scratch_blocks = int(scratch_blocks)
         o.esdf_mode = int(esdf_mode)
+        o.euclidean = 1 if euclidean else 0
         h = ctypes.c_void_p()
         _check(self._lib.vbx_create_map(voxel_size, voxels_per_block, truncation, max_esdf_dist, ctypes.byref(o), ctypes.byref(h)))
         self._h = h
@@ -332,6 +341,22 @@ class Map:
             order = np.lexsort((keys[:, 2], keys[:, 1], keys[:, 0]))
             keys, tsdf, d, parent, flags = keys[order], tsdf[order], d[order], parent[order], flags[order]
         return dict(keys=keys, D=tsdf[..., 0], W=tsdf[..., 1], d=d, parent=parent, flags=flags)
+
+    def export_sites(self, sort: bool = True, stream=None):
+        """Euclidean maps: (offsets (nb, B^3, 3) int8 site - voxel, has_site (nb, B^3) bool), in
+        the block order of export(sort)."""
+        nb = self.num_blocks(stream)
+        B3 = self.B ** 3
+        off = np.zeros((max(nb, 1), B3, 3), np.int8)
+        has = np.zeros((max(nb, 1), B3), np.uint8)
+        keys = np.zeros((max(nb, 1), 3), np.int32)
+        _check(self._lib.vbx_export_sites(self._h, off.ctypes.data, has.ctypes.data, max(nb, 1), _stream_ptr(stream)))
+        _check(self._lib.vbx_export_blocks(self._h, keys.ctypes.data, None, None, None, None, max(nb, 1), _stream_ptr(stream)))
+        off, has, keys = off[:nb], has[:nb].astype(bool), keys[:nb]
+        if sort and nb:
+            order = np.lexsort((keys[:, 2], keys[:, 1], keys[:, 0]))
+            off, has = off[order], has[order]
+        return off, has
 
     def last_updated(self, stream=None) -> np.ndarray:
         n = ctypes.c_int64()
@@ -432,8 +457,9 @@ class MapBatch:
         _check(self._lib.vbx_batch_create(arr, len(self.maps), int(max_queries), ctypes.byref(h)))
         self._h = h
         self.count = len(self.maps)
-        self._scans = (vbx_scan_in * self.count)()
-        self._queries = (vbx_query_io * self.count)()
+        # descriptors as numpy records with the C layouts of vbx_scan_in / vbx_query_io
+        self._scans = np.zeros(self.count, SCAN_IN_DTYPE)
+        self._queries = np.zeros(self.count, QUERY_IO_DTYPE)
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -450,39 +476,41 @@ class MapBatch:
         _check(self._lib.vbx_batch_bind(self._h, int(slot), m.handle))
         self.maps[slot] = m
 
-    def _fill(self, points, poses, queries):
-        for i in range(self.count):
-            s = self._scans[i]
-            p = points[i] if points is not None else None
-            if p is None or p.shape[0] == 0:
-                s.points_dev, s.n = None, 0
-            else:
+    def _fill(self, points, poses, queries, slots=None):
+        """Descriptors of one step. Without `slots`, points / poses / queries have one entry per
+        slot (None: nothing for that slot); with `slots`, they hold entries for those slots only
+        and every other slot is idle."""
+        sc, qd = self._scans, self._queries
+        sc["points_dev"] = 0
+        sc["n"] = 0
+        qd[:] = 0
+        idx = range(self.count) if slots is None else slots
+        for j, i in enumerate(idx):
+            k = i if slots is None else j
+            p = points[k] if points is not None else None
+            if p is not None and p.shape[0] > 0:
                 _dev_f32(p, 3)
-                s.points_dev, s.n = p.data_ptr(), p.shape[0]
-            if poses is not None and poses[i] is not None:
-                T = np.asarray(poses[i], dtype=np.float32).reshape(16)
-                for j in range(16):
-                    s.T_world_sensor[j] = float(T[j])
-            q = self._queries[i]
-            if queries is None or queries[i] is None:
-                q.q_dev, q.n, q.dist_dev, q.grad_dev, q.status_dev = None, 0, None, None, None
-            else:
-                qq, dist, grad, status = queries[i]
+                sc["points_dev"][i] = p.data_ptr()
+                sc["n"][i] = p.shape[0]
+            if poses is not None and poses[k] is not None:
+                sc["T"][i] = np.asarray(poses[k], dtype=np.float32).reshape(16)
+            if queries is not None and queries[k] is not None:
+                qq, dist, grad, status = queries[k]
                 _dev_f32(qq, 3)
-                q.q_dev, q.n = qq.data_ptr(), qq.shape[0]
-                q.dist_dev, q.grad_dev, q.status_dev = dist.data_ptr(), grad.data_ptr(), status.data_ptr()
+                qd[i] = (qq.data_ptr(), qq.shape[0], dist.data_ptr(), grad.data_ptr(), status.data_ptr())
 
-    def step(self, points=None, poses=None, queries=None, flags: int = STEP_INTEGRATE | STEP_ESDF, stream=None) -> None:
-        """points[i]: (N,3) device tensor or None; poses[i]: 4x4; queries[i]: (q, dist, grad, status) or None."""
-        self._fill(points, poses, queries)
-        _check(self._lib.vbx_batch_step(self._h, ctypes.byref(self._scans), ctypes.byref(self._queries), int(flags), _stream_ptr(stream)))
+    def step(self, points=None, poses=None, queries=None, flags: int = STEP_INTEGRATE | STEP_ESDF, stream=None, slots=None) -> None:
+        """points[i]: (N,3) device tensor or None; poses[i]: 4x4; queries[i]: (q, dist, grad, status)
+        or None; one entry per slot, or per listed slot when `slots` is given."""
+        self._fill(points, poses, queries, slots)
+        _check(self._lib.vbx_batch_step(self._h, self._scans.ctypes.data, self._queries.ctypes.data, int(flags), _stream_ptr(stream)))
 
     def autotune(self, points=None, poses=None, queries=None, flags: int = STEP_INTEGRATE | STEP_ESDF, stream=None) -> str:
         self._fill(points, poses, queries)
         buf = ctypes.create_string_buffer(256)
         _check(
             self._lib.vbx_batch_autotune(
-                self._h, ctypes.byref(self._scans), ctypes.byref(self._queries), int(flags), _stream_ptr(stream), buf, 256
+                self._h, self._scans.ctypes.data, self._queries.ctypes.data, int(flags), _stream_ptr(stream), buf, 256
             )
         )
         return buf.value.decode()
