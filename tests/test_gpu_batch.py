@@ -1,9 +1,12 @@
 """Batched form: several maps of different scenes and parameters advanced by the same
-launches (direct and CUDA-graph replay) give exactly the maps each would reach alone."""
+launches (direct and CUDA-graph replay) give exactly the maps each would reach alone, and
+every batched map matches the float64 oracle run on the same scans."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_1611_03631_gb300 import scenes
+from parity_util import compare_with_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -55,6 +58,7 @@ def test_batch_matches_maps_updated_alone(vbx, graph):
     alone = _maps(vbx, ss)
     mixed = _maps(vbx, ss)
     batch = vbx.MapBatch(mixed, max_queries=2048)
+    orc = [oracle.OracleMap.from_scene_params(s.params) for s in ss]
     flags = vbx.STEP_INTEGRATE | vbx.STEP_ESDF | (vbx.STEP_GRAPH if graph else 0)
     for f in range(3):
         pts = [torch.from_numpy(s.points[f]).cuda() for s in ss]
@@ -65,6 +69,10 @@ def test_batch_matches_maps_updated_alone(vbx, graph):
         batch.sync()
         for a, b in zip(alone, mixed):
             _same(a, b)
+        for o, s, b in zip(orc, ss, mixed):
+            o.integrate(s.points[f], s.poses[f])
+            o.update_esdf()
+            compare_with_oracle(b.export(), o.export(), s.params)
     # queries through the batch equal the single-map queries
     qs = [torch.from_numpy(scenes.random_queries(s, 1500, radius=2.0, seed=3)).cuda() for s in ss]
     outs = [(q, torch.empty(q.shape[0], device="cuda"), torch.empty((q.shape[0], 3), device="cuda"),

@@ -1,9 +1,12 @@
 """Served form: sessions admitted under a memory budget and advanced by continuously
-re-formed batches give the same map and query results as each session run alone."""
+re-formed batches (several steps in flight) give the same map and query results as each
+session run alone, and every session's map matches the float64 oracle on the same frames."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_1611_03631_gb300 import scenes
+from parity_util import compare_with_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -62,6 +65,12 @@ def test_sessions_alone_equal_sessions_in_the_mix(mods):
             m.update_esdf()
         d, g, st = m.query(q)
         ex, (d2, g2, st2) = got[spec.sid]
+        o = oracle.OracleMap.from_scene_params(pool.params[spec.kind])
+        for k in range(spec.n_scans):
+            f = (spec.offset + k) % len(sets[spec.kind][spec.seq].points)
+            o.integrate(sets[spec.kind][spec.seq].points[f], sets[spec.kind][spec.seq].poses[f])
+            o.update_esdf()
+        compare_with_oracle(ex, o.export(), pool.params[spec.kind])
         mine = m.export()
         assert np.array_equal(mine["keys"], ex["keys"])
         assert np.array_equal(mine["flags"], ex["flags"])
