@@ -330,23 +330,21 @@ class MapServer:
                 else:
                     time.sleep(5e-5)
                 continue
-            points = [None] * self.slots
-            poses = [None] * self.slots
-            queries = [None] * self.slots
-            scans = []
+            points, poses, queries, scans = [], [], [], []
             for s in ready:
                 a = active[s]
                 p, T, q = self.pool.frame(a.spec, a.next)
-                points[s], poses[s] = p, T
-                queries[s] = (q,) + self.out[s]
+                points.append(p)
+                poses.append(T)
+                queries.append((q,) + self.out[s])
                 scans.append((float(a.arrivals[a.next]), a.spec.kind, a.next == 0))
             if in_flight:
                 overlap_issues += 1
             f = dict(e0=event(), e1=event(), e2=event(), scans=scans, t_scan=None, t_issue=time.perf_counter() - t0)
             f["e0"].record()
-            self.batch.step(points, poses, flags=flags_map)
+            self.batch.step(points, poses, flags=flags_map, slots=ready)
             f["e1"].record()
-            self.batch.step(queries=queries, flags=flags_q)
+            self.batch.step(queries=queries, flags=flags_q, slots=ready)
             f["e2"].record()
             in_flight.append(f)
             batch_sizes.append(len(ready))
