@@ -20,7 +20,7 @@ namespace vbx {
 const char* const kKernelNames[kNumKernels] = {"reset_counters", "bin_points",  "group_rays",  "link_blocks",
                                                "integrate_rays", "apply",       "esdf",        "query",
                                                "import_alloc",   "import_set",  "init_groups", "mesh_select",
-                                               "mesh_blocks",    "mesh_clear"};
+                                               "mesh_blocks",    "mesh_clear",  "scratch_links"};
 }  // namespace vbx
 
 namespace {
@@ -334,6 +334,7 @@ vbx_status vbx_create_map(float voxel_size, int voxels_per_block, float truncati
   VBX_ALLOC(d.tsdf, V, 0);
   VBX_ALLOC(d.slist_h, (size_t)scr, 0);
   VBX_ALLOC(d.slist, (size_t)scr, 0);
+  VBX_ALLOC(d.snbr, (size_t)scr * 27, 0xff);
   VBX_ALLOC(d.sacc, 4 * SV, 0);
   VBX_ALLOC(d.stouch, SV, 0);
   VBX_ALLOC(d.esdf, V, 0);
@@ -1179,7 +1180,7 @@ vbx_status vbx_map_bytes(int B, const vbx_map_options* opt_in, int64_t* out) {
   bytes += cap * (12 + 27 * 4 + 8 + 4 + 1 + 4);           // block coords, links, scratch index/epoch, new list,
                                                           // mesh marks and list
   bytes += V * (8 + 8 + 1 + 4 + 4);                       // tsdf, esdf, flags, updated and dirty lists
-  bytes += scr * (4 + 4) + scr * B3 * (32 + 1);           // scratch blocks: lists, sums, touch flags
+  bytes += scr * (4 + 4 + 27 * 4) + scr * B3 * (32 + 1);  // scratch blocks: lists, neighbour links, sums, touch flags
   bytes += 4 * (V / 32) * 4;                              // frontier bitmasks
   bytes += tiles * (2 * 4 + 4 * 8);                       // tile stamps, active lists
   {

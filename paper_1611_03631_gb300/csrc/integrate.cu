@@ -490,6 +490,31 @@ __global__ void __launch_bounds__(kThreads) k_link_blocks(Batch b) {
   }
 }
 
+// The scratch block of each neighbour of every scratch block of the scan, so that a ray stepping
+// into the next block needs one load of a table its lane prefetched, not a chain of two (the
+// neighbour's pool slot, then that slot's scratch block).
+__global__ void __launch_bounds__(kThreads) k_scratch_links(Batch b) {
+  __shared__ unsigned pfx[kMaxBatch + 1];
+  const int nm = nmaps_of(b);
+  const unsigned total = cta_prefix(pfx, b, [&](unsigned mi) { return scratch_blocks(map_of(b, mi)) * 27u; });
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    const unsigned mi = map_index(pfx, nm, t);
+    const DevMap& m = map_of(b, mi);
+    const unsigned u = t - pfx[mi];
+    const unsigned i = u / 27u, k = u % 27u;
+    const uint32_t slot = __ldcg(&m.slist[i]);
+    uint32_t sb = kInvalid;
+    if (slot < m.cap_blocks) {
+      const uint32_t q = k == 13 ? slot : __ldcg(&m.nbr[(size_t)slot * 27 + k]);
+      if (q != kInvalid && q < m.cap_blocks) {
+        const unsigned long long w = __ldcg(&m.sinfo[q]);
+        if ((unsigned)(w >> 32) == scan_of(b, mi).epoch) sb = (uint32_t)w;
+      }
+    }
+    m.snbr[(size_t)i * 27 + k] = sb;
+  }
+}
+
 // ------------------------------------------------------------------------------------ A4
 // Splits a float32 record into its exact two-part fixed-point representation.
 __device__ __forceinline__ void fx_split(float x, long long* hi, long long* lo) {
@@ -581,7 +606,8 @@ __global__ void __launch_bounds__(kThreads, VBX_RAYS_MIN_CTAS) k_integrate_rays(
       Dda dda;
       int dsel = 0, left = 0, dk = 0;
       int bcx = 0, bcy = 0, bcz = 0;
-      uint32_t slot = kInvalid, sb = kInvalid;
+      uint32_t sb = kInvalid;
+      uint32_t nx = kInvalid, ny = kInvalid, nz = kInvalid;  // scratch blocks behind the three exit faces
       if (active) {
         for (int a = 0; a < 3; ++a) {
           gp[a] = sh_pg[wid][own][a];
@@ -595,8 +621,13 @@ __global__ void __launch_bounds__(kThreads, VBX_RAYS_MIN_CTAS) k_integrate_rays(
         bcx = dda.cx >> blog;
         bcy = dda.cy >> blog;
         bcz = dda.cz >> blog;
-        slot = block_lookup(m, bcx, bcy, bcz);
-        sb = scratch_of(m, slot, ep);
+        sb = scratch_of(m, block_lookup(m, bcx, bcy, bcz), ep);
+        if (sb != kInvalid) {
+          const uint32_t* row = &m.snbr[(size_t)sb * 27];
+          nx = __ldcg(&row[(dda.sx + 1) * 9 + 4]);
+          ny = __ldcg(&row[9 + (dda.sy + 1) * 3 + 1]);
+          nz = __ldcg(&row[13 + dda.sz]);
+        }
       }
       while (__any_sync(kFull, active)) {
         uint32_t vid = kInvalid;
@@ -638,30 +669,36 @@ __global__ void __launch_bounds__(kThreads, VBX_RAYS_MIN_CTAS) k_integrate_rays(
             if (ax == dsel && ++dk == K) {
               active = false;  // the next cell starts the ray's next segment
             } else {
-              // block transition: a 6-connected step into the face neighbour
-              int k = -1;
+              // block transition: a 6-connected step into the face neighbour, whose scratch
+              // block this lane loaded when it entered the current block
+              bool moved = false;
               if (ax == 0) {
                 const int nb = dda.cx >> blog;
                 if (nb != bcx) {
                   bcx = nb;
-                  k = (dda.sx + 1) * 9 + 4;
+                  sb = nx;
+                  moved = true;
                 }
               } else if (ax == 1) {
                 const int nb = dda.cy >> blog;
                 if (nb != bcy) {
                   bcy = nb;
-                  k = 9 + (dda.sy + 1) * 3 + 1;
+                  sb = ny;
+                  moved = true;
                 }
               } else {
                 const int nb = dda.cz >> blog;
                 if (nb != bcz) {
                   bcz = nb;
-                  k = 13 + dda.sz;
+                  sb = nz;
+                  moved = true;
                 }
               }
-              if (k >= 0) {
-                slot = slot != kInvalid ? __ldg(&m.nbr[(size_t)slot * 27 + k]) : block_lookup(m, bcx, bcy, bcz);
-                sb = scratch_of(m, slot, ep);
+              if (moved && sb != kInvalid) {
+                const uint32_t* row = &m.snbr[(size_t)sb * 27];
+                nx = __ldcg(&row[(dda.sx + 1) * 9 + 4]);
+                ny = __ldcg(&row[9 + (dda.sy + 1) * 3 + 1]);
+                nz = __ldcg(&row[13 + dda.sz]);
               }
             }
           }
@@ -722,8 +759,15 @@ __device__ __forceinline__ unsigned apply_flags_per_lane(const DevMap& m, bool w
 // are cleared, and it joins the scan's updated list and (once) the queue of the next ESDF
 // update. Each lane reads the touch flags of 4 or 16 consecutive scratch voxels; the warp
 // compacts the touched ones (possibly of two maps) and gives each lane one at a time.
+// One map per launch: the updated and queued voxels of a CTA are collected in shared memory and
+// each list's space is reserved with one atomic per CTA flush, not one per warp round (the two
+// counters of a map would otherwise take tens of thousands of serialised atomics per scan).
+constexpr int kApplyBuf = 2048;
+
 __global__ void __launch_bounds__(kThreads) k_apply(Batch b, unsigned warp_slots) {
   __shared__ unsigned pfx[kMaxBatch + 1];
+  __shared__ uint32_t s_upd[kApplyBuf], s_dty[kApplyBuf];
+  __shared__ unsigned s_cnt[2], s_base[2];
   const int lane = threadIdx.x & 31;
   const int nm = nmaps_of(b);
   // 16 flags per lane only when the launch has enough scratch voxels to keep every resident
@@ -736,7 +780,27 @@ __global__ void __launch_bounds__(kThreads) k_apply(Batch b, unsigned warp_slots
     return (scratch_blocks(m) << m.b3log) / apply_flags_per_lane(m, wide);  // B^3 >= 64
   });
   const unsigned stride = gridDim.x * blockDim.x;
-  for (unsigned base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < total; base += stride) {
+  // 4 flags per lane at most: one CTA round appends at most kThreads * 4 voxels to each list
+  const bool buffered = nm == 1 && !wide;
+  static_assert(kApplyBuf >= 2 * kThreads * 4, "a CTA round fits the half-full buffer");
+  if (threadIdx.x == 0) s_cnt[0] = s_cnt[1] = 0u;
+  __syncthreads();
+  auto flush = [&]() {  // all threads of the CTA
+    __syncthreads();
+    const DevMap& m = map_of(b, 0);
+    if (threadIdx.x == 0) {
+      s_base[0] = s_cnt[0] ? atomicAdd(&m.ctr->nupdated, s_cnt[0]) : 0u;
+      s_base[1] = s_cnt[1] ? atomicAdd(&m.ctr->ndirty, s_cnt[1]) : 0u;
+    }
+    __syncthreads();
+    for (unsigned j = threadIdx.x; j < s_cnt[0]; j += kThreads) m.updated[s_base[0] + j] = s_upd[j];
+    for (unsigned j = threadIdx.x; j < s_cnt[1]; j += kThreads) m.dirty[s_base[1] + j] = s_dty[j];
+    __syncthreads();
+    if (threadIdx.x == 0) s_cnt[0] = s_cnt[1] = 0u;
+    __syncthreads();
+  };
+  for (unsigned cbase = blockIdx.x * blockDim.x; cbase < total; cbase += stride) {
+    const unsigned base = cbase + (threadIdx.x & ~31u);
     const unsigned i = base + lane;
     unsigned mi = 0, v0 = 0, bits = 0;
     uint32_t slot = 0;
@@ -798,9 +862,30 @@ __global__ void __launch_bounds__(kThreads) k_apply(Batch b, unsigned warp_slots
       m.tsdf[vid] = make_float2(D, fminf(Wn, m.wmax));
       const bool queue = !(vf & kQueuedForEsdf);
       if (queue) m.vflags[vid] = (uint8_t)(vf | kQueuedForEsdf);
-      append_updated_dirty(m, vid, queue);
+      if (buffered) {
+        const unsigned act = __activemask();
+        const unsigned qm = __ballot_sync(act, queue);
+        const int leader = __ffs(act) - 1;
+        const unsigned below = (1u << lane) - 1u;
+        unsigned bu = 0, bd = 0;
+        if (lane == leader) {
+          bu = atomicAdd(&s_cnt[0], (unsigned)__popc(act));
+          if (qm) bd = atomicAdd(&s_cnt[1], (unsigned)__popc(qm));
+        }
+        bu = __shfl_sync(act, bu, leader);
+        bd = __shfl_sync(act, bd, leader);
+        s_upd[bu + __popc(act & below)] = vid;
+        if (queue) s_dty[bd + __popc(qm & below)] = vid;
+      } else {
+        append_updated_dirty(m, vid, queue);
+      }
+    }
+    if (buffered) {
+      __syncthreads();
+      if (s_cnt[0] > (unsigned)(kApplyBuf - kThreads * 4)) flush();
     }
   }
+  if (buffered) flush();
 }
 
 // ------------------------------------------------------------------------------ reset
@@ -944,6 +1029,9 @@ cudaError_t launch_integrate(const Batch& b, const LaunchCfg& cfg, LaunchHook* h
   hook->begin(kKLink, s);
   k_link_blocks<<<cfg.num_sms * 4, kThreads, 0, s>>>(b);
   hook->end(kKLink, s);
+  hook->begin(kKScratchLinks, s);
+  k_scratch_links<<<cfg.num_sms * 4, kThreads, 0, s>>>(b);
+  hook->end(kKScratchLinks, s);
   hook->begin(kKIntegrateRays, s);
   k_integrate_rays<<<grays, kThreads, 0, s>>>(b, (unsigned)(grays * kWarps));
   hook->end(kKIntegrateRays, s);

@@ -92,6 +92,7 @@ enum KernelId {
   kKMeshSelect,
   kKMeshBlocks,
   kKMeshClear,
+  kKScratchLinks,
   kNumKernels
 };
 

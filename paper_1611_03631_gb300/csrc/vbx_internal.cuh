@@ -157,6 +157,8 @@ struct DevMap {
   uint32_t scr_cap;
   uint32_t* slist_h;
   uint32_t* slist;
+  uint32_t* snbr;  // per scratch block of the current scan: the scratch block of each of its 27
+                   // neighbours (kInvalid if that block has none this scan)
   unsigned long long* sacc;
   uint8_t* stouch;
   unsigned long long* esdf;
