@@ -55,21 +55,23 @@ FLUSH_BYTES = 256 << 20  # > 129 MB L2
 # and the SHA-256 prefix of the source files it was captured on (KERNEL_SOURCE): once one of
 # them changes the entry no longer matches and the reported traffic is null.
 NCU_TRAFFIC = {
-    # k_integrate_rays, LiDAR growth scan 3 (dram__bytes_read.sum 62,646,528 + write 27,521,792)
-    ("integrate_rays", "integrate.cu", "8cc3dfdaee1ac4cf"): 90168320,
-    # k_apply, LiDAR growth scan 3 (dram__bytes_read.sum 94,035,712 + write 39,201,792)
-    ("apply", "integrate.cu", "8cc3dfdaee1ac4cf"): 133237504,
-    # k_esdf<512> x 2 per SM, room workload, one scan (dram__bytes_read.sum 2,320,384 + write 47,616)
-    ("esdf", "esdf.cu", "5f585b9c2a3af0cc"): 2368000,
+    # LiDAR growth scan 3 (bench.py --only-headline --no-cpu-baseline --steps 3 --warmup 3):
+    # dram__bytes.sum.per_second x gpu__time_duration.sum of one launch each
+    # k_integrate_rays: 0.186846 TB/s x 0.486176 ms
+    ("integrate_rays", "lidar", "integrate.cu", "acd45f923c02b257"): 90840000,
+    # k_apply: 2.624806 TB/s x 0.050208 ms
+    ("apply", "lidar", "integrate.cu", "acd45f923c02b257"): 131790000,
+    # k_esdf<512> x 2 per SM: 0.045752 TB/s x 1.743040 ms
+    ("esdf", "lidar", "esdf.cu", "44d12481f39866bc"): 79750000,
     # k_mesh_blocks<16>, full mesh of the room map (dram__bytes_read.sum 25,988,096 + write 2,304;
     # the 17 MB of triangles it writes are still in L2 when it ends)
-    ("mesh_blocks", "mesh.cu", "cbd5b0c8554fc2d5"): 25990400,
+    ("mesh_blocks", "room", "mesh.cu", "cbd5b0c8554fc2d5"): 25990400,
 }
 # the files a kernel's code and launch shape come from (the single-map ESDF shape is in launch.h)
 KERNEL_SOURCE = {"mesh_blocks": "mesh.cu", "esdf": ("esdf.cu", "launch.h"), "integrate_rays": "integrate.cu", "apply": "integrate.cu", "bin_points": "integrate.cu", "query": "query.cu"}
 
 
-def _ncu_traffic(kernel: str):
+def _ncu_traffic(kernel: str, workload: str):
     import hashlib
 
     srcs = KERNEL_SOURCE.get(kernel)
@@ -80,7 +82,7 @@ def _ncu_traffic(kernel: str):
     for src in srcs:
         with open(os.path.join(ROOT, "paper_1611_03631_gb300", "csrc", src), "rb") as f:
             h.update(f.read())
-    return NCU_TRAFFIC.get((kernel, srcs[0], h.hexdigest()[:16]))
+    return NCU_TRAFFIC.get((kernel, workload, srcs[0], h.hexdigest()[:16]))
 
 
 def _scene(frames: int):
@@ -148,8 +150,8 @@ def _workers():
 
 
 BATCH_MAPS = 64
-BATCH_FRAMES = 4
 BATCH_STEPS = 20  # timed steps of the batched sections (after 3 warm-up steps)
+BATCH_FRAMES = BATCH_STEPS + 3  # every warm-up and timed step integrates a scan the map has not seen
 SERVE_SESSIONS = 256
 SERVE_SLOTS = 128
 SERVE_BUDGET = 120e9
@@ -160,6 +162,9 @@ SERVE_C1_ARRIVALS = 256.0  # enough concurrent robots to offer more scans/s than
 SERVE_C1_SESSIONS = 768
 SERVE_C1_SLOTS = 256
 SERVE_C1_CAPACITY = {"plane_sphere": 45056}  # the 10-frame circle allocates about 42.3k blocks of 8^3
+# a plane+sphere map of that capacity takes about 0.85 GB: 120 GB admit about 140 sessions, whose
+# 10-30 Hz scans offer about 2.7k scans/s; 220 GB admit enough sessions to keep the GPU busy
+SERVE_C1_BUDGET = 220e9
 
 
 def _batch_sets(n_maps: int = BATCH_MAPS):
@@ -189,10 +194,18 @@ def _serve_sets():
 
 
 def _capacity(params) -> int:
-    if params["voxels_per_block"] == 16:
-        return 2048
+    """Block pool of a batched map: a whole 40 m room holds about 10k blocks of 0.8 m; a LiDAR
+    terrain of up to 80 m, some 20k blocks of 1.6 m."""
     if params["voxel_size"] < 0.15:
         return 16384
+    return 1 << 16
+
+
+def _scratch(params) -> int:
+    """Blocks one scan of a batched map may enter (a 640x480 frame enters about a thousand
+    0.8 m blocks; a 64x2048 LiDAR scan, up to about 25k blocks of 1.6 m)."""
+    if params["voxel_size"] < 0.15:
+        return 8192
     return 1 << 15
 
 
@@ -202,11 +215,13 @@ def run_batched(args, vbx, torch, dev):
     sets = _batch_sets(args.batch_maps)
     pts = [[torch.from_numpy(p).to(dev) for p in s.points] for s in sets]
     maps = [
-        vbx.Map.from_scene_params(s.params, block_capacity=_capacity(s.params), max_points=max(p.shape[0] for p in s.points))
+        vbx.Map.from_scene_params(
+            s.params, block_capacity=_capacity(s.params), scratch_blocks=_scratch(s.params), max_points=max(p.shape[0] for p in s.points)
+        )
         for s in sets
     ]
     stream = torch.cuda.current_stream()
-    order = [k % BATCH_FRAMES for k in range(args.warmup + args.steps)]
+    order = [k % BATCH_FRAMES for k in range(args.warmup + args.steps)]  # distinct frames (warm-up + steps <= frames)
 
     def plain_step(f):
         for m, s, p in zip(maps, sets, pts):
@@ -273,7 +288,7 @@ def run_batched(args, vbx, torch, dev):
     return {
         "workload": f"{n} independent maps ({sum(s.name == 'room' for s in sets)} rooms 5-40 m with v in {{0.05, 0.1}} m and "
         f"160x120..640x480 RGB-D, {sum(s.name != 'room' for s in sets)} LiDAR terrains 40-80 m with v=0.2 m and 16x1024..64x2048 beams), "
-        "one scan per map per step, TSDF + ESDF",
+        f"one scan per map per step, TSDF + ESDF; every step integrates a new scan of each map ({BATCH_FRAMES} per map)",
         "value": n * args.steps / total_batch,
         "unit": "scans/s",
         "plain_value": n * args.steps / total_plain,
@@ -402,11 +417,12 @@ def _serve_c1_sets():
     return {"plane_sphere": [scenes.plane_sphere(seed=60 + i) for i in range(4)]}
 
 
-def _serve_once(serve, sets, arrivals: float, capacity, slots: int = SERVE_SLOTS, sessions: int = SERVE_SESSIONS, profile: bool = False):
+def _serve_once(serve, sets, arrivals: float, capacity, slots: int = SERVE_SLOTS, sessions: int = SERVE_SESSIONS, profile: bool = False,
+                budget: float = SERVE_BUDGET):
     pool = serve.ScanPool(sets, n_queries=N_QUERIES)
     scratch = serve.scratch_for_pool(pool, capacity)
     srv = serve.MapServer(
-        pool, slots=slots, hbm_budget=SERVE_BUDGET, capacity=capacity, use_graph=True, scratch=scratch, prealloc="fill"
+        pool, slots=slots, hbm_budget=budget, capacity=capacity, use_graph=True, scratch=scratch, prealloc="fill"
     )
     specs = serve.poisson_sessions(
         sessions,
@@ -446,11 +462,12 @@ def run_served(args, vbx, torch):
     sat["workload"] = f"as above, sessions arriving at {SERVE_SATURATED_ARRIVALS:.0f}/s (more scans offered than the GPU serves)"
     res["saturated"] = sat
     c1_sets = _serve_c1_sets()
-    c1 = _serve_once(serve, c1_sets, SERVE_C1_ARRIVALS, SERVE_C1_CAPACITY, slots=SERVE_C1_SLOTS, sessions=SERVE_C1_SESSIONS)
+    c1 = _serve_once(serve, c1_sets, SERVE_C1_ARRIVALS, SERVE_C1_CAPACITY, slots=SERVE_C1_SLOTS, sessions=SERVE_C1_SESSIONS,
+                     budget=SERVE_C1_BUDGET)
     c1["workload"] = (
         f"{SERVE_C1_SESSIONS} sessions of the plane+sphere scene (64x48 depth, v=0.1 m, 8^3 blocks) arriving at "
         f"{SERVE_C1_ARRIVALS:.0f}/s, 16 scans each at U(10,30) Hz, each scan followed by {N_QUERIES // 1000}k "
-        f"distance+gradient queries within 2 m of the sensor; {SERVE_C1_SLOTS} batch slots, {SERVE_BUDGET/1e9:.0f} GB map budget"
+        f"distance+gradient queries within 2 m of the sensor; {SERVE_C1_SLOTS} batch slots, {SERVE_C1_BUDGET/1e9:.0f} GB map budget"
     )
     c1["plain"] = _plain_plane_sphere(vbx, torch, c1_sets["plane_sphere"][0])
     res["plane_sphere"] = c1
@@ -572,7 +589,7 @@ def run_mesh(args, vbx, torch, dev, s, pts_dev, flush):
             "peak": peak,
             "unit": "GB/s",
             "frac": gbs / peak,
-            "traffic": _ncu_traffic("mesh_blocks"),
+            "traffic": _ncu_traffic("mesh_blocks", "room"),
             "bytes_per_launch": alg,
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6800 GB/s",
         },
@@ -831,10 +848,10 @@ def _alg_bytes(st, n_pts: int, B: int):
     }
 
 
-TSDF_KERNELS = ("bin_points", "group_rays", "link_blocks", "integrate_rays", "apply")
+TSDF_KERNELS = ("bin_points", "group_rays", "link_blocks", "scratch_links", "integrate_rays", "apply")
 
 
-def _roofline_entry(kernel, ms, launches, alg, peak, peaks):
+def _roofline_entry(kernel, ms, launches, alg, peak, peaks, workload="lidar"):
     per = ms / max(launches, 1)
     b = alg / max(launches, 1)
     ach = b / (per * 1e-3) / 1e9 if per > 0 else 0.0
@@ -845,14 +862,14 @@ def _roofline_entry(kernel, ms, launches, alg, peak, peaks):
         "peak": peak,
         "unit": "GB/s",
         "frac": ach / peak,
-        "traffic": _ncu_traffic(kernel),
+        "traffic": _ncu_traffic(kernel, workload),
         "bytes_per_launch": b,
         "ms_per_launch": per,
         "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6800 GB/s",
     }
 
 
-def run_plain(args, vbx, torch, dev, s, qs, map_kw, flush, dist=None, ws=1, local=0, headline=False):
+def run_plain(args, vbx, torch, dev, s, qs, map_kw, flush, dist=None, ws=1, local=0, headline=False, traffic_key="lidar"):
     """The plain per-scan path on one map: a timed pass (CUDA events around each step, L2
     flushed between steps outside the events), a per-kernel pass (the library's own events on
     the launching stream) for the roofline, and an end-to-end pass from pinned host buffers."""
@@ -963,14 +980,14 @@ def run_plain(args, vbx, torch, dev, s, qs, map_kw, flush, dist=None, ws=1, loca
     live = {k: v for k, v in kt.items() if v["launches"]}
     dom = max(live, key=lambda k: live[k]["ms"])
     kernels = {
-        k: _roofline_entry(k, live[k]["ms"], live[k]["launches"], alg[k], peak, peaks)
+        k: _roofline_entry(k, live[k]["ms"], live[k]["launches"], alg[k], peak, peaks, traffic_key)
         for k in ("integrate_rays", "apply", "esdf", "bin_points", "group_rays", "query")
         if k in live and k in alg
     }
     tsdf_ms = sum(live[k]["ms"] for k in TSDF_KERNELS if k in live)
-    kernels["tsdf_total"] = _roofline_entry("tsdf_total", tsdf_ms, args.steps, alg["tsdf_total"], peak, peaks)
+    kernels["tsdf_total"] = _roofline_entry("tsdf_total", tsdf_ms, args.steps, alg["tsdf_total"], peak, peaks, traffic_key)
     kernels["tsdf_total"]["kernels"] = list(TSDF_KERNELS)
-    roofline = dict(kernels[dom]) if dom in kernels else _roofline_entry(dom, live[dom]["ms"], live[dom]["launches"], 0, peak, peaks)
+    roofline = dict(kernels[dom]) if dom in kernels else _roofline_entry(dom, live[dom]["ms"], live[dom]["launches"], 0, peak, peaks, traffic_key)
     roofline["kernels"] = kernels
     roofline["kernels_ms_per_step"] = {k: v["ms"] / args.steps for k, v in live.items()}
 
@@ -1151,7 +1168,7 @@ def run_gpu(args):
         room_qs = _queries(s_room, 30)
         room_args = argparse.Namespace(**vars(args))
         room_args.steps, room_args.warmup = 30, 3
-        room = run_plain(room_args, vbx, torch, dev, s_room, room_qs, {}, flush)
+        room = run_plain(room_args, vbx, torch, dev, s_room, room_qs, {}, flush, traffic_key="room")
         room["workload"] = ROOM_WORKLOAD + "; 30 timed steps cycling the sequence after 3 warm-up frames"
 
     esdf_cmp = None

@@ -7,6 +7,9 @@ at the voxel centres, the evaluation the paper plots in Fig. 7:
   * occupancy      -- negative TSDF voxels are occupied at distance 0 (the occupancy ESDF)
   * half_band      -- fixed band |D| < delta / 2
   * one_voxel_band -- fixed band |D| < v (the method the paper recommends)
+  * half_band_euclidean, one_voxel_band_euclidean -- the same bands with full Euclidean
+    distances (each voxel keeps the offset to its site) instead of quasi-Euclidean ones; the
+    paper reports the error reduction and the time increase of this choice for the half band
 
 Errors are taken over observed free-space voxels whose true distance lies in (0, 1.5] m (below
 the ESDF's 2 m cap). Times are GPU times (CUDA events) summed over the scans.
@@ -19,13 +22,15 @@ import numpy as np
 
 from . import scenes, vbx
 
-METHODS = ("occupancy", "half_band", "one_voxel_band")
+METHODS = ("occupancy", "half_band", "half_band_euclidean", "one_voxel_band", "one_voxel_band_euclidean")
 EVAL_MAX_DIST = 1.5
 
 
 def method_options(method: str, params: Dict[str, float]) -> Dict[str, object]:
     if method == "occupancy":
         return dict(esdf_mode=1)
+    if method.endswith("_euclidean"):
+        return dict(method_options(method[: -len("_euclidean")], params), euclidean=True)
     if method == "half_band":
         return dict(fixed_band=0.5 * float(params["truncation"]))
     if method == "one_voxel_band":
@@ -99,4 +104,23 @@ def compare(scans: scenes.ScanSet, voxel_sizes=(0.05, 0.10, 0.20)) -> Dict[str, 
         for meth in METHODS:
             out.append(run(s, meth))
         out.append(run(s, "one_voxel_band", grouped=False))
-    return dict(results=out)
+    # full Euclidean against quasi-Euclidean distances, per band and voxel size: the ESDF error
+    # reduction and the ESDF time increase (Sec. VI-B reports both for the half band)
+    by = {(r["method"], r["voxel_size"], r["grouped"]): r for r in out}
+    euclid = []
+    for v in voxel_sizes:
+        vv = float(v)
+        for band in ("half_band", "one_voxel_band"):
+            q = by.get((band, vv, True))
+            e = by.get((band + "_euclidean", vv, True))
+            if q is None or e is None:
+                continue
+            euclid.append(
+                dict(
+                    band=band,
+                    voxel_size=vv,
+                    error_reduction_pct=100.0 * (q["esdf_mean_abs_err_m"] - e["esdf_mean_abs_err_m"]) / q["esdf_mean_abs_err_m"],
+                    esdf_time_increase_pct=100.0 * (e["esdf_ms_per_scan"] - q["esdf_ms_per_scan"]) / q["esdf_ms_per_scan"],
+                )
+            )
+    return dict(results=out, euclidean_vs_quasi=euclid)

@@ -163,7 +163,12 @@ class MapServer:
                 need = self.map_bytes(kind)
                 if self.used + need > self.budget:
                     break
-                m = self._new_map(kind)
+                try:
+                    m = self._new_map(kind)
+                except vbx.VbxError as e:  # the device has less free memory than the budget
+                    if e.status != 2:
+                        raise
+                    break
                 self.used += m.device_bytes()
                 self.peak = max(self.peak, self.used)
                 self.free[kind].append(m)
@@ -203,7 +208,12 @@ class MapServer:
                 m.close()
         if self.used + need > self.budget:
             return None
-        m = self._new_map(kind)
+        try:
+            m = self._new_map(kind)
+        except vbx.VbxError as e:  # out of device memory below the budget: the session waits
+            if e.status != 2:
+                raise
+            return None
         self.used += m.device_bytes()
         self.peak = max(self.peak, self.used)
         return m
@@ -262,6 +272,7 @@ class MapServer:
 
         gpu_ms = 0.0
         overlap_issues = 0  # steps issued while an earlier one was still on the GPU
+        host = dict(issue=0.0, wait=0.0, admit=0.0, loops=0)  # host seconds by activity
         t0 = time.perf_counter()
 
         def retire(block: bool):
@@ -273,11 +284,13 @@ class MapServer:
                         f["t_scan"] = now
                 f = in_flight[0]
                 if block:
+                    tw = time.perf_counter()
                     if f["t_scan"] is None:
                         f["e1"].synchronize()
                         f["t_scan"] = time.perf_counter() - t0
                     f["e2"].synchronize()
                     now = time.perf_counter() - t0
+                    host["wait"] += time.perf_counter() - tw
                 elif not f["e2"].query():
                     return
                 if f["t_scan"] is None:
@@ -303,6 +316,8 @@ class MapServer:
             if now > time_limit:
                 raise RuntimeError("serving run exceeded its time limit")
             retire(False)
+            host["loops"] += 1
+            ta = time.perf_counter()
             # admission: arrival order, a free slot and room in the memory budget
             while waiting and waiting[0].start <= now and free_slots:
                 spec = waiting[0]
@@ -318,6 +333,7 @@ class MapServer:
                 admitted += 1
             max_active = max(max_active, len(active))
             ready = [s for s, a in active.items() if a.arrivals[a.next] <= now]
+            host["admit"] += time.perf_counter() - ta
             if not ready or len(in_flight) >= max_in_flight:
                 if not ready and not in_flight:
                     nxt = [a.arrivals[a.next] for a in active.values()]
@@ -341,11 +357,13 @@ class MapServer:
             if in_flight:
                 overlap_issues += 1
             f = dict(e0=event(), e1=event(), e2=event(), scans=scans, t_scan=None, t_issue=time.perf_counter() - t0)
+            ti = time.perf_counter()
             f["e0"].record()
             self.batch.step(points, poses, flags=flags_map, slots=ready)
             f["e1"].record()
             self.batch.step(queries=queries, flags=flags_q, slots=ready)
             f["e2"].record()
+            host["issue"] += time.perf_counter() - ti
             in_flight.append(f)
             batch_sizes.append(len(ready))
             if profile_steps:
@@ -414,6 +432,8 @@ class MapServer:
             peak_map_bytes=self.peak,
             budget_bytes=self.budget,
             steps_issued_while_gpu_busy=overlap_issues,
+            host_ms_per_step={k: 1e3 * host[k] / max(len(batch_sizes), 1) for k in ("issue", "wait", "admit")},
+            loop_iterations=host["loops"],
             max_in_flight=max_in_flight,
             slow_step_kernels=_slow_step_kernels(step_kernels) if profile_steps else None,
         )
