@@ -158,9 +158,9 @@ SERVE_BUDGET = 120e9
 SERVE_CAPACITY = {"room": 2048, "lidar_terrain": 1 << 16}
 SERVE_ARRIVALS = 32.0  # sessions per second
 SERVE_SATURATED_ARRIVALS = 1024.0
-SERVE_C1_ARRIVALS = 256.0  # enough concurrent robots to offer more scans/s than the plain path serves
-SERVE_C1_SESSIONS = 768
-SERVE_C1_SLOTS = 256
+SERVE_C1_ARRIVALS = 512.0  # more robots arrive than the slots and budget admit: the server runs saturated
+SERVE_C1_SESSIONS = 1536
+SERVE_C1_SLOTS = 192  # about 3.8k scans/s offered: above the plain path, below the GPU's saturation
 SERVE_C1_CAPACITY = {"plane_sphere": 45056}  # the 10-frame circle allocates about 42.3k blocks of 8^3
 # a plane+sphere map of that capacity takes about 0.85 GB: 120 GB admit about 140 sessions, whose
 # 10-30 Hz scans offer about 2.7k scans/s; 220 GB admit enough sessions to keep the GPU busy

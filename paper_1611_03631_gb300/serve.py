@@ -226,7 +226,21 @@ class MapServer:
         self.free.clear()
 
     # -------------------------------------------------------------------------- run
-    def run(
+    def run(self, sessions: List[SessionSpec], **kw) -> Dict[str, object]:
+        """Serves `sessions` (see _serve for the keyword arguments). Python's cyclic garbage
+        collector is paused meanwhile: its collections stall the host loop for milliseconds,
+        which scans waiting for their step would see as latency."""
+        import gc
+
+        enabled = gc.isenabled()
+        gc.disable()
+        try:
+            return self._serve(sessions, **kw)
+        finally:
+            if enabled:
+                gc.enable()
+
+    def _serve(
         self,
         sessions: List[SessionSpec],
         seed: int = 7,
@@ -273,6 +287,8 @@ class MapServer:
         gpu_ms = 0.0
         overlap_issues = 0  # steps issued while an earlier one was still on the GPU
         host = dict(issue=0.0, wait=0.0, admit=0.0, loops=0)  # host seconds by activity
+        done_times = []  # host time at which each scan's step finished
+        sat = [None, None]  # first and last time a session that had arrived waited for admission
         t0 = time.perf_counter()
 
         def retire(block: bool):
@@ -301,6 +317,7 @@ class MapServer:
                 f["map_ms"] = f["e0"].elapsed_time(f["e1"])
                 scan_gpu_s = f["map_ms"] * 1e-3
                 for arrival, kind, first in f["scans"]:
+                    done_times.append(t_done)
                     lat_query.append(t_done - arrival)
                     lat_scan.append(f["t_scan"] - arrival)
                     scan_kind.append(kind)
@@ -332,6 +349,9 @@ class MapServer:
                 active[slot] = _Active(spec, m, arrivals)
                 admitted += 1
             max_active = max(max_active, len(active))
+            if waiting and waiting[0].start <= now:  # saturated: an arrived session waits for a slot or memory
+                sat[0] = now if sat[0] is None else sat[0]
+                sat[1] = now
             ready = [s for s, a in active.items() if a.arrivals[a.next] <= now]
             host["admit"] += time.perf_counter() - ta
             if not ready or len(in_flight) >= max_in_flight:
@@ -421,6 +441,12 @@ class MapServer:
             scans=n,
             wall_s=wall,
             scans_per_s=n / wall,
+            saturated_window_s=(sat[1] - sat[0]) if sat[0] is not None else 0.0,
+            saturated_scans_per_s=(
+                sum(1 for t in done_times if sat[0] <= t <= sat[1]) / (sat[1] - sat[0])
+                if sat[0] is not None and sat[1] - sat[0] > 0.5
+                else None
+            ),
             gpu_busy_frac=gpu_ms / 1e3 / wall,
             scans_per_gpu_s=n / (gpu_ms / 1e3),
             steps=len(batch_sizes),
