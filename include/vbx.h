@@ -286,8 +286,8 @@ vbx_status vbx_batch_create(const vbx_map_t* maps, int count, int64_t max_querie
 /* Rebinds slot `slot` to `map` (same device, not bound to another slot). Steps already issued keep
  * the map they were issued with; the next step takes the new one. The call synchronises the
  * device only when the map needs larger ESDF work lists or a larger block edge than the batch has
- * held so far (it reallocates them), so binding maps of the kinds already bound never stalls
- * steps in flight. */
+ * held so far (it reallocates them, at least doubling the lists), so binding maps of the kinds
+ * already bound never stalls steps in flight. */
 vbx_status vbx_batch_bind(vbx_batch_t batch, int slot, vbx_map_t map);
 
 /* One batched step on `stream`: scans[count] (VBX_STEP_INTEGRATE), ESDF update of every slot

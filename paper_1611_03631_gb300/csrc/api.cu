@@ -141,6 +141,9 @@ struct vbx_map_s {
   MapHook hook;
 
   vbx::LaunchCfg cfg(void* stream) const { return vbx::LaunchCfg{num_sms, (cudaStream_t)stream, vbx::kMapTuning}; }
+  // dirty voxels of the last ESDF update, copied back asynchronously after each update (pinned;
+  // read without waiting, so it may lag by an update): picks the next update's launch shape
+  unsigned* h_last_esdf_in = nullptr;
 
   std::vector<size_t> alloc_bytes;
 
@@ -166,6 +169,7 @@ struct vbx_map_s {
   }
   ~vbx_map_s() {
     for (void* p : allocs) cudaFree(p);
+    if (h_last_esdf_in) cudaFreeHost(h_last_esdf_in);
   }
 };
 
@@ -376,6 +380,12 @@ vbx_status vbx_create_map(float voxel_size, int voxels_per_block, float truncati
     delete m;
     return st;
   }
+  if ((e = cudaMallocHost((void**)&m->h_last_esdf_in, sizeof(unsigned))) != cudaSuccess) {
+    m->h_last_esdf_in = nullptr;
+    delete m;
+    return cuda_fail(e, "pinned update counter");
+  }
+  *m->h_last_esdf_in = 0u;
   if ((e = cudaMemcpy(m->d_dev, &m->d, sizeof(vbx::DevMap), cudaMemcpyHostToDevice)) != cudaSuccess) {
     delete m;
     return cuda_fail(e, "device map descriptor");
@@ -454,11 +464,16 @@ vbx_status vbx_update_esdf(vbx_map_t m, void* stream) {
   if (e != cudaSuccess) return cuda_fail(e, "reset esdf counters");
   e = cudaMemsetAsync(m->ctl_dev, 0, offsetof(vbx::EsdfCtl, cap), s);
   if (e != cudaSuccess) return cuda_fail(e, "reset esdf control");
-  if (m->opt.euclidean)
+  if (m->opt.euclidean) {
     e = vbx::launch_esdf_euclid(m->d_dev, m->B, m->ctl_dev, m->cfg(stream), &m->hook);
-  else  // one map: its rounds would hold about one tile per SM, so the waves run as work queues
-    e = vbx::launch_esdf(m->d_dev, 1, m->B, m->ctl_dev, m->cfg(stream), &m->hook, true);
+  } else {  // one map: its rounds would hold about one tile per SM, so the waves run as work queues
+    vbx::LaunchCfg cfg = m->cfg(stream);
+    if (*(volatile unsigned*)m->h_last_esdf_in >= vbx::kMapLargeUpdate) cfg.tune = vbx::kMapTuningLarge;
+    e = vbx::launch_esdf(m->d_dev, 1, m->B, m->ctl_dev, cfg, &m->hook, true);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "esdf cooperative launch");
+  e = cudaMemcpyAsync(m->h_last_esdf_in, &m->d.ctr->esdf_in, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_fail(e, "esdf update count");
   return VBX_OK;
 }
 
@@ -1008,9 +1023,11 @@ vbx_status vbx_batch_bind(vbx_batch_t b, int slot, vbx_map_t map) {
     vbx::EsdfCtl ctl{};
     if ((e = cudaMemcpy(&ctl, b->ctl_dev, sizeof(ctl), cudaMemcpyDeviceToHost)) != cudaSuccess)
       return cuda_fail(e, "esdf control");
-    const uint64_t ring = lower_ring_slots(cap_sum, b->num_sms);
-    const size_t bytes[6] = {cap_sum * sizeof(uint2), cap_sum * sizeof(uint2), cap_sum * sizeof(uint2),
-                             cap_sum * sizeof(uint2), ring * sizeof(uint2),    ring * sizeof(unsigned long long)};
+    // grow geometrically: a server binding maps one by one reallocates a few times, not per map
+    const uint64_t cap = std::min<uint64_t>(std::max<uint64_t>(cap_sum, 2 * b->ctl_cap), UINT32_MAX);
+    const uint64_t ring = lower_ring_slots(cap, b->num_sms);
+    const size_t bytes[6] = {cap * sizeof(uint2), cap * sizeof(uint2), cap * sizeof(uint2),
+                             cap * sizeof(uint2), ring * sizeof(uint2), ring * sizeof(unsigned long long)};
     void* lists[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     for (int i = 0; i < 6; ++i) {
       if ((e = cudaMalloc(&lists[i], bytes[i])) != cudaSuccess ||
@@ -1027,7 +1044,7 @@ vbx_status vbx_batch_bind(vbx_batch_t b, int slot, vbx_map_t map) {
     ctl.lring = (uint2*)lists[4];
     ctl.ltag = (unsigned long long*)lists[5];
     ctl.rcap = (unsigned)std::min<uint64_t>(ring, UINT32_MAX);
-    ctl.cap = (unsigned)std::min<uint64_t>(cap_sum, UINT32_MAX);
+    ctl.cap = (unsigned)cap;
     if ((e = cudaMemcpy(b->ctl_dev, &ctl, sizeof(ctl), cudaMemcpyHostToDevice)) != cudaSuccess)
       return cuda_fail(e, "esdf control");
     b->ctl_cap = ctl.cap;

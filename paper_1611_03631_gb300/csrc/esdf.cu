@@ -462,7 +462,9 @@ __device__ void raise_tile(const DevMap& m, uint32_t item, uint32_t* cur_bits, c
     }
     for (int j = threadIdx.x; j < (G::S3 + 31) / 32; j += NT)
       t.in[((it + 1) & 1) * (G::S3 / 32 > 0 ? G::S3 / 32 : 1) + j] = 0u;
-    // reset the raised voxels first, so that no child test below sees a stale parent
+    // reset the raised voxels; no barrier before the child tests below: a test that still sees
+    // the old parent of a voxel raised in this same iteration raises it once more, and one that
+    // sees it reset seeds it into the lower wave, which only costs a pop
     for (unsigned i = threadIdx.x; i < na; i += NT) {
       const int c = cur[i];
       const unsigned long long w = t.w[c];
@@ -472,7 +474,6 @@ __device__ void raise_tile(const DevMap& m, uint32_t item, uint32_t* cur_bits, c
         atomicOr(&t.chg[c >> 5], 1u << (c & 31));
       }
     }
-    __syncthreads();
     for (unsigned p = threadIdx.x; p < na * 26u; p += NT) {
       const unsigned i = p / 26u;
       const int kk = (int)(p - i * 26u);
@@ -661,16 +662,11 @@ __device__ __forceinline__ unsigned upper_index(const unsigned* pfx, int n, unsi
   return (unsigned)lo;
 }
 
-// 256- and 128-thread CTAs (batches) are held to 6 and 12 per SM worth of registers: more tiles
-// in flight per SM outweigh the few spilled registers
-#ifndef VBX_ESDF_MINB_256
-#define VBX_ESDF_MINB_256 6
-#endif
-#ifndef VBX_ESDF_MINB_128
-#define VBX_ESDF_MINB_128 12
-#endif
-template <int NT>
-__global__ void __launch_bounds__(NT, NT == 256 ? VBX_ESDF_MINB_256 : (NT == 128 ? VBX_ESDF_MINB_128 : (NT == 512 ? 2 : 1))) k_esdf(const DevMap* __restrict__ maps, int nmaps, EsdfCtl* ctl, int allow_async) {
+// NT threads per CTA, at least MINB CTAs per SM worth of registers: the 128- and 256-thread
+// batch shapes are held to 12 and 6 per SM (more tiles in flight per SM outweigh a few spilled
+// registers); 256 x 4 (64 registers) serves single maps with large updates.
+template <int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_esdf(const DevMap* __restrict__ maps, int nmaps, EsdfCtl* ctl, int allow_async) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ unsigned pfx[kMaxBatch + 1];
   __shared__ unsigned long long cta_pops;
@@ -1307,12 +1303,12 @@ size_t esdf_smem_bytes(int max_B) { return tile_bytes(max_B < kTileEdge ? max_B 
 
 namespace {
 
-const void* esdf_kernel(int threads) {
+const void* esdf_kernel(int threads, int ctas_per_sm) {
   switch (threads) {
-    case 128: return (const void*)k_esdf<128>;
-    case 256: return (const void*)k_esdf<256>;
-    case 512: return (const void*)k_esdf<512>;
-    case 1024: return (const void*)k_esdf<1024>;
+    case 128: return (const void*)k_esdf<128, 12>;
+    case 256: return ctas_per_sm > 0 && ctas_per_sm <= 4 ? (const void*)k_esdf<256, 4> : (const void*)k_esdf<256, 6>;
+    case 512: return (const void*)k_esdf<512, 2>;
+    case 1024: return (const void*)k_esdf<1024, 1>;
     default: return nullptr;
   }
 }
@@ -1320,7 +1316,7 @@ const void* esdf_kernel(int threads) {
 }  // namespace
 
 int esdf_grid(int num_sms, int max_B, int ctas_per_sm, int threads) {
-  const void* k = esdf_kernel(threads);
+  const void* k = esdf_kernel(threads, ctas_per_sm);
   if (!k) return 0;
   const size_t smem = esdf_smem_bytes(max_B);
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
@@ -1334,7 +1330,7 @@ cudaError_t launch_esdf(const DevMap* maps_dev, int nmaps, int max_B, EsdfCtl* c
                         LaunchHook* hook, bool allow_async) {
   if (nmaps <= 0 || nmaps > kMaxBatch) return cudaErrorInvalidValue;
   const int threads = cfg.tune.esdf_threads;
-  const void* k = esdf_kernel(threads);
+  const void* k = esdf_kernel(threads, cfg.tune.esdf_ctas_per_sm);
   if (!k) return cudaErrorInvalidValue;
   const int grid = esdf_grid(cfg.num_sms, max_B, cfg.tune.esdf_ctas_per_sm, threads);
   if (grid <= 0) return cudaErrorCooperativeLaunchTooLarge;

@@ -46,8 +46,16 @@ constexpr unsigned kFull = 0xffffffffu;
 #ifndef VBX_SEG_FILL
 #define VBX_SEG_FILL 64
 #endif
+// The voxel walk keeps about 106 registers live. A single map's rays are cut into segments
+// spread over the lanes: there 2 CTAs per SM without spills beat 4 CTAs per SM at 64 registers
+// (about 150 B of spills per thread) by 12 % on the LiDAR sequence. A large batch's rays are
+// walked whole, one per lane, and more warps in flight win: 4 CTAs per SM (3.1 against 3.9 ms
+// on the 64-map mix).
 #ifndef VBX_RAYS_MIN_CTAS
-#define VBX_RAYS_MIN_CTAS 4
+#define VBX_RAYS_MIN_CTAS 2
+#endif
+#ifndef VBX_RAYS_MIN_CTAS_BATCH
+#define VBX_RAYS_MIN_CTAS_BATCH 4
 #endif
 constexpr int kVoxSeg = VBX_VOX_SEG;
 constexpr int kBlkSeg = 4;
@@ -540,7 +548,8 @@ __device__ __forceinline__ uint32_t scratch_of(const DevMap& m, uint32_t slot, u
   return (unsigned)(w >> 32) == ep ? (uint32_t)w : kInvalid;
 }
 
-__global__ void __launch_bounds__(kThreads, VBX_RAYS_MIN_CTAS) k_integrate_rays(Batch b, unsigned warp_slots) {
+template <int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) k_integrate_rays(Batch b, unsigned warp_slots) {
   __shared__ unsigned pfx[kMaxBatch + 1];
   __shared__ long long sh_v[4][kWarps][32];
   __shared__ long long sh_se[kWarps][32][6];  // each lane's ray ends S, E (fixed point)
@@ -1011,15 +1020,18 @@ cudaError_t launch_integrate(const Batch& b, const LaunchCfg& cfg, LaunchHook* h
   const int gpts = b.maps ? cfg.num_sms * bin_per_sm : grid_for(b.one_scan.n, cfg.num_sms, bin_per_sm);
   // the ray kernels run a grid of at most their resident CTAs over all SMs and cut the rays
   // into warp tasks sized for that many warps
-  static int occ_group = 0, occ_rays = 0;
+  static int occ_group = 0, occ_rays = 0, occ_rays_b = 0;
   if (!occ_group) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_group, k_group_rays, kThreads, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_rays, k_integrate_rays, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_rays, k_integrate_rays<VBX_RAYS_MIN_CTAS>, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_rays_b, k_integrate_rays<VBX_RAYS_MIN_CTAS_BATCH>, kThreads, 0);
     if (occ_group < 1) occ_group = 1;
     if (occ_rays < 1) occ_rays = 1;
+    if (occ_rays_b < 1) occ_rays_b = 1;
   }
+  const bool batched = b.maps != nullptr;
   const int ggroup = cfg.num_sms * std::min(occ_group, cfg.tune.bin_ctas_per_sm);
-  const int grays = cfg.num_sms * std::min(occ_rays, cfg.tune.rays_ctas_per_sm);
+  const int grays = cfg.num_sms * std::min(batched ? occ_rays_b : occ_rays, cfg.tune.rays_ctas_per_sm);
   hook->begin(kKBin, s);
   k_bin_points<<<gpts, kThreads, 0, s>>>(b);
   hook->end(kKBin, s);
@@ -1033,7 +1045,10 @@ cudaError_t launch_integrate(const Batch& b, const LaunchCfg& cfg, LaunchHook* h
   k_scratch_links<<<cfg.num_sms * 4, kThreads, 0, s>>>(b);
   hook->end(kKScratchLinks, s);
   hook->begin(kKIntegrateRays, s);
-  k_integrate_rays<<<grays, kThreads, 0, s>>>(b, (unsigned)(grays * kWarps));
+  if (batched)
+    k_integrate_rays<VBX_RAYS_MIN_CTAS_BATCH><<<grays, kThreads, 0, s>>>(b, (unsigned)(grays * kWarps));
+  else
+    k_integrate_rays<VBX_RAYS_MIN_CTAS><<<grays, kThreads, 0, s>>>(b, (unsigned)(grays * kWarps));
   hook->end(kKIntegrateRays, s);
   hook->begin(kKApply, s);
   static int occ_apply = 0;

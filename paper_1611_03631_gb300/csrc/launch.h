@@ -53,9 +53,12 @@ struct Tuning {
 };
 // Start point of the batch autotuner (the ESDF grid is clamped to the kernel's occupancy).
 constexpr Tuning kDefaultTuning = {16, 16, 16, 8, 256};
-// Calls on one map: the ESDF waves run as work queues, and a wave advances as fast as a tile's
-// local relaxation (wide CTAs shorten it) while several tiles along its front are in flight
-// (more CTAs); on the room sequence 512 x 2 per SM beat 1024 x 1 and 256 x 4.
+// Calls on one map: the ESDF waves run as work queues. A wave advances as fast as a tile's local
+// relaxation (wide CTAs shorten it) while several tiles along its front are in flight (more
+// CTAs): updates of a few hundred thousand voxels (a room frame) are paced by the wave's
+// critical path and run best as 512 x 2 per SM; updates of millions of voxels (a LiDAR scan)
+// have tiles to spare and run best as 256 x 4 (ESDF 2.40 -> 1.83 ms on the LiDAR sequence, room
+// 0.343 -> 0.444 ms the other way round).
 #ifndef VBX_MAP_ESDF_THREADS
 #define VBX_MAP_ESDF_THREADS 512
 #endif
@@ -63,6 +66,10 @@ constexpr Tuning kDefaultTuning = {16, 16, 16, 8, 256};
 #define VBX_MAP_ESDF_CTAS 2
 #endif
 constexpr Tuning kMapTuning = {16, 16, 16, VBX_MAP_ESDF_CTAS, VBX_MAP_ESDF_THREADS};
+constexpr Tuning kMapTuningLarge = {16, 16, 16, 4, 256};
+// Dirty voxels at or above which a map's update uses kMapTuningLarge (the previous update's
+// count is the predictor: consecutive scans of a sequence update similar amounts).
+constexpr unsigned kMapLargeUpdate = 1u << 19;
 
 struct LaunchCfg {
   int num_sms;

@@ -172,6 +172,14 @@ class MapServer:
                 self.used += m.device_bytes()
                 self.peak = max(self.peak, self.used)
                 self.free[kind].append(m)
+        # the batch's ESDF work lists are sized by the maps bound to it: bind the warm maps (the
+        # largest first) to the slots once now, so that admissions during the run do not have to
+        # grow them (growing them synchronises the device)
+        spare = sorted((m for ms in self.free.values() for m in ms), key=lambda m: -m.device_bytes())[:slots]
+        for slot, m in enumerate(spare):
+            self.batch.bind(slot, m)
+        for slot in range(len(spare)):
+            self.batch.bind(slot, self.idle[slot])
         q = pool.n_queries
         self.out = [
             (
