@@ -1147,6 +1147,13 @@ def run_gpu(args):
     from paper_1611_03631_gb300 import vbx
 
     dev = torch.device("cuda", local)
+    if args.only_room:
+        flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        s_room = _scene(30)
+        room_args = argparse.Namespace(**vars(args))
+        room_args.steps, room_args.warmup = min(args.steps, 30), 3
+        print(json.dumps({"room": run_plain(room_args, vbx, torch, dev, s_room, _queries(s_room, 30), {}, flush, traffic_key="room")}), flush=True)
+        return 0
     if args.only_batched:
         print(json.dumps({"batched": run_batched(args, vbx, torch, dev)}), flush=True)
         return 0
@@ -1267,6 +1274,7 @@ def main():
     )
     ap.add_argument("--batch-maps", type=int, default=64, help="maps of the batched section")
     ap.add_argument("--only-batched", action="store_true", help="run the batched section alone (profiling)")
+    ap.add_argument("--only-room", action="store_true", help="run the room RGB-D section alone, at most --steps steps (profiling)")
     ap.add_argument(
         "--only-batched-plane-sphere", action="store_true", help="run the batched plane+sphere section alone with --batch-maps maps (profiling)"
     )

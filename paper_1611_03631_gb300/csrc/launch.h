@@ -57,8 +57,8 @@ constexpr Tuning kDefaultTuning = {16, 16, 16, 8, 256};
 // relaxation (wide CTAs shorten it) while several tiles along its front are in flight (more
 // CTAs): updates of a few hundred thousand voxels (a room frame) are paced by the wave's
 // critical path and run best as 512 x 2 per SM; updates of millions of voxels (a LiDAR scan)
-// have tiles to spare and run best as 256 x 4 (ESDF 2.40 -> 1.83 ms on the LiDAR sequence, room
-// 0.343 -> 0.444 ms the other way round).
+// have tiles to spare, and every extra CTA per SM helps them (LiDAR ESDF 1.70 ms at 512 x 3,
+// 1.54 at 256 x 4, 1.36 at 256 x 6, 1.30 at 256 x 8; room 0.31 ms at 512 x 2, 0.46 at 256 x 6).
 #ifndef VBX_MAP_ESDF_THREADS
 #define VBX_MAP_ESDF_THREADS 512
 #endif
@@ -66,7 +66,13 @@ constexpr Tuning kDefaultTuning = {16, 16, 16, 8, 256};
 #define VBX_MAP_ESDF_CTAS 2
 #endif
 constexpr Tuning kMapTuning = {16, 16, 16, VBX_MAP_ESDF_CTAS, VBX_MAP_ESDF_THREADS};
-constexpr Tuning kMapTuningLarge = {16, 16, 16, 4, 256};
+#ifndef VBX_MAP_LARGE_THREADS
+#define VBX_MAP_LARGE_THREADS 256
+#endif
+#ifndef VBX_MAP_LARGE_CTAS
+#define VBX_MAP_LARGE_CTAS 8
+#endif
+constexpr Tuning kMapTuningLarge = {16, 16, 16, VBX_MAP_LARGE_CTAS, VBX_MAP_LARGE_THREADS};
 // Dirty voxels at or above which a map's update uses kMapTuningLarge (the previous update's
 // count is the predictor: consecutive scans of a sequence update similar amounts).
 constexpr unsigned kMapLargeUpdate = 1u << 19;
@@ -123,7 +129,8 @@ cudaError_t launch_reset_map(const DevMap& m, const LaunchCfg& cfg);
 
 // esdf.cu: one cooperative launch updates the ESDF of nmaps maps (device array of DevMap)
 size_t esdf_smem_bytes(int max_B);
-int esdf_grid(int num_sms, int max_B, int ctas_per_sm, int threads);
+// be: the block edge of a single map whose waves run as work queues (0: the batch kernel)
+int esdf_grid(int num_sms, int max_B, int ctas_per_sm, int threads, int be = 0);
 // allow_async: the raise and lower waves may run as asynchronous work queues instead of rounds
 // (the kernel takes them when few maps of the launch have work)
 // Full Euclidean ESDF update of one map (the map's device descriptor, block edge B).
