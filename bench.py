@@ -56,13 +56,20 @@ FLUSH_BYTES = 256 << 20  # > 129 MB L2
 # them changes the entry no longer matches and the reported traffic is null.
 NCU_TRAFFIC = {
     # LiDAR growth scan 3 (bench.py --only-headline --no-cpu-baseline --steps 3 --warmup 3):
-    # dram__bytes.sum.per_second x gpu__time_duration.sum of one launch each
-    # k_integrate_rays: 0.186846 TB/s x 0.486176 ms
-    ("integrate_rays", "lidar", "integrate.cu", "acd45f923c02b257"): 90840000,
-    # k_apply: 2.624806 TB/s x 0.050208 ms
-    ("apply", "lidar", "integrate.cu", "acd45f923c02b257"): 131790000,
-    # k_esdf<512> x 2 per SM: 0.045752 TB/s x 1.743040 ms
-    ("esdf", "lidar", "esdf.cu", "44d12481f39866bc"): 79750000,
+    # dram__bytes_read.sum + dram__bytes_write.sum of one launch each
+    # k_integrate_rays<2>: 61.354752 MB + 13.538304 MB
+    ("integrate_rays", "lidar", "integrate.cu", "25e4467e02c17ebb"): 74893056,
+    # k_apply: 94.037760 MB + 34.214144 MB
+    ("apply", "lidar", "integrate.cu", "25e4467e02c17ebb"): 128251904,
+    # k_esdf<256, 8, 8>: 74.117888 MB + 3.999232 MB
+    ("esdf", "lidar", "esdf.cu", "aa0489d1a59c13fa"): 78117120,
+    # room frame 3 (bench.py --only-room --no-cpu-baseline --steps 3 --warmup 3)
+    # k_integrate_rays<2>: 1.528320 MB + 3.328 kB
+    ("integrate_rays", "room", "integrate.cu", "25e4467e02c17ebb"): 1531648,
+    # k_apply: 2.209024 MB + 0
+    ("apply", "room", "integrate.cu", "25e4467e02c17ebb"): 2209024,
+    # k_esdf<512, 2, 0>: 2.343680 MB + 31.232 kB
+    ("esdf", "room", "esdf.cu", "aa0489d1a59c13fa"): 2374912,
     # k_mesh_blocks<16>, full mesh of the room map (dram__bytes_read.sum 25,988,096 + write 2,304;
     # the 17 MB of triangles it writes are still in L2 when it ends)
     ("mesh_blocks", "room", "mesh.cu", "cbd5b0c8554fc2d5"): 25990400,
