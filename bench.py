@@ -862,6 +862,7 @@ def _roofline_entry(kernel, ms, launches, alg, peak, peaks, workload="lidar"):
     per = ms / max(launches, 1)
     b = alg / max(launches, 1)
     ach = b / (per * 1e-3) / 1e9 if per > 0 else 0.0
+    traffic = _ncu_traffic(kernel, workload)
     return {
         "bound": "hbm",
         "kernel": kernel,
@@ -869,7 +870,10 @@ def _roofline_entry(kernel, ms, launches, alg, peak, peaks, workload="lidar"):
         "peak": peak,
         "unit": "GB/s",
         "frac": ach / peak,
-        "traffic": _ncu_traffic(kernel, workload),
+        "traffic": traffic,
+        # the DRAM rate those captured bytes imply at this run's launch time (implementation
+        # bytes, not algorithmic ones)
+        "traffic_gbs": traffic / (per * 1e-3) / 1e9 if traffic and per > 0 else None,
         "bytes_per_launch": b,
         "ms_per_launch": per,
         "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6800 GB/s",

@@ -347,6 +347,7 @@ vbx_status vbx_create_map(float voxel_size, int voxels_per_block, float truncati
   VBX_ALLOC(d.rbits1, V / 32, 0);
   VBX_ALLOC(d.lbits0, V / 32, 0);
   VBX_ALLOC(d.lbits1, V / 32, 0);
+  VBX_ALLOC(d.pbits, V / 32, 0);
   const size_t items = (size_t)cap << d.tile_shift;  // ESDF tiles
   VBX_ALLOC(d.bstamp_r, items, 0);
   VBX_ALLOC(d.bstamp_l, items, 0);
@@ -1198,7 +1199,7 @@ vbx_status vbx_map_bytes(int B, const vbx_map_options* opt_in, int64_t* out) {
                                                           // mesh marks and list
   bytes += V * (8 + 8 + 1 + 4 + 4);                       // tsdf, esdf, flags, updated and dirty lists
   bytes += scr * (4 + 4 + 27 * 4) + scr * B3 * (32 + 1);  // scratch blocks: lists, neighbour links, sums, touch flags
-  bytes += 4 * (V / 32) * 4;                              // frontier bitmasks
+  bytes += 5 * (V / 32) * 4;                              // frontier and pull bitmasks
   bytes += tiles * (2 * 4 + 4 * 8);                       // tile stamps, active lists
   {
     int dev = 0, sms = 152;  // lower-wave queue ring (this device's SM count, else 152)

@@ -276,7 +276,8 @@ __device__ __forceinline__ int coords_tile_dir(int x, int y, int z) {
 // memory, appended to the active list), then its words with the one-voxel halo (one tile row of
 // T words per thread, the S interior words of a row read as 16-byte vectors).
 template <int NT, int B, int S>
-__device__ void stage_tile(const DevMap& m, const TileRef& r, uint32_t* cur_bits, const Tile& t, bool ordered) {
+__device__ void stage_tile(const DevMap& m, const TileRef& r, uint32_t* cur_bits, const Tile& t, bool ordered,
+                           bool pull = false) {
   using G = Geo<B, S>;
   if (threadIdx.x < 27) {
     const int k = threadIdx.x;
@@ -291,6 +292,10 @@ __device__ void stage_tile(const DevMap& m, const TileRef& r, uint32_t* cur_bits
   }
   for (int i = threadIdx.x; i < (2 * G::S3 + 31) / 32; i += NT) t.in[i] = 0u;
   __syncthreads();
+  // with `pull` (lower wave): the first list is also recorded in the second half of t.in, and
+  // the tile's pull marks are taken into a list in t.b (t.cnt[5] entries), which is free until
+  // the first local iteration fills it
+  uint32_t* first = t.in + (G::S3 / 32 > 0 ? G::S3 / 32 : 1);
   auto take_bits = [&]() {
     // frontier bits: tile row (z, y) = S consecutive bits of the block bitmap, inside one word
     for (int row = threadIdx.x; row < S * S; row += NT) {
@@ -298,14 +303,28 @@ __device__ void stage_tile(const DevMap& m, const TileRef& r, uint32_t* cur_bits
       const uint32_t base = (r.slot << (3 * G::LOGB)) + (uint32_t)((((r.oz + z) << G::LOGB) | (r.oy + y)) << G::LOGB) + r.ox;
       uint32_t* wp = &cur_bits[base >> 5];
       const uint32_t mask = ((1u << S) - 1u) << (base & 31);
-      if (!(__ldcg(wp) & mask)) continue;
-      uint32_t chunk = (atomicAnd(wp, ~mask) & mask) >> (base & 31);
-      const unsigned at = atomicAdd(&t.cnt[0], (unsigned)__popc(chunk));
-      unsigned i = at;
-      while (chunk) {
-        const int x = __ffs(chunk) - 1;
-        chunk &= chunk - 1;
-        t.a[i++] = (uint16_t)G::cell_of_local((((z << G::LOGS) | y) << G::LOGS) | x);
+      const uint32_t fw = __ldcg(wp);
+      const uint32_t pw = pull ? __ldcg(&m.pbits[base >> 5]) : 0u;
+      if (fw & mask) {
+        uint32_t chunk = (atomicAnd(wp, ~mask) & mask) >> (base & 31);
+        const unsigned at = atomicAdd(&t.cnt[0], (unsigned)__popc(chunk));
+        unsigned i = at;
+        while (chunk) {
+          const int x = __ffs(chunk) - 1;
+          chunk &= chunk - 1;
+          const int nl = (((z << G::LOGS) | y) << G::LOGS) | x;
+          t.a[i++] = (uint16_t)G::cell_of_local(nl);
+          if (pull) atomicOr(&first[nl >> 5], 1u << (nl & 31));
+        }
+      }
+      if (pw & mask) {
+        uint32_t chunk = (atomicAnd(&m.pbits[base >> 5], ~mask) & mask) >> (base & 31);
+        unsigned i = atomicAdd(&t.cnt[5], (unsigned)__popc(chunk));
+        while (chunk) {
+          const int x = __ffs(chunk) - 1;
+          chunk &= chunk - 1;
+          t.b[i++] = (uint16_t)G::cell_of_local((((z << G::LOGS) | y) << G::LOGS) | x);
+        }
       }
     }
   };
@@ -524,9 +543,11 @@ __device__ void raise_tile(const DevMap& m, uint32_t item, uint32_t* cur_bits, c
     if (threadIdx.x == 0) t.cnt[(it + 2) % 3] = 0u;
     for (int j = threadIdx.x; j < (G::S3 + 31) / 32; j += NT)
       t.in[((it + 1) & 1) * (G::S3 / 32 > 0 ? G::S3 / 32 : 1) + j] = 0u;
-    // reset the raised voxels; no barrier before the child tests below: a test that still sees
-    // the old parent of a voxel raised in this same iteration raises it once more, and one that
-    // sees it reset seeds it into the lower wave, which only costs a pop
+    // reset the raised voxels; each joins the lower frontier itself and takes its new value from
+    // its neighbours when the lower wave stages its tile (its other observed neighbours, whose
+    // values stand, would otherwise all be popped to offer it theirs). No barrier before the
+    // child tests below: a test that still sees the old parent of a voxel raised in this same
+    // iteration raises it once more, which only costs a pop.
     for (unsigned i = threadIdx.x; i < na; i += NT) {
       const int c = cur[i];
       const unsigned long long w = t.w[c];
@@ -534,6 +555,7 @@ __device__ void raise_tile(const DevMap& m, uint32_t item, uint32_t* cur_bits, c
       if (!(fl & kFixed)) {
         t.w[c] = ew_pack(ew_d(w) < 0.0f ? -dmax : dmax, fl, kNoParent);
         atomicOr(&t.chg[c >> 5], 1u << (c & 31));
+        atomicOr(&t.lseed[c >> 5], 1u << (c & 31));
       }
     }
     for (unsigned p = threadIdx.x; p < na * 26u; p += NT) {
@@ -554,10 +576,6 @@ __device__ void raise_tile(const DevMap& m, uint32_t item, uint32_t* cur_bits, c
           set_bit(ra.nxt_bits, cell_vid<B, S>(t, r, nc));
           atomicOr(&t.cnt[3], 1u << cell_tile_dir<B, S>(nc));
         }
-      } else if (__fadd_rn(fabsf(ew_d(nw)), m.L1) < dmax) {
-        // any other observed neighbour that can lower a voxel re-seeds the lower wave (marked
-        // once per cell below)
-        atomicOr(&t.lseed[nc >> 5], 1u << (nc & 31));
       }
     }
     __syncthreads();
@@ -569,12 +587,14 @@ __device__ void raise_tile(const DevMap& m, uint32_t item, uint32_t* cur_bits, c
   }
   unsigned ahead = 0;  // the CTA's next ticket
   if (ra.q && threadIdx.x == kAheadThread) ahead = atomicAdd(&ra.q->ctl->qhead, 1u);
-  // write back the raised voxels (raise rounds never lower words, plain stores suffice), and
-  // the lower-wave seeds
+  // write back the raised voxels (raise rounds never lower words, plain stores suffice); each
+  // joins the lower frontier and pulls
   for (int c = threadIdx.x; c < G::T3; c += NT) {
     if (t.chg[c >> 5] & (1u << (c & 31))) m.esdf[cell_vid<B, S>(t, r, c)] = t.w[c];
     if (t.lseed[c >> 5] & (1u << (c & 31))) {
-      set_bit(m.lbits0, cell_vid<B, S>(t, r, c));
+      const uint32_t vid = cell_vid<B, S>(t, r, c);
+      set_bit(m.pbits, vid);
+      set_bit(m.lbits0, vid);
       atomicOr(&t.cnt[4], 1u << cell_tile_dir<B, S>(c));
     }
   }
@@ -611,11 +631,46 @@ __device__ void lower_tile(const DevMap& m, uint32_t item, uint32_t* cur_bits, c
   using G = Geo<B, S>;
   const Tile t = carve(smem, S);
   const TileRef r = tile_ref<B, S>(item);
-  stage_tile<NT, B, S>(m, r, cur_bits, t, ra.q != nullptr);
+  stage_tile<NT, B, S>(m, r, cur_bits, t, ra.q != nullptr, true);
   const float L1 = m.L1, L2 = m.L2, L3 = m.L3;
   // a voxel lowered to |d| with |d| + v >= d_max cannot lower any neighbour (no value exceeds
   // d_max), so it is written back but not put on a frontier
   const float reach = m.dmax;
+  // Voxels marked to pull (raised, or newly observed; staging listed the marks it took in t.b)
+  // take the best offer of their observed same-sign neighbours: the least word {|d_n| + step,
+  // flags, direction}, the choice the atomicMin of pushes from all those neighbours would make.
+  // A mark is set with the voxel's frontier bit before the wave, so the staging that takes one
+  // normally takes the other; if the value drops and another visit took the frontier bit, this
+  // visit's first list gets the voxel too.
+  {
+    const uint32_t* first = t.in + (G::S3 / 32 > 0 ? G::S3 / 32 : 1);
+    for (unsigned i = threadIdx.x; i < t.cnt[5]; i += NT) {
+      {
+        const int c = t.b[i];
+        const unsigned long long w = t.w[c];
+        const unsigned fl = ew_flags(w);
+        const bool neg = ew_d(w) < 0.0f;
+        unsigned long long best = w;
+        for (int k = 0; k < 27; ++k) {
+          if (k == 13) continue;
+          const unsigned long long nw = t.w[c + t.doff[k]];
+          const float dn = ew_d(nw);
+          if (!(ew_flags(nw) & kObserved) || (dn < 0.0f) != neg) continue;
+          const int n1 = t.dcls[k];
+          const float cand = __fadd_rn(fabsf(dn), n1 == 1 ? L1 : (n1 == 2 ? L2 : L3));
+          const unsigned long long cw = ew_pack(neg ? -cand : cand, fl, (unsigned)k);
+          if (cw < best) best = cw;
+        }
+        if (best < w) {
+          atomicMin(&t.w[c], best);
+          atomicOr(&t.chg[c >> 5], 1u << (c & 31));
+          const int nl = interior_local<B, S>(c);
+          if (!(first[nl >> 5] & (1u << (nl & 31)))) smem_append(t.a, &t.cnt[0], (uint16_t)c);
+        }
+      }
+    }
+    __syncthreads();
+  }
   unsigned iters = 0;
   unsigned long long pops = 0;
   for (int it = 0;; ++it) {
@@ -861,27 +916,14 @@ __global__ void __launch_bounds__(NT, MINB) k_esdf(const DevMap* __restrict__ ma
       m.esdf[vid] = ew_pack(sdmax, kObserved, kNoParent);
       set_bit(m.rbits0, vid);
       activate(ctl->ract0, &ctl->rcnt[0], m.bstamp_r, slot, e0, mi);
-    } else if (!obs) {  // newly observed: its observed neighbours will lower it
+    } else if (!obs) {
+      // newly observed: it joins the lower frontier itself and takes its value from its
+      // neighbours when the lower wave stages its tile (one pull instead of a frontier entry for
+      // every neighbour that could lower it)
       m.esdf[vid] = ew_pack(sdmax, kObserved, kNoParent);
-      uint32_t last = kInvalid;
-      for (int k = 0; k < 27; ++k) {
-        if (k == 13) continue;
-        const uint32_t n = neighbor_vid(m, vid, k);
-        if (n == kInvalid) continue;
-        // only a neighbour whose value can lower this voxel (same sign, |d| + step < d_max) joins
-        // the frontier: a lower value that a neighbour takes later comes from seeding or from
-        // lowering, both of which put it on the frontier anyway
-        const unsigned long long nw = __ldcg(&m.esdf[n]);
-        const float dn = ew_d(nw);
-        const int n1 = (k / 9 != 1) + ((k / 3) % 3 != 1) + (k % 3 != 1);
-        if ((ew_flags(nw) & kObserved) && (dn < 0.0f) == neg &&
-            __fadd_rn(fabsf(dn), n1 == 1 ? m.L1 : (n1 == 2 ? m.L2 : m.L3)) < dmax) {
-          set_bit(m.lbits0, n);
-          const uint32_t nb = tile_item_of(m, n);
-          if (nb != last) activate(ctl->lact0, &ctl->lcnt[0], m.bstamp_l, nb, e0, mi);
-          last = nb;
-        }
-      }
+      set_bit(m.pbits, vid);
+      set_bit(m.lbits0, vid);
+      activate(ctl->lact0, &ctl->lcnt[0], m.bstamp_l, slot, e0, mi);
     } else if ((de < 0.0f) != neg) {  // sign flip of a propagated voxel
       m.esdf[vid] = ew_pack(sdmax, kObserved, kNoParent);
       set_bit(m.rbits0, vid);

@@ -933,6 +933,7 @@ __global__ void __launch_bounds__(kThreads) k_reset_map(DevMap m) {
     m.rbits1[i] = 0u;
     m.lbits0[i] = 0u;
     m.lbits1[i] = 0u;
+    m.pbits[i] = 0u;
   }
   for (size_t i = i0; i < SV; i += st) {
     m.stouch[i] = 0u;

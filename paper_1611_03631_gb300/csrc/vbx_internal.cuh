@@ -167,6 +167,10 @@ struct DevMap {
   uint32_t* rbits1;
   uint32_t* lbits0;
   uint32_t* lbits1;
+  // quasi-Euclidean ESDF update: voxels (raised, or newly observed) that take their value from
+  // their neighbours when the lower wave first stages their tile; each bit is set together with
+  // the voxel's lower-frontier bit and taken by that staging
+  uint32_t* pbits;
   uint32_t* bstamp_r;
   uint32_t* bstamp_l;
   // mesh: per block, whether its TSDF may have changed since the last extraction; the blocks
