@@ -57,19 +57,19 @@ FLUSH_BYTES = 256 << 20  # > 129 MB L2
 NCU_TRAFFIC = {
     # LiDAR growth scan 3 (bench.py --only-headline --no-cpu-baseline --steps 3 --warmup 3):
     # dram__bytes_read.sum + dram__bytes_write.sum of one launch each
-    # k_integrate_rays<2>: 61.354752 MB + 13.538304 MB
-    ("integrate_rays", "lidar", "integrate.cu", "25e4467e02c17ebb"): 74893056,
-    # k_apply: 94.037760 MB + 34.214144 MB
-    ("apply", "lidar", "integrate.cu", "25e4467e02c17ebb"): 128251904,
-    # k_esdf<256, 8, 8>: 74.117888 MB + 3.999232 MB
-    ("esdf", "lidar", "esdf.cu", "aa0489d1a59c13fa"): 78117120,
+    # k_integrate_rays<2>: 61.447424 MB + 13.539072 MB
+    ("integrate_rays", "lidar", "integrate.cu", "7121226917bc928b"): 74986496,
+    # k_apply: 94.034688 MB + 34.408960 MB
+    ("apply", "lidar", "integrate.cu", "7121226917bc928b"): 128443648,
+    # k_esdf<256, 8, 8>: 75.650304 MB + 3.010048 MB
+    ("esdf", "lidar", "esdf.cu", "cf93a790faeb4c3d"): 78660352,
     # room frame 3 (bench.py --only-room --no-cpu-baseline --steps 3 --warmup 3)
-    # k_integrate_rays<2>: 1.528320 MB + 3.328 kB
-    ("integrate_rays", "room", "integrate.cu", "25e4467e02c17ebb"): 1531648,
-    # k_apply: 2.209024 MB + 0
-    ("apply", "room", "integrate.cu", "25e4467e02c17ebb"): 2209024,
-    # k_esdf<512, 2, 0>: 2.343680 MB + 31.232 kB
-    ("esdf", "room", "esdf.cu", "aa0489d1a59c13fa"): 2374912,
+    # k_integrate_rays<2>: 1.531392 MB + 2.816 kB
+    ("integrate_rays", "room", "integrate.cu", "7121226917bc928b"): 1534208,
+    # k_apply: 2.208000 MB + 0
+    ("apply", "room", "integrate.cu", "7121226917bc928b"): 2208000,
+    # k_esdf<512, 2, 0>: 2.292736 MB + 28.416 kB
+    ("esdf", "room", "esdf.cu", "cf93a790faeb4c3d"): 2321152,
     # k_mesh_blocks<16>, full mesh of the room map (dram__bytes_read.sum 25,988,096 + write 2,304;
     # the 17 MB of triangles it writes are still in L2 when it ends)
     ("mesh_blocks", "room", "mesh.cu", "cbd5b0c8554fc2d5"): 25990400,
