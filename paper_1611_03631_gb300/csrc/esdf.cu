@@ -671,6 +671,21 @@ __device__ void lower_tile(const DevMap& m, uint32_t item, uint32_t* cur_bits, c
     }
     __syncthreads();
   }
+  // First-list voxels with |d| + v >= d_max cannot lower any neighbour (no value exceeds d_max):
+  // above all new or raised voxels inside a new or raised region, which found no offer. They
+  // leave the list (through t.b, free again) before their 26 neighbour checks.
+  {
+    for (unsigned i = threadIdx.x; i < t.cnt[0]; i += NT) {
+      const int c = t.a[i];
+      if (__fadd_rn(fabsf(ew_d(t.w[c])), L1) < reach) smem_append(t.b, &t.cnt[6], (uint16_t)c);
+    }
+    __syncthreads();
+    const unsigned n = t.cnt[6];
+    for (unsigned i = threadIdx.x; i < n; i += NT) t.a[i] = t.b[i];
+    __syncthreads();
+    if (threadIdx.x == 0) t.cnt[0] = n;
+    __syncthreads();
+  }
   unsigned iters = 0;
   unsigned long long pops = 0;
   for (int it = 0;; ++it) {
