@@ -686,6 +686,11 @@ __device__ void lower_tile(const DevMap& m, uint32_t item, uint32_t* cur_bits, c
     if (threadIdx.x == 0) t.cnt[0] = n;
     __syncthreads();
   }
+  // this lane's direction for the visit (lanes 26-31 take direction 0 and stay idle)
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int k = (lane < 13 ? lane : lane + 1) % 27;
+  const int dk = t.doff[k];
+  const float Lk = t.dcls[k] == 1 ? L1 : (t.dcls[k] == 2 ? L2 : L3);
   unsigned iters = 0;
   unsigned long long pops = 0;
   for (int it = 0;; ++it) {
@@ -704,23 +709,21 @@ __device__ void lower_tile(const DevMap& m, uint32_t item, uint32_t* cur_bits, c
     if (threadIdx.x == 0) t.cnt[(it + 2) % 3] = 0u;
     for (int j = threadIdx.x; j < (G::S3 + 31) / 32; j += NT)
       t.in[((it + 1) & 1) * (G::S3 / 32 > 0 ? G::S3 / 32 : 1) + j] = 0u;
-    for (unsigned p = threadIdx.x; p < na * 26u; p += NT) {
-      const unsigned i = p / 26u;
-      const int kk = (int)(p - i * 26u);
-      const int k = kk < 13 ? kk : kk + 1;
+    // one voxel per warp, one of its 26 directions per lane (lanes 26-31 idle): the voxel's word
+    // is one broadcast, and each lane's offset and step stay in registers for the whole visit
+    for (unsigned i = (unsigned)wid; i < na; i += NT / 32) {
       const int c = cur[i];
       const unsigned long long w = t.w[c];
-      if (!(ew_flags(w) & kObserved)) continue;
+      if (lane >= 26 || !(ew_flags(w) & kObserved)) continue;
       const float dv = ew_d(w);
       const bool neg = dv < 0.0f;
-      const int nc = c + t.doff[k];
+      const int nc = c + dk;
       const unsigned long long nw = t.w[nc];
       const unsigned nfl = ew_flags(nw);
       if ((nfl & (kObserved | kFixed)) != kObserved) continue;
       const float dn = ew_d(nw);
       if ((dn < 0.0f) != neg) continue;
-      const int n1 = t.dcls[k];
-      const float cand = __fadd_rn(fabsf(dv), n1 == 1 ? L1 : (n1 == 2 ? L2 : L3));
+      const float cand = __fadd_rn(fabsf(dv), Lk);
       if (!(cand < fabsf(dn))) continue;
       const unsigned long long old = atomicMin(&t.w[nc], ew_pack(neg ? -cand : cand, nfl, (unsigned)(26 - k)));
       if (!(fabsf(ew_d(old)) > cand)) continue;
