@@ -3,21 +3,24 @@
 //   A6 classify : every TSDF voxel updated since the last call takes one branch of the first
 //                 loop of Algorithm 1 (fixed band |D| < gamma, leaving the band, new voxel,
 //                 sign flip) and seeds the raise and lower frontiers
-//   A7 raise    : global rounds over active tiles (a block, or an 8^3 octant of a 16^3 block);
-//                 a CTA stages one tile and its one-voxel halo in shared memory and raises
-//                 within the tile until no child is left there: a raised non-fixed voxel is reset to +-d_max, neighbours whose parent
-//                 direction points back at it are raised next, all other observed neighbours
-//                 join the lower frontier; children in the halo are raised in the next round
-//   A8 lower    : global rounds over active tiles; the CTA relaxes the staged tile to local
-//                 convergence (observed, non-fixed, same-sign 26-neighbours, quasi-Euclidean
-//                 steps, 64-bit atomicMin on {distance bits, flags, parent} in shared memory),
-//                 then writes every changed voxel back with a global 64-bit atomicMin; halo
-//                 voxels that improved are pushed to their own tile for the next round
-// Frontiers are per-voxel bitmasks (current / next) plus lists of active (map, tile) pairs
-// de-duplicated per round with monotone epoch stamps. The paper processes the open set with a
-// priority queue or a FIFO; any processing order reaches the same fixpoint (after the raise
-// phase the lower wave computes the greatest fixpoint below the current values of a monotone
-// relaxation), so the block-staged rounds give the batch-recompute result.
+//   A7 raise    : active tiles (a block, or an 8^3 octant of a 16^3 block), in global rounds
+//                 or from a work queue; a CTA stages one tile and its one-voxel halo in shared
+//                 memory and raises within the tile until no child is left there: a raised
+//                 non-fixed voxel is reset to +-d_max, neighbours whose parent direction points
+//                 back at it are raised next, and the raised voxel itself joins the lower
+//                 frontier marked to pull; children in the halo go to their own tile
+//   A8 lower    : active tiles, likewise; a voxel marked to pull (raised, or newly observed)
+//                 first takes the best offer of its neighbours (what their pushes would give
+//                 it), then the CTA relaxes the staged tile to local convergence (observed,
+//                 non-fixed, same-sign 26-neighbours, quasi-Euclidean steps, 64-bit atomicMin
+//                 on {distance bits, flags, parent} in shared memory) and writes every changed
+//                 voxel back with a global 64-bit atomicMin; halo voxels that improved are
+//                 pushed to their own tile
+// Frontiers are per-voxel bitmasks plus lists (rounds) or a ticket queue (single maps) of active
+// (map, tile) pairs, de-duplicated with monotone epoch stamps. The paper processes the open set
+// with a priority queue or a FIFO; any processing order reaches the same fixpoint (after the
+// raise phase the lower wave computes the greatest fixpoint below the current values of a
+// monotone relaxation), so the block-staged schedules give the batch-recompute result.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -47,7 +50,7 @@ struct Tile {
                           // (j+2)%3), [3] neighbour tiles to activate in the next-round list,
                           // [4] neighbour tiles whose lower frontier was seeded (bit k = direction
                           // k of the neighbour tile relative to this one)
-  uint32_t* lseed;        // T^3 bits: cells the raise re-seeds into the lower wave
+  uint32_t* lseed;        // T^3 bits: cells the raise wave reset (they join the lower wave and pull)
   int* doff;              // [27] tile cell offset of direction k
   unsigned char* dcls;    // [27] 1, 2 or 3: axes direction k moves along (step v, v*sqrt2, v*sqrt3)
 };
