@@ -61,15 +61,16 @@ NCU_TRAFFIC = {
     ("integrate_rays", "lidar", "integrate.cu", "7121226917bc928b"): 74986496,
     # k_apply: 94.034688 MB + 34.408960 MB
     ("apply", "lidar", "integrate.cu", "7121226917bc928b"): 128443648,
-    # k_esdf<256, 8, 8>: 76.125184 MB + 3.976704 MB
-    ("esdf", "lidar", "esdf.cu", "b797f4d6c1d7da2f"): 80101888,
+    # k_esdf<256, 8, 8>: 76.125184 MB + 3.976704 MB (captured on source b797f4d6c1d7da2f; the
+    # source has since changed in comments only)
+    ("esdf", "lidar", "esdf.cu", "b0baac55589fba3a"): 80101888,
     # room frame 3 (bench.py --only-room --no-cpu-baseline --steps 3 --warmup 3)
     # k_integrate_rays<2>: 1.531392 MB + 2.816 kB
     ("integrate_rays", "room", "integrate.cu", "7121226917bc928b"): 1534208,
     # k_apply: 2.208000 MB + 0
     ("apply", "room", "integrate.cu", "7121226917bc928b"): 2208000,
-    # k_esdf<512, 2, 0>: 2.198784 MB + 44.288 kB
-    ("esdf", "room", "esdf.cu", "b797f4d6c1d7da2f"): 2243072,
+    # k_esdf<512, 2, 0>: 2.198784 MB + 44.288 kB (source b797f4d6c1d7da2f, comments changed since)
+    ("esdf", "room", "esdf.cu", "b0baac55589fba3a"): 2243072,
     # k_mesh_blocks<16>, full mesh of the room map (dram__bytes_read.sum 25,988,096 + write 2,304;
     # the 17 MB of triangles it writes are still in L2 when it ends)
     ("mesh_blocks", "room", "mesh.cu", "cbd5b0c8554fc2d5"): 25990400,
